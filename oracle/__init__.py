@@ -1,0 +1,414 @@
+"""CPU oracle for the one-sided hyperbolic (J-)Jacobi method.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the benchmark's
+CPU-baseline leg import this package. The product library (the CUDA path)
+never imports, links or calls it, and the two share no code. The oracle is
+plain and slow on purpose: every function follows one passage of the paper
+("Three-Level Parallel J-Jacobi Algorithms for Hermitian Matrices", Singer et
+al.) in the paper's order and notation.
+
+Contents
+  rotation(...)        Alg. 3.1 rotation parameters (C, jj_oracle_body.h).
+  solve_plain(...)     Alg. 3.2 + Alg. 3.1, non-blocked, float64 or long double,
+                       row-cyclic / column-cyclic / round-robin order (C).
+  eigenpairs(...)      lambda_i = J_ii ||g_i||^2, u_i = g_i/||g_i|| (Alg. 5.2 end).
+  uniform_partition    block sizes of the uniform partition (3.3).
+  schedule(...)        per-step block pairs of Initialize/MMStep/RLStep
+                       (Algs. 4.1-4.3), simulated rank by rank.
+  column_rr_table(n)   the round-robin order of Alg. 4.3 over single columns.
+  solve_blocked(...)   the two-level full-block algorithm (2F) of Alg. 5.2 on one
+                       address space: Gram (3.6), Cholesky, inner Alg. 3.2 on R
+                       with explicit accumulation of W (3.12), update (2.9).
+
+Every function is pinned by tests/test_oracle_*.py against closed forms,
+invariants, constructions with known eigenvalues, LAPACK special cases and
+brute force; none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_NAME = "liboracle_jj.so"
+_lib = None
+
+# Convergence threshold of the published workloads: 128 * eps with
+# eps = 2^-53 (unit roundoff of float64).
+TOL_DEFAULT = 128.0 * 2.0 ** -53
+
+ORDER_ROW_CYCLIC = 0
+ORDER_COLUMN_CYCLIC = 1
+ORDER_ROUND_ROBIN = 2
+
+STRATEGY_ROUND_ROBIN = 0
+STRATEGY_MODULUS = 1
+
+
+def build(outdir: Optional[str] = None, force: bool = False) -> str:
+    """Compile jj_oracle.c into a shared library with gcc (plain C11, -O2)."""
+    outdir = outdir or _HERE
+    out = os.path.join(outdir, _LIB_NAME)
+    src = os.path.join(_HERE, "jj_oracle.c")
+    body = os.path.join(_HERE, "jj_oracle_body.h")
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= max(os.path.getmtime(src), os.path.getmtime(body))):
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build()
+    lib = ctypes.CDLL(path)
+    i64 = ctypes.c_int64
+    vp = ctypes.c_void_p
+    for sfx, R in (("z", ctypes.c_double), ("d", ctypes.c_double),
+                   ("zl", ctypes.c_longdouble), ("dl", ctypes.c_longdouble)):
+        f = getattr(lib, "jjo_solve_" + sfx)
+        f.restype = ctypes.c_int
+        f.argtypes = [i64, i64, vp, i64, vp, R, ctypes.c_int, ctypes.c_int, vp, i64,
+                      vp, vp, vp, ctypes.c_int, vp, ctypes.c_int]
+        g = getattr(lib, "jjo_eig_" + sfx)
+        g.restype = None
+        g.argtypes = [i64, i64, vp, i64, vp, vp, vp, i64]
+        h = getattr(lib, "jjo_rotation_" + sfx)
+        h.restype = ctypes.c_int
+        h.argtypes = [R, R, R, R, ctypes.c_int, ctypes.c_int, vp]
+    lib.jjo_long_double_mantissa_bits.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def long_double_bits() -> int:
+    """Mantissa bits of this host's C long double (64 on x86-64, 113 on aarch64)."""
+    return _load().jjo_long_double_mantissa_bits()
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _suffix(cplx: bool, precision: str) -> str:
+    return ("z" if cplx else "d") + ("l" if precision == "ld" else "")
+
+
+def rotation(arr: float, ass: float, ars: complex, hyp: int, cplx: bool = True,
+             precision: str = "f64", mutation: int = 0) -> Optional[Dict[str, float]]:
+    """Rotation parameters of Alg. 3.1 for one pivot (a_rr, a_ss, a_rs), hyp = J_rr J_ss.
+
+    Returns c, s, e^{i alpha}, t, eta and the updated d_rr, d_ss, or None if the
+    hyperbolic case has theta^2 < 1 (pivot not positive definite).
+    """
+    lib = _load()
+    sfx = _suffix(cplx, precision)
+    R = np.longdouble if precision == "ld" else np.float64
+    out = np.zeros(8, dtype=R)
+    ars = complex(ars)
+    rc = getattr(lib, "jjo_rotation_" + sfx)(arr, ass, ars.real, ars.imag, int(hyp),
+                                             int(mutation), _ptr(out))
+    if rc:
+        return None
+    return dict(c=out[0], s=out[1], e=complex(float(out[2]), float(out[3])), t=out[4],
+                eta=out[5], d_r=out[6], d_s=out[7])
+
+
+def _as_work(G: np.ndarray, precision: str) -> np.ndarray:
+    cplx = np.iscomplexobj(G)
+    if precision == "ld":
+        dt = np.clongdouble if cplx else np.longdouble
+    else:
+        dt = np.complex128 if cplx else np.float64
+    return np.asfortranarray(np.array(G, dtype=dt, copy=True))
+
+
+def solve_plain(G: np.ndarray, J: Sequence[int], tol: float = TOL_DEFAULT,
+                max_sweeps: int = 60, order: int = ORDER_ROW_CYCLIC,
+                accumulate: bool = False, precision: str = "f64",
+                mutation: int = 0) -> Dict[str, object]:
+    """Non-blocked one-sided J-Jacobi (Alg. 3.2 with Alg. 3.1 as the sweep).
+
+    G is m x n (m >= n, full column rank), J a vector of +-1. Returns a dict with
+    the final Gt = G W, the eigenpairs (lam, U), the accumulated W (if asked),
+    the number of sweeps, applied rotations, the status (0 converged,
+    2 not converged, 3 loss of positive definiteness) and the largest scaled
+    off-diagonal |a_rs|/sqrt(a_rr a_ss) seen in the last sweep.
+    """
+    lib = _load()
+    cplx = np.iscomplexobj(G)
+    sfx = _suffix(cplx, precision)
+    Gw = _as_work(G, precision)
+    m, n = Gw.shape
+    Jc = np.ascontiguousarray(np.asarray(J, dtype=np.int32))
+    W = None
+    if accumulate:
+        W = np.asfortranarray(np.zeros((n, n), dtype=Gw.dtype))
+    sweeps = np.zeros(1, dtype=np.int32)
+    rots = np.zeros(1, dtype=np.int64)
+    R = np.longdouble if precision == "ld" else np.float64
+    maxoff = np.zeros(1, dtype=R)
+    table = None
+    nsteps = 0
+    if order == ORDER_ROUND_ROBIN:
+        tab = column_rr_table(n)
+        nsteps = tab.shape[0]
+        table = np.ascontiguousarray(tab.astype(np.int32))
+    st = getattr(lib, "jjo_solve_" + sfx)(m, n, _ptr(Gw), m, _ptr(Jc), tol, max_sweeps,
+                                          order, _ptr(W), n, _ptr(sweeps), _ptr(rots),
+                                          _ptr(maxoff), int(mutation), _ptr(table), nsteps)
+    lam, U = eigenpairs(Gw, Jc, precision=precision)
+    return dict(Gt=Gw, lam=lam, U=U, W=W, sweeps=int(sweeps[0]), rotations=int(rots[0]),
+                status=int(st), maxoff=float(maxoff[0]))
+
+
+def eigenpairs(Gt: np.ndarray, J: Sequence[int], precision: Optional[str] = None
+               ) -> Tuple[np.ndarray, np.ndarray]:
+    """lambda_i = J_ii ||g_i||^2 and u_i = g_i/||g_i|| from the final factor (Alg. 5.2)."""
+    lib = _load()
+    cplx = np.iscomplexobj(Gt)
+    if precision is None:
+        precision = "ld" if Gt.dtype in (np.longdouble, np.clongdouble) else "f64"
+    Gw = _as_work(Gt, precision)
+    m, n = Gw.shape
+    Jc = np.ascontiguousarray(np.asarray(J, dtype=np.int32))
+    R = np.longdouble if precision == "ld" else np.float64
+    lam = np.zeros(n, dtype=R)
+    U = np.asfortranarray(np.zeros_like(Gw))
+    getattr(lib, "jjo_eig_" + _suffix(cplx, precision))(m, n, _ptr(Gw), m, _ptr(Jc),
+                                                        _ptr(lam), _ptr(U), m)
+    return lam, U
+
+
+# ---------------------------------------------------------------------------
+# Block partition and parallel orderings (Secs. 3.1, 4.1, 4.2)
+# ---------------------------------------------------------------------------
+
+def uniform_partition(n: int, nbl: int) -> List[int]:
+    """Block sizes of the uniform partition (3.3): the first n mod nbl blocks get
+    floor(n/nbl)+1 columns, the rest floor(n/nbl)."""
+    assert 1 <= nbl <= n
+    br = n % nbl
+    nmin = n // nbl
+    return [nmin + 1 if l < br else nmin for l in range(nbl)]
+
+
+def _initialize(rank: int, nbl: int):
+    """Alg. 4.1: starting pivot of process `rank` (1-based block indices)."""
+    ip = rank + 1
+    i_blk = ip
+    jp = nbl - rank
+    j_blk = jp
+    return [ip, jp, i_blk, j_blk]
+
+
+def _ring(rank: int, nproc: int, nsweep: int) -> Tuple[int, int]:
+    """Neighbour ranks of Algs. 4.2/4.3 (their last if/else): (snd_rnk, rcv_rnk)."""
+    if nsweep % 2 > 0:
+        return (nproc + rank - 1) % nproc, (nproc + rank + 1) % nproc
+    return (nproc + rank + 1) % nproc, (nproc + rank - 1) % nproc
+
+
+def _mm_step(rank, nbl, nproc, nsweep, state):
+    """Alg. 4.2 (modified modulus), one step for one process."""
+    ip, jp, i_blk, j_blk = state
+    if ip + jp > nbl:
+        snd_blk = i_blk
+        ip = ip + 1
+        if ip == jp:
+            ip = ip - nbl // 2
+            jp = ip
+        i_blk = ip
+        rcv_blk = i_blk
+    else:
+        snd_blk = j_blk
+        jp = jp + 1
+        j_blk = jp
+        rcv_blk = j_blk
+    snd_rnk, rcv_rnk = _ring(rank, nproc, nsweep)
+    return [ip, jp, i_blk, j_blk], snd_blk, rcv_blk, snd_rnk, rcv_rnk, 0
+
+
+def _rl_step(rank, nbl, nproc, nsweep, state):
+    """Alg. 4.3 (modified round-robin), one step for one process."""
+    ip, jp, i_blk, j_blk = state
+    swflag = 0
+    if ip + jp > nbl:
+        if jp < nbl:
+            snd_blk = i_blk
+            ip = ip + 1
+            if ip < jp:
+                i_blk = ip
+                rcv_blk = i_blk
+            else:
+                ip = jp
+                i_blk = j_blk
+                swflag = 1
+                jp = nbl
+                j_blk = jp
+                rcv_blk = j_blk
+        else:
+            if ip > nbl // 2:
+                snd_blk = i_blk
+                ip = ip - nbl // 2 + 1
+                i_blk = ip
+                rcv_blk = i_blk
+            else:
+                snd_blk = j_blk
+                jp = ip + 1
+                j_blk = jp
+                rcv_blk = j_blk
+    else:
+        snd_blk = j_blk
+        jp = jp + 1
+        j_blk = jp
+        rcv_blk = j_blk
+    snd_rnk, rcv_rnk = _ring(rank, nproc, nsweep)
+    return [ip, jp, i_blk, j_blk], snd_blk, rcv_blk, snd_rnk, rcv_rnk, swflag
+
+
+def steps_per_sweep(nbl: int, strategy: int) -> int:
+    """2p steps for modulus, 2p - 1 for round-robin (Sec. 5.3), nbl = 2p."""
+    return nbl if strategy == STRATEGY_MODULUS else nbl - 1
+
+
+def simulate(nbl: int, strategy: int, sweeps: int = 1) -> List[List[dict]]:
+    """Run Initialize and then MMStep/RLStep for every process for `sweeps` sweeps.
+
+    Returns, per sweep, per step, a dict with the per-rank pivot blocks
+    `pairs[q] = (i_blk, j_blk)` (1-based, as held by process q at that step,
+    before the step's exchange) and the exchange that follows the step:
+    `snd_blk[q]`, `rcv_blk[q]`, `snd_rnk[q]`, `rcv_rnk[q]`.
+    """
+    assert nbl >= 2 and nbl % 2 == 0
+    p = nbl // 2
+    st = [_initialize(q, nbl) for q in range(p)]
+    stepfn = _mm_step if strategy == STRATEGY_MODULUS else _rl_step
+    out = []
+    for nsweep in range(1, sweeps + 1):
+        tab = []
+        for _ in range(steps_per_sweep(nbl, strategy)):
+            rec = dict(pairs=[(s[2], s[3]) for s in st], snd_blk=[], rcv_blk=[],
+                       snd_rnk=[], rcv_rnk=[])
+            new = []
+            for q in range(p):
+                ns, sb, rb, sr, rr, _ = stepfn(q, nbl, p, nsweep, st[q])
+                new.append(ns)
+                rec["snd_blk"].append(sb)
+                rec["rcv_blk"].append(rb)
+                rec["snd_rnk"].append(sr)
+                rec["rcv_rnk"].append(rr)
+            st = new
+            tab.append(rec)
+        out.append(tab)
+    return out
+
+
+def schedule(nbl: int, strategy: int, sweep: int = 1) -> np.ndarray:
+    """Block pairs of one sweep as an int array [steps, nbl/2, 2], 0-based, i < j.
+
+    Pair q of a step is the pivot held by process q (Sec. 5.3)."""
+    tab = simulate(nbl, strategy, sweep)[sweep - 1]
+    arr = np.zeros((len(tab), nbl // 2, 2), dtype=np.int64)
+    for s, rec in enumerate(tab):
+        for q, (a, b) in enumerate(rec["pairs"]):
+            arr[s, q] = (min(a, b) - 1, max(a, b) - 1)
+    return arr
+
+
+def column_rr_table(n: int) -> np.ndarray:
+    """Round-robin order over single columns for the plain parallel sweep:
+    the pairs of Alg. 4.3 with every 'block' one column (n padded to even;
+    index n is the dummy column, skipped)."""
+    npl = n + (n & 1)
+    if npl < 2:
+        return np.zeros((0, 1, 2), dtype=np.int64)
+    return schedule(npl, STRATEGY_ROUND_ROBIN, 1)
+
+
+# ---------------------------------------------------------------------------
+# Blocked two-level full-block algorithm (Alg. 5.2, case 2F) on one process
+# ---------------------------------------------------------------------------
+
+def j_sort_permutation(J: Sequence[int]) -> np.ndarray:
+    """Column permutation P1 that orders J as diag(I_nu, -I_{n-nu}) (Sec. 2.3), stable."""
+    J = np.asarray(J)
+    return np.concatenate([np.nonzero(J > 0)[0], np.nonzero(J < 0)[0]])
+
+
+def solve_blocked(G: np.ndarray, J: Sequence[int], block_width: int,
+                  strategy: int = STRATEGY_ROUND_ROBIN, tol: float = TOL_DEFAULT,
+                  max_sweeps: int = 60, inner_max_sweeps: int = 30,
+                  max_steps: Optional[int] = None) -> Dict[str, object]:
+    """Two-level full-block one-sided J-Jacobi (Alg. 5.2, 2F), sequentially.
+
+    Steps of one parallel step, for every pivot pair (i, j) of the schedule:
+      A_P = [G_i G_j]^* [G_i G_j]                       (3.6), (4.1)
+      A_P = R^* R (Cholesky, R upper triangular)        (3.8)
+      R W = U Sigma by Alg. 3.2 on R with J_P, W accumulated explicitly (3.12)
+      [G_i G_j] <- [G_i G_j] W                          (2.9)
+    J is first sorted as diag(I, -I) by P1 (Sec. 2.3); the blocks are the
+    uniform partition (3.3) with nbl = 2 ceil(n / (2 b)) blocks. A sweep with no
+    inner rotation ends the iteration (Sec. 5.3). The returned Gt is in the
+    caller's original column order. `max_steps` stops after that many parallel
+    steps (for step-by-step comparisons).
+    """
+    G = np.asarray(G)
+    m, n = G.shape
+    Jv = np.asarray(J, dtype=np.int64)
+    perm = j_sort_permutation(Jv)
+    Gp = np.asfortranarray(G[:, perm].astype(np.complex128 if np.iscomplexobj(G) else np.float64))
+    Jp = Jv[perm]
+    nbl = 2 * ((n + 2 * block_width - 1) // (2 * block_width))
+    nbl = max(2, min(nbl, n - (n & 1)))
+    sizes = uniform_partition(n, nbl)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    status = 2
+    sweeps = 0
+    total_rot = 0
+    steps_done = 0
+    for sweep in range(1, max_sweeps + 1):
+        sweeps = sweep
+        tab = schedule(nbl, strategy, sweep)
+        rot_sweep = 0
+        for step in range(tab.shape[0]):
+            if max_steps is not None and steps_done >= max_steps:
+                break
+            for q in range(tab.shape[1]):
+                i, j = tab[step, q]
+                cols = np.concatenate([np.arange(offs[i], offs[i + 1]),
+                                       np.arange(offs[j], offs[j + 1])])
+                GP = Gp[:, cols]
+                AP = GP.conj().T @ GP
+                try:
+                    L = np.linalg.cholesky(AP)
+                except np.linalg.LinAlgError:
+                    return dict(Gt=None, status=3, sweeps=sweeps, rotations=total_rot)
+                Rm = np.asfortranarray(L.conj().T)
+                res = solve_plain(Rm, Jp[cols], tol=tol, max_sweeps=inner_max_sweeps,
+                                  order=ORDER_ROW_CYCLIC, accumulate=True)
+                if res["status"] == 3:
+                    return dict(Gt=None, status=3, sweeps=sweeps, rotations=total_rot)
+                rot_sweep += res["rotations"]
+                Gp[:, cols] = GP @ res["W"]
+            steps_done += 1
+        total_rot += rot_sweep
+        if max_steps is not None and steps_done >= max_steps:
+            status = 2
+            break
+        if rot_sweep == 0:
+            status = 0
+            break
+    Gt = np.empty_like(Gp)
+    Gt[:, perm] = Gp
+    lam, U = eigenpairs(Gt, Jv)
+    return dict(Gt=Gt, lam=lam, U=U, status=status, sweeps=sweeps, rotations=total_rot,
+                nbl=nbl, sizes=sizes)
