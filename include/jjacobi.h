@@ -1,0 +1,164 @@
+/*
+ * jjacobi.h -- C ABI of the GB300 one-sided hyperbolic (J-)Jacobi eigensolver.
+ *
+ * Problem (Sec. 2.2, (2.5)-(2.6); Alg. 5.2 "Parallel_Jacobi"): given a full
+ * column rank factor G (m x n, m >= n) and J = diag(+-1) with H = G J G^*,
+ * compute the eigenpairs of H belonging to its nonzero eigenvalues by the
+ * one-sided J-Jacobi method: J-unitary plane rotations from the right on G
+ * ((2.9), trigonometric when J_rr = J_ss, hyperbolic otherwise (2.7)) until the
+ * columns of G~ = G W are orthogonal to working precision (2.10); then
+ *     lambda_i = J_ii ||g~_i||^2,   u_i = g~_i / ||g~_i||    (Alg. 5.2, end).
+ *
+ * Forms:
+ *   block_width == 0  plain, non-blocked method (Algs. 3.1/3.2) with the
+ *                     round-robin parallel order over single columns.
+ *   block_width  > 0  blocked full-block method (Sec. 3.3, Alg. 5.2 case 2F):
+ *                     per parallel step, for every block pair (i, j):
+ *                     Gram A_P = [G_i G_j]^*[G_i G_j] (3.6), Cholesky
+ *                     A_P = R^* R (3.8), inner J-Jacobi R W_P = U Sigma with W_P
+ *                     accumulated (3.12), update [G_i G_j] <- [G_i G_j] W_P (2.9).
+ *   inner_block_width > 0   three-level form (Sec. 5.1, case 3F): the inner
+ *                     J-Jacobi on R is itself blocked (Alg. 3.3).
+ *
+ * Conventions (all entry points):
+ *   - Matrices are column-major with a leading dimension (ld >= rows), as in
+ *     the paper's Fortran (Sec. 2.3). Complex values are interleaved
+ *     (re, im) pairs of doubles (C99 double complex layout).
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary host memory (pinned is faster).
+ *   - J is a host array of n int8 entries, each +1 or -1.
+ *   - Every call returns a status (jj_status); no exception crosses the ABI.
+ *     On failure, output buffers may hold partial results.
+ *   - A handle is used by one host thread at a time; different handles are
+ *     independent. Work is enqueued on the handle's stream; calls that return
+ *     results to the host synchronise that stream.
+ */
+#ifndef JJACOBI_H
+#define JJACOBI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JJACOBI_VERSION 10000 /* 1.0.0 */
+
+typedef struct jj_ctx *jj_handle;
+
+/* Element type of G. */
+typedef enum { JJ_F64 = 0, JJ_C128 = 1 } jj_dtype;
+
+/* Parallel block-pivot strategy (Sec. 4): modified round-robin (Alg. 4.3,
+ * nbl - 1 steps per sweep) or modified modulus (Alg. 4.2, nbl steps, the
+ * blocks on the p-th superdiagonal transformed twice). */
+typedef enum { JJ_ORDER_ROUND_ROBIN = 0, JJ_ORDER_MODULUS = 1 } jj_order;
+
+/* How the blocked form computes its two dense contractions (Gram (3.6) and
+ * update (2.9)): FP64 on the FP64 pipe, or split into exact fp16 slices on the
+ * tensor cores (tcgen05) with fp32 accumulation and FP64 recombination. */
+typedef enum { JJ_GEMM_FP64 = 0, JJ_GEMM_OZAKI_FP16 = 1, JJ_GEMM_AUTO = 3 } jj_gemm;
+
+typedef enum {
+    JJ_OK = 0,
+    JJ_INVALID_ARG = 1,    /* m < n, n < 1, bad ld, J entry not +-1, bad params */
+    JJ_NOT_CONVERGED = 2,  /* max_sweeps reached; results are still extractable */
+    JJ_NOT_POSDEF = 3,     /* G not of full column rank in working precision
+                              (a pivot Cholesky or a hyperbolic rotation failed,
+                              Secs. 2.2, 3.2) */
+    JJ_NONFINITE = 4,      /* NaN or Inf met in G or in a rotation */
+    JJ_DEVICE_TIMEOUT = 5, /* a bounded device-side wait expired */
+    JJ_CUDA_ERROR = 6,     /* a CUDA runtime call failed */
+    JJ_NOT_SOLVED = 7      /* extract called before a successful solve */
+} jj_status;
+
+typedef struct {
+    int64_t m;                 /* rows of G (m >= n) */
+    int64_t n;                 /* columns of G */
+    int32_t dtype;             /* jj_dtype */
+    int32_t block_width;       /* 0: plain; >0: target columns per block (b) */
+    int32_t inner_block_width; /* 0: two-level; >0: inner block width (three-level) */
+    int32_t order;             /* jj_order (blocked form; the plain form is round-robin) */
+    int32_t gemm;              /* jj_gemm */
+    int32_t ozaki_slices;      /* 0: automatic */
+    double tol;                /* <= 0: 128 * 2^-53; rotate when |a_rs| > tol sqrt(a_rr a_ss) */
+    int32_t max_sweeps;        /* <= 0: 60 */
+    int32_t inner_max_sweeps;  /* <= 0: 30 (inner J-Jacobi on R, blocked form) */
+    void *cuda_stream;         /* cudaStream_t to run on; NULL: the legacy default stream */
+} jj_params;
+
+typedef struct {
+    int32_t status;            /* jj_status of the call */
+    int32_t sweeps;            /* sweeps run (the last one applied no rotation if converged) */
+    int64_t rotations;         /* rotations applied (inner rotations in the blocked form) */
+    double last_max_offdiag;   /* max |a_rs| / sqrt(a_rr a_ss) seen in the last sweep */
+    double seconds;            /* wall time of the call */
+    int32_t block_width;       /* block width actually used (0 for plain) */
+    int32_t nbl;               /* number of blocks (2 x pairs per step), 0 for plain */
+    int32_t steps_per_sweep;   /* parallel steps per sweep */
+    int32_t kernel_launches;   /* kernels launched by the call */
+} jj_info;
+
+/* Fill *p with defaults for an m x n problem of the given dtype (plain form). */
+void jjacobi_default_params(jj_params *p, int64_t m, int64_t n, int32_t dtype);
+
+/* Create a solver handle for problems of size p->m x p->n: validates the
+ * parameters, allocates every device workspace (the ping-pong copies of G that
+ * hold the block columns of the update (Sec. 3.3), the pivot Gram/R/W blocks,
+ * the ordering tables and counters). Returns JJ_INVALID_ARG or JJ_CUDA_ERROR on
+ * failure, with *h set to NULL. */
+int jjacobi_create(jj_handle *h, const jj_params *p);
+
+/* Solve H = G J G^* in place: G (device, m x n, leading dimension ldg >= m,
+ * dtype of the handle) is overwritten by G~ = G W in the caller's column order
+ * (the final re-permutation of Sec. 3.3). J (host, n entries of +-1) is copied.
+ * Columns are permuted internally so that J = diag(I, -I) (Sec. 2.3).
+ * info may be NULL. The handle keeps the G pointer for jjacobi_extract. */
+int jjacobi_solve(jj_handle h, void *G, int64_t ldg, const int8_t *J, jj_info *info);
+
+/* Eigenpairs of the last solve (Alg. 5.2): lambda[i] = J_ii ||g~_i||^2
+ * (host or device pointer, n doubles, detected), and if U is not NULL
+ * (device, m x n, ldu >= m, dtype of the handle) u_i = g~_i / ||g~_i||.
+ * Column i belongs to column i of the caller's G. sort != 0 sorts lambda
+ * ascending (and U with it). */
+int jjacobi_extract(jj_handle h, double *lambda, void *U, int64_t ldu, int32_t sort);
+
+/* End-to-end call with host buffers: copies G_host (m x n, ldg) to the device,
+ * solves, extracts lambda_host (n doubles) and, if U_host is not NULL, the
+ * eigenvectors (m x n, ldu), and copies them back. G_host is not modified. */
+int jjacobi_solve_host(jj_handle h, const void *G_host, int64_t ldg, const int8_t *J,
+                       double *lambda_host, void *U_host, int64_t ldu, jj_info *info);
+
+/* Batched solve of `count` independent problems of uneven order in one stream
+ * of launches (every parallel step of every problem in one launch per kernel).
+ * G[k] (device, m[k] x n[k], ldg[k]) is overwritten by G~_k; J[k] host.
+ * The handle's m and n are the maxima allowed (p->m >= max m[k], p->n >= max n[k]);
+ * infos (may be NULL) receives one jj_info per problem. lambda_out (device,
+ * sum of n[k] doubles, problem k at offset sum_{l<k} n[l]) receives the
+ * eigenvalues if not NULL. */
+int jjacobi_solve_batched(jj_handle h, int32_t count, void *const *G, const int64_t *m,
+                          const int64_t *n, const int64_t *ldg, const int8_t *const *J,
+                          double *lambda_out, jj_info *infos);
+
+/* Release the handle and every device resource it owns. NULL is a no-op. */
+void jjacobi_destroy(jj_handle h);
+
+/* Human-readable name of a jj_status value. */
+const char *jjacobi_status_string(int status);
+
+/* Library version (JJACOBI_VERSION). */
+int32_t jjacobi_version(void);
+
+/* The block pairs of one sweep of the parallel ordering for nbl blocks
+ * (nbl even >= 2): Initialize (Alg. 4.1) then RLStep (Alg. 4.3) or MMStep
+ * (Alg. 4.2) for every process, sweep number `sweep` (>= 1). Writes
+ * steps x (nbl/2) pairs (i, j), 0-based, i < j, pair q being the pivot of
+ * process q, into pairs (host, capacity >= 2 * nbl * nbl/2 ints) and returns the
+ * number of steps, or -1 on invalid arguments. */
+int32_t jjacobi_schedule(int32_t nbl, int32_t order, int32_t sweep, int32_t *pairs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JJACOBI_H */

@@ -16,6 +16,8 @@ Contents
   schedule(...)        per-step block pairs of Initialize/MMStep/RLStep
                        (Algs. 4.1-4.3), simulated rank by rank.
   column_rr_table(n)   the round-robin order of Alg. 4.3 over single columns.
+  gram, cholesky_upper, inner_solve, update
+                       the four steps of one pivot of the blocked form.
   solve_blocked(...)   the two-level full-block algorithm (2F) of Alg. 5.2 on one
                        address space: Gram (3.6), Cholesky, inner Alg. 3.2 on R
                        with explicit accumulation of W (3.12), update (2.9).
@@ -344,6 +346,36 @@ def j_sort_permutation(J: Sequence[int]) -> np.ndarray:
     return np.concatenate([np.nonzero(J > 0)[0], np.nonzero(J < 0)[0]])
 
 
+def gram(GP: np.ndarray) -> np.ndarray:
+    """Pivot Gram A_P = G_P^* G_P of (3.6) (a library matmul as the step)."""
+    GP = np.asarray(GP)
+    return GP.conj().T @ GP
+
+
+def cholesky_upper(AP: np.ndarray) -> np.ndarray:
+    """Cholesky factor R (upper, positive diagonal) with A_P = R^* R, (3.8).
+
+    Uses LAPACK's lower Cholesky, R = L^*; raises LinAlgError if A_P is not
+    positive definite (G_P not of full column rank, Sec. 3.2)."""
+    L = np.linalg.cholesky(np.asarray(AP))
+    return np.asfortranarray(L.conj().T)
+
+
+def inner_solve(R: np.ndarray, JP: Sequence[int], tol: float = TOL_DEFAULT,
+                max_sweeps: int = 30) -> Dict[str, object]:
+    """HSVD of the pivot factor, R W = U Sigma (3.12), by Alg. 3.2 applied to
+    the columns of R with the transformations accumulated explicitly in W."""
+    res = solve_plain(R, JP, tol=tol, max_sweeps=max_sweeps, order=ORDER_ROW_CYCLIC,
+                      accumulate=True)
+    return dict(Rt=res["Gt"], W=res["W"], status=res["status"], rotations=res["rotations"],
+                lam=res["lam"])
+
+
+def update(GP: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """Block update [G_i G_j] <- [G_i G_j] W of (2.9) (a library matmul)."""
+    return np.asarray(GP) @ np.asarray(W)
+
+
 def solve_blocked(G: np.ndarray, J: Sequence[int], block_width: int,
                   strategy: int = STRATEGY_ROUND_ROBIN, tol: float = TOL_DEFAULT,
                   max_sweeps: int = 60, inner_max_sweeps: int = 30,
@@ -387,18 +419,16 @@ def solve_blocked(G: np.ndarray, J: Sequence[int], block_width: int,
                 cols = np.concatenate([np.arange(offs[i], offs[i + 1]),
                                        np.arange(offs[j], offs[j + 1])])
                 GP = Gp[:, cols]
-                AP = GP.conj().T @ GP
+                AP = gram(GP)
                 try:
-                    L = np.linalg.cholesky(AP)
+                    Rm = cholesky_upper(AP)
                 except np.linalg.LinAlgError:
                     return dict(Gt=None, status=3, sweeps=sweeps, rotations=total_rot)
-                Rm = np.asfortranarray(L.conj().T)
-                res = solve_plain(Rm, Jp[cols], tol=tol, max_sweeps=inner_max_sweeps,
-                                  order=ORDER_ROW_CYCLIC, accumulate=True)
+                res = inner_solve(Rm, Jp[cols], tol=tol, max_sweeps=inner_max_sweeps)
                 if res["status"] == 3:
                     return dict(Gt=None, status=3, sweeps=sweeps, rotations=total_rot)
                 rot_sweep += res["rotations"]
-                Gp[:, cols] = GP @ res["W"]
+                Gp[:, cols] = update(GP, res["W"])
             steps_done += 1
         total_rot += rot_sweep
         if max_steps is not None and steps_done >= max_steps:

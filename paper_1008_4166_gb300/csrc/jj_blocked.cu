@@ -1,0 +1,451 @@
+// Blocked full-block form, FP64 kernels: the pivot Gram (3.6), the inner
+// solve on the Cholesky factor (Cholesky (3.8) + one-sided J-Jacobi (3.12)
+// with explicit accumulation of W_P) and the block update (2.9).
+//
+// Pair descriptor: int32 {off_i, n_i, off_j, n_j}; the k = n_i + n_j pivot
+// columns are G[:, off_i + a] for a < n_i and G[:, off_j + a - n_i] after.
+// Per-pair blocks (A_P, R, W_P) are kmax x kmax column-major at
+// pair * kmax * kmax elements (complex: interleaved).
+#include "jj_common.cuh"
+
+namespace jj {
+namespace {
+
+__device__ __forceinline__ int64_t pivot_col(const int32_t *pd, int a) {
+    return a < pd[1] ? (int64_t)pd[0] + a : (int64_t)pd[2] + (a - pd[1]);
+}
+
+// ---------------------------------------------------------------------------
+// Gram, FP64 on the FP64 pipe: one block per (32 x 32 tile of A_P, pair);
+// only tiles on or above the diagonal are formed, the lower triangle is
+// written as the conjugate transpose.
+// ---------------------------------------------------------------------------
+constexpr int GT = 32;   // output tile edge
+constexpr int GKR = 16;  // rows of G staged per k-step
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) gram_fp64_kernel(const double *__restrict__ G, int64_t ld,
+                                                         int64_t m, const int32_t *__restrict__ pairs,
+                                                         double *__restrict__ A, int kmax) {
+    constexpr int E = CPLX ? 2 : 1;
+    __shared__ double xa[GKR][GT][E];
+    __shared__ double xb[GKR][GT][E];
+    const int32_t *pd = pairs + 4 * blockIdx.y;
+    const int k = pd[1] + pd[3];
+    // map linear tile index to (ta, tb) with ta <= tb
+    int t = blockIdx.x, ta = 0;
+    const int T = (kmax + GT - 1) / GT;
+    while (t >= T - ta) {
+        t -= T - ta;
+        ++ta;
+    }
+    const int tb = ta + t;
+    const int a0 = ta * GT, b0 = tb * GT;
+    if (a0 >= k || b0 >= k) return;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2 x 2 outputs each
+    double acc[2][2][E];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[i][j][e] = 0.0;
+    // loader: 256 threads load GKR x GT entries of each operand
+    const int lr = threadIdx.x / GT * 2;  // 0,2,..,14 (rows, two per thread)
+    const int lc = threadIdx.x % GT;
+    const int64_t ca = a0 + lc < k ? pivot_col(pd, a0 + lc) : -1;
+    const int64_t cb = b0 + lc < k ? pivot_col(pd, b0 + lc) : -1;
+    for (int64_t l0 = 0; l0 < m; l0 += GKR) {
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+            const int64_t l = l0 + lr + rr;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                xa[lr + rr][lc][e] = (ca >= 0 && l < m) ? G[(ca * ld + l) * E + e] : 0.0;
+                xb[lr + rr][lc][e] = (cb >= 0 && l < m) ? G[(cb * ld + l) * E + e] : 0.0;
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int q = 0; q < GKR; ++q) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int a = ty + 16 * i;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int b = tx + 16 * j;
+                    if (CPLX) {
+                        const double ar = xa[q][a][0], ai = xa[q][a][1];
+                        const double br = xb[q][b][0], bi = xb[q][b][1];
+                        acc[i][j][0] = fma(ar, br, fma(ai, bi, acc[i][j][0]));
+                        acc[i][j][E - 1] = fma(ar, bi, fma(-ai, br, acc[i][j][E - 1]));
+                    } else {
+                        acc[i][j][0] = fma(xa[q][a][0], xb[q][b][0], acc[i][j][0]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    double *Ap = A + (int64_t)blockIdx.y * kmax * kmax * E;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int a = a0 + ty + 16 * i;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int b = b0 + tx + 16 * j;
+            if (a < k && b < k) {
+                Ap[((int64_t)b * kmax + a) * E] = acc[i][j][0];
+                if (CPLX) Ap[((int64_t)b * kmax + a) * E + 1] = acc[i][j][E - 1];
+                if (ta != tb || a != b) {
+                    Ap[((int64_t)a * kmax + b) * E] = acc[i][j][0];
+                    if (CPLX) Ap[((int64_t)a * kmax + b) * E + 1] = -acc[i][j][E - 1];
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Update, FP64: Gd[:, pivot cols] = Gs[:, pivot cols] * W_P. One block per
+// (64-row x 32-column tile, pair).
+// ---------------------------------------------------------------------------
+constexpr int UR = 64, UC = 32, UK = 16;
+
+template <bool CPLX>
+__global__ void __launch_bounds__(256) update_fp64_kernel(const double *__restrict__ Gs,
+                                                           double *__restrict__ Gd, int64_t ld,
+                                                           int64_t m, const int32_t *__restrict__ pairs,
+                                                           const double *__restrict__ W, int kmax) {
+    constexpr int E = CPLX ? 2 : 1;
+    __shared__ double xs[UK][UR][E];
+    __shared__ double ws[UK][UC][E];
+    const int32_t *pd = pairs + 4 * blockIdx.z;
+    const int k = pd[1] + pd[3];
+    const int b0 = blockIdx.y * UC;
+    if (b0 >= k) return;
+    const int64_t l0 = (int64_t)blockIdx.x * UR;
+    const double *Wp = W + (int64_t)blockIdx.z * kmax * kmax * E;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // outputs rows ty+16i (4), cols tx+16j (2)
+    double acc[4][2][E];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[i][j][e] = 0.0;
+    for (int a0 = 0; a0 < k; a0 += UK) {
+        // X tile: UK columns x UR rows (4 entries per thread)
+#pragma unroll
+        for (int v = 0; v < (UK * UR) / 256; ++v) {
+            const int idx = threadIdx.x + 256 * v;
+            const int q = idx / UR, r = idx % UR;
+            const int a = a0 + q;
+            const int64_t l = l0 + r;
+            const bool ok = a < k && l < m;
+            const int64_t col = ok ? pivot_col(pd, a) : 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) xs[q][r][e] = ok ? Gs[(col * ld + l) * E + e] : 0.0;
+        }
+        // W tile: UK rows x UC columns (2 entries per thread)
+#pragma unroll
+        for (int v = 0; v < (UK * UC) / 256; ++v) {
+            const int idx = threadIdx.x + 256 * v;
+            const int q = idx % UK, c = idx / UK;
+            const int a = a0 + q, b = b0 + c;
+            const bool ok = a < k && b < k;
+#pragma unroll
+            for (int e = 0; e < E; ++e) ws[q][c][e] = ok ? Wp[((int64_t)b * kmax + a) * E + e] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int q = 0; q < UK; ++q) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = ty + 16 * i;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int c = tx + 16 * j;
+                    if (CPLX) {
+                        const double xr = xs[q][r][0], xi = xs[q][r][1];
+                        const double wr = ws[q][c][0], wi = ws[q][c][1];
+                        acc[i][j][0] = fma(xr, wr, fma(-xi, wi, acc[i][j][0]));
+                        acc[i][j][E - 1] = fma(xr, wi, fma(xi, wr, acc[i][j][E - 1]));
+                    } else {
+                        acc[i][j][0] = fma(xs[q][r][0], ws[q][c][0], acc[i][j][0]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t l = l0 + ty + 16 * i;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int b = b0 + tx + 16 * j;
+            if (l < m && b < k) {
+                const int64_t col = pivot_col(pd, b);
+#pragma unroll
+                for (int e = 0; e < E; ++e) Gd[(col * ld + l) * E + e] = acc[i][j][e];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inner solve, one block per pair: Cholesky of A_P into R (upper), then the
+// one-sided J-Jacobi method on the k columns of R in the standard round-robin
+// parallel order (k/2 disjoint column pairs per inner step, one warp per
+// pair), W_P accumulated from I. The tracked diagonal is recomputed at the
+// start of each inner sweep (Alg. 3.2). R and W stay in global memory (they are
+// L2-resident) and are accessed with .cg loads/stores.
+// ---------------------------------------------------------------------------
+constexpr int IT = 256;  // threads
+
+template <bool CPLX>
+__device__ __forceinline__ void inner_rr_pair(int npl, int step, int q, int &a, int &b) {
+    // Standard round-robin (circle) schedule over npl (even) players: player
+    // npl-1 is fixed, the others rotate by one each step.
+    const int P = npl - 1;
+    if (q == 0) {
+        a = P;
+        b = step;
+    } else {
+        a = (step + q) % P;
+        b = (step - q + P) % P;
+    }
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, double *__restrict__ Wb,
+                                                    int kmax, const int32_t *__restrict__ pairs,
+                                                    const int8_t *__restrict__ J, double tol,
+                                                    int max_sweeps,
+                                                    unsigned long long *__restrict__ counters) {
+    constexpr int E = CPLX ? 2 : 1;
+    extern __shared__ double smem[];
+    double *dsh = smem;                        // kmax tracked diagonal
+    int *jsh = reinterpret_cast<int *>(dsh + kmax);  // kmax signs
+    __shared__ int s_rot, s_fail;
+    const int32_t *pd = pairs + 4 * blockIdx.x;
+    const int k = pd[1] + pd[3];
+    double *R = A + (int64_t)blockIdx.x * kmax * kmax * E;
+    double *W = Wb + (int64_t)blockIdx.x * kmax * kmax * E;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int a = tid; a < k; a += IT) jsh[a] = J[pivot_col(pd, a)];
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    // --- Cholesky, right-looking, upper: A = R^* R --------------------------
+    for (int j = 0; j < k; ++j) {
+        __shared__ double piv;
+        if (tid == 0) {
+            const double ajj = R[((int64_t)j * kmax + j) * E];
+            if (!(ajj > 0.0) || !isfinite(ajj)) {
+                s_fail = 1;
+                piv = 1.0;
+            } else {
+                piv = sqrt(ajj);
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const double rjj = piv, inv = 1.0 / rjj;
+        // row j of R: r_jl = a_jl / r_jj for l > j
+        for (int l = j + 1 + tid; l < k; l += IT) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) R[((int64_t)l * kmax + j) * E + e] *= inv;
+        }
+        if (tid == 0) {
+            R[((int64_t)j * kmax + j) * E] = rjj;
+            if (CPLX) R[((int64_t)j * kmax + j) * E + 1] = 0.0;
+        }
+        __syncthreads();
+        // trailing update of the upper triangle: a_{l1 l2} -= conj(r_{j l1}) r_{j l2}
+        const int rem = k - j - 1;
+        const int total = rem * (rem + 1) / 2;
+        for (int t = tid; t < total; t += IT) {
+            // t -> (l1 <= l2) over the remaining upper triangle, column-wise
+            int l2 = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+            while ((l2 + 1) * (l2 + 2) / 2 <= t) ++l2;
+            while (l2 * (l2 + 1) / 2 > t) --l2;
+            const int l1 = t - l2 * (l2 + 1) / 2;
+            const int c1 = j + 1 + l1, c2 = j + 1 + l2;
+            if (CPLX) {
+                const double ur = R[((int64_t)c1 * kmax + j) * E], ui = R[((int64_t)c1 * kmax + j) * E + 1];
+                const double vr = R[((int64_t)c2 * kmax + j) * E], vi = R[((int64_t)c2 * kmax + j) * E + 1];
+                double *dst = R + ((int64_t)c2 * kmax + c1) * E;
+                dst[0] -= ur * vr + ui * vi;
+                dst[1] -= ur * vi - ui * vr;
+            } else {
+                R[(int64_t)c2 * kmax + c1] -= R[(int64_t)c1 * kmax + j] * R[(int64_t)c2 * kmax + j];
+            }
+        }
+        __syncthreads();
+    }
+    if (s_fail) {
+        if (tid == 0) atomicOr(&counters[kCntErr], kErrNotPosdef);
+        // leave W = I so that the update is the identity
+        for (int64_t t = tid; t < (int64_t)k * k; t += IT) {
+            const int a = (int)(t % k), b = (int)(t / k);
+            W[((int64_t)b * kmax + a) * E] = a == b ? 1.0 : 0.0;
+            if (CPLX) W[((int64_t)b * kmax + a) * E + 1] = 0.0;
+        }
+        return;
+    }
+    // zero the strictly lower triangle of R, W = I
+    for (int64_t t = tid; t < (int64_t)k * k; t += IT) {
+        const int a = (int)(t % k), b = (int)(t / k);
+        if (a > b) {
+            R[((int64_t)b * kmax + a) * E] = 0.0;
+            if (CPLX) R[((int64_t)b * kmax + a) * E + 1] = 0.0;
+        }
+        W[((int64_t)b * kmax + a) * E] = a == b ? 1.0 : 0.0;
+        if (CPLX) W[((int64_t)b * kmax + a) * E + 1] = 0.0;
+    }
+    __syncthreads();
+    // --- inner one-sided J-Jacobi on the columns of R ------------------------
+    const int npl = k + (k & 1);
+    unsigned long long total_rot = 0;
+    double maxoff = 0.0;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        // d_c = ||r_c||^2
+        for (int c = warp; c < k; c += IT / 32) {
+            double acc = 0.0;
+            for (int l = lane; l < k; l += 32) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const double v = R[((int64_t)c * kmax + l) * E + e];
+                    acc = fma(v, v, acc);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) dsh[c] = acc;
+        }
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        maxoff = 0.0;
+        for (int step = 0; step < npl - 1; ++step) {
+            for (int q = warp; q < npl / 2; q += IT / 32) {
+                int a, b;
+                inner_rr_pair<CPLX>(npl, step, q, a, b);
+                if (a >= k || b >= k) continue;
+                if (a > b) {
+                    const int t = a;
+                    a = b;
+                    b = t;
+                }
+                double sr = 0.0, si = 0.0;
+                double *ra = R + (int64_t)a * kmax * E, *rb = R + (int64_t)b * kmax * E;
+                for (int l = lane; l < k; l += 32) {
+                    if (CPLX) {
+                        const double xr = ra[2 * l], xi = ra[2 * l + 1];
+                        const double yr = rb[2 * l], yi = rb[2 * l + 1];
+                        sr = fma(xr, yr, fma(xi, yi, sr));
+                        si = fma(xr, yi, fma(-xi, yr, si));
+                    } else {
+                        sr = fma(ra[l], rb[l], sr);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                const double da = dsh[a], db = dsh[b];
+                const double absa = CPLX ? sqrt(sr * sr + si * si) : fabs(sr);
+                const double rel = absa / sqrt(da * db);
+                if (!isfinite(rel)) {
+                    if (lane == 0) atomicOr(&counters[kCntErr], kErrNonfinite);
+                    continue;
+                }
+                maxoff = fmax(maxoff, rel);
+                if (!(rel > tol)) continue;
+                Rot Q;
+                const bool ok = rotation(da, db, sr, si, jsh[a] * jsh[b], CPLX, Q);
+                if (!ok) {
+                    if (lane == 0) atomicOr(&counters[kCntErr], kErrNotPosdef);
+                    continue;
+                }
+                if (lane == 0) {
+                    dsh[a] = Q.dr;
+                    dsh[b] = Q.ds;
+                    atomicAdd(&s_rot, 1);
+                }
+                double *wa = W + (int64_t)a * kmax * E, *wb = W + (int64_t)b * kmax * E;
+                for (int l = lane; l < k; l += 32) {
+                    if (CPLX) {
+                        rot_apply_c(Q, ra[2 * l], ra[2 * l + 1], rb[2 * l], rb[2 * l + 1]);
+                        rot_apply_c(Q, wa[2 * l], wa[2 * l + 1], wb[2 * l], wb[2 * l + 1]);
+                    } else {
+                        rot_apply_r(Q, ra[l], rb[l]);
+                        rot_apply_r(Q, wa[l], wb[l]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        const int rot = s_rot;
+        total_rot += (unsigned long long)rot;
+        __syncthreads();
+        if (rot == 0) break;
+    }
+    // block max of maxoff
+    __shared__ double smax[IT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxoff = fmax(maxoff, __shfl_xor_sync(0xffffffffu, maxoff, o));
+    if (lane == 0) smax[warp] = maxoff;
+    __syncthreads();
+    if (tid == 0) {
+        double mo = 0.0;
+        for (int w = 0; w < IT / 32; ++w) mo = fmax(mo, smax[w]);
+        atomic_max_nonneg(&counters[kCntMaxOff], mo);
+        if (total_rot) atomicAdd(&counters[kCntRot], total_rot);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_t m,
+                        const int32_t *pairs, int npairs, double *A, int kmax,
+                        cudaStream_t st) {
+    (void)gemm;
+    if (npairs <= 0) return cudaSuccess;
+    const int T = (kmax + GT - 1) / GT;
+    dim3 grid(T * (T + 1) / 2, npairs);
+    if (cplx)
+        gram_fp64_kernel<true><<<grid, 256, 0, st>>>(G, ld, m, pairs, A, kmax);
+    else
+        gram_fp64_kernel<false><<<grid, 256, 0, st>>>(G, ld, m, pairs, A, kmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int64_t ld,
+                          int64_t m, const int32_t *pairs, int npairs, const double *W,
+                          int kmax, cudaStream_t st) {
+    (void)gemm;
+    if (npairs <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((m + UR - 1) / UR), (kmax + UC - 1) / UC, npairs);
+    if (cplx)
+        update_fp64_kernel<true><<<grid, 256, 0, st>>>(Gs, Gd, ld, m, pairs, W, kmax);
+    else
+        update_fp64_kernel<false><<<grid, 256, 0, st>>>(Gs, Gd, ld, m, pairs, W, kmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
+                         int npairs, const int8_t *J, double tol, int inner_max_sweeps,
+                         int inner_block, unsigned long long *counters, cudaStream_t st) {
+    (void)inner_block;
+    if (npairs <= 0) return cudaSuccess;
+    const size_t sh = (size_t)kmax * sizeof(double) + (size_t)kmax * sizeof(int);
+    if (cplx)
+        inner_kernel<true><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters);
+    else
+        inner_kernel<false><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters);
+    return cudaGetLastError();
+}
+
+}  // namespace jj

@@ -1,0 +1,130 @@
+// Internal declarations shared by the CUDA translation units of libjjacobi.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/jjacobi.h"
+#include "../../include/jjacobi_kernels.h"
+
+namespace jj {
+
+// Error flags accumulated on the device (counters[2]).
+constexpr unsigned long long kErrNotPosdef = 1ull;
+constexpr unsigned long long kErrNonfinite = 2ull;
+constexpr unsigned long long kErrTimeout = 4ull;
+
+// 128 * 2^-53: the convergence threshold of the published workloads.
+constexpr double kDefaultTol = 128.0 * 1.1102230246251565404e-16;
+
+// Counter slots.
+enum { kCntRot = 0, kCntMaxOff = 1, kCntErr = 2 };
+
+// Parameters of one J-unitary rotation on a column pair (g_r, g_s), in the form
+//   g_r' = ce * g_r - hs * g_s,   g_s' = se * g_r + c * g_s
+// with ce = c e^{i alpha}, se = s e^{i alpha}, hs = hyp * s (Alg. 3.1, (2.3)).
+struct Rot {
+    double ce_re, ce_im, se_re, se_im, c, hs;
+    double dr, ds;  // updated diagonal a_rr', a_ss'
+};
+
+// Rotation of Alg. 3.1 for the pivot (a_rr, a_ss, a_rs), hyp = J_rr J_ss.
+//   eta = sgn(Re a_rs) |a_rs|, e^{i alpha} = a_rs / eta (real: eta = a_rs);
+//   theta = hyp (a_ss - hyp a_rr) / (2 eta);
+//   t = sgn(theta) / (|theta| + sqrt(theta^2 + hyp)), or 1/(2 theta) when
+//   |theta| > 1e150; c = 1/sqrt(1 + hyp t^2), s = c t;
+//   a_rr' = a_rr - hyp t eta, a_ss' = a_ss + t eta.
+// hyp = +J_rr J_ss is the reading of the printed sign that keeps W_P
+// J-unitary; sgn(0) = +1. Returns false when the hyperbolic case has
+// theta^2 < 1 (the pair is not positive definite in working precision).
+__device__ __forceinline__ bool rotation(double arr, double ass, double are, double aim,
+                                         int hyp, bool cplx, Rot &o) {
+    const double absa = cplx ? sqrt(are * are + aim * aim) : fabs(are);
+    const double eta = are >= 0.0 ? absa : -absa;
+    double er = 1.0, ei = 0.0;
+    if (cplx) {
+        const double inv = 1.0 / eta;
+        er = are * inv;
+        ei = aim * inv;
+    }
+    const double h = (double)hyp;
+    const double theta = h * (ass - h * arr) / (2.0 * eta);
+    const double at = fabs(theta);
+    double t;
+    if (at > 1e150) {
+        t = 0.5 / theta;
+    } else {
+        const double rad = theta * theta + h;
+        if (!(rad >= 0.0)) return false;
+        t = 1.0 / (at + sqrt(rad));
+        if (theta < 0.0) t = -t;
+    }
+    const double q = 1.0 + h * t * t;
+    if (!(q > 0.0)) return false;
+    const double c = 1.0 / sqrt(q);
+    const double s = c * t;
+    o.c = c;
+    o.hs = h * s;
+    o.ce_re = c * er;
+    o.ce_im = c * ei;
+    o.se_re = s * er;
+    o.se_im = s * ei;
+    o.dr = arr - h * t * eta;
+    o.ds = ass + t * eta;
+    return true;
+}
+
+// Apply a rotation to one row entry of a complex column pair.
+__device__ __forceinline__ void rot_apply_c(const Rot &R, double &xr, double &xi, double &yr,
+                                            double &yi) {
+    const double nxr = fma(R.ce_re, xr, fma(-R.ce_im, xi, -R.hs * yr));
+    const double nxi = fma(R.ce_re, xi, fma(R.ce_im, xr, -R.hs * yi));
+    const double nyr = fma(R.se_re, xr, fma(-R.se_im, xi, R.c * yr));
+    const double nyi = fma(R.se_re, xi, fma(R.se_im, xr, R.c * yi));
+    xr = nxr;
+    xi = nxi;
+    yr = nyr;
+    yi = nyi;
+}
+
+__device__ __forceinline__ void rot_apply_r(const Rot &R, double &x, double &y) {
+    const double nx = fma(R.ce_re, x, -R.hs * y);
+    const double ny = fma(R.se_re, x, R.c * y);
+    x = nx;
+    y = ny;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v) {
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (host functions, defined in the .cu files)
+// ---------------------------------------------------------------------------
+cudaError_t launch_column_norms(bool cplx, const double *G, int64_t ld, int64_t m, int64_t n,
+                                double *d, cudaStream_t st);
+cudaError_t launch_plain_step(bool cplx, double *G, int64_t ld, int64_t m, int64_t n,
+                              const int32_t *pairs, int npairs, const int8_t *J, double *d,
+                              double tol, unsigned long long *counters, cudaStream_t st);
+cudaError_t launch_extract(bool cplx, const double *G, int64_t ld, int64_t m, int64_t n,
+                           const int8_t *J, const int32_t *perm, double *lambda, double *U,
+                           int64_t ldu, cudaStream_t st);
+// Gw[:, c] = G[:, src[c]] (gather) or G[:, src[c]] = Gw[:, c] (scatter).
+cudaError_t launch_permute_columns(bool cplx, const double *A, int64_t lda, double *B,
+                                   int64_t ldb, int64_t m, int64_t n, const int32_t *perm,
+                                   bool scatter, cudaStream_t st);
+
+cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_t m,
+                        const int32_t *pairs, int npairs, double *A, int kmax,
+                        cudaStream_t st);
+cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
+                         int npairs, const int8_t *J, double tol, int inner_max_sweeps,
+                         int inner_block, unsigned long long *counters, cudaStream_t st);
+cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int64_t ld,
+                          int64_t m, const int32_t *pairs, int npairs, const double *W,
+                          int kmax, cudaStream_t st);
+
+// Host-side ordering tables (jj_schedule.cpp).
+int schedule_pairs(int nbl, int order, int sweep, int32_t *pairs);
+
+}  // namespace jj

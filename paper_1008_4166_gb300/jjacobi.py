@@ -1,0 +1,257 @@
+"""Python binding of libjjacobi (ctypes): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module never
+computes. PyTorch tensors are accepted for device memory and streams. If the
+shared library is missing it raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libjjacobi.so")
+
+JJ_F64, JJ_C128 = 0, 1
+JJ_ORDER_ROUND_ROBIN, JJ_ORDER_MODULUS = 0, 1
+JJ_GEMM_FP64, JJ_GEMM_OZAKI_FP16, JJ_GEMM_AUTO = 0, 1, 3
+(JJ_OK, JJ_INVALID_ARG, JJ_NOT_CONVERGED, JJ_NOT_POSDEF, JJ_NONFINITE, JJ_DEVICE_TIMEOUT,
+ JJ_CUDA_ERROR, JJ_NOT_SOLVED) = range(8)
+
+# Every symbol the C headers declare (include/jjacobi.h, include/jjacobi_kernels.h).
+EXPORTS = [
+    "jjacobi_default_params", "jjacobi_create", "jjacobi_solve", "jjacobi_extract",
+    "jjacobi_solve_host", "jjacobi_solve_batched", "jjacobi_destroy",
+    "jjacobi_status_string", "jjacobi_version", "jjacobi_schedule",
+    "jjk_column_norms", "jjk_plain_step", "jjk_gram", "jjk_inner", "jjk_update", "jjk_extract",
+]
+
+
+class jj_params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("block_width", ctypes.c_int32), ("inner_block_width", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("gemm", ctypes.c_int32),
+                ("ozaki_slices", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("max_sweeps", ctypes.c_int32), ("inner_max_sweeps", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class jj_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("rotations", ctypes.c_int64), ("last_max_offdiag", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("block_width", ctypes.c_int32),
+                ("nbl", ctypes.c_int32), ("steps_per_sweep", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class JJError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libjjacobi.so (built by __graft_entry__.build() / _build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libjjacobi.so not found at {p}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "jjacobi_default_params": (None, [P(jj_params), i64, i64, i32]),
+        "jjacobi_create": (ctypes.c_int, [P(ctypes.c_void_p), P(jj_params)]),
+        "jjacobi_solve": (ctypes.c_int, [vp, vp, i64, vp, P(jj_info)]),
+        "jjacobi_extract": (ctypes.c_int, [vp, vp, vp, i64, i32]),
+        "jjacobi_solve_host": (ctypes.c_int, [vp, vp, i64, vp, vp, vp, i64, P(jj_info)]),
+        "jjacobi_solve_batched": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "jjacobi_destroy": (None, [vp]),
+        "jjacobi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "jjacobi_version": (i32, []),
+        "jjacobi_schedule": (i32, [i32, i32, i32, vp]),
+        "jjk_column_norms": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, vp]),
+        "jjk_plain_step": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, i32, vp, vp, dbl, vp, vp]),
+        "jjk_gram": (ctypes.c_int, [i32, i32, vp, i64, i64, vp, i32, vp, i32, vp]),
+        "jjk_inner": (ctypes.c_int, [i32, vp, vp, i32, vp, i32, vp, dbl, i32, i32, vp, vp]),
+        "jjk_update": (ctypes.c_int, [i32, i32, vp, vp, i64, i64, vp, i32, vp, i32, vp]),
+        "jjk_extract": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, vp, vp, i64, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().jjacobi_status_string(int(status)).decode()
+
+
+def _check(rc: int, where: str, ok=(JJ_OK,)):
+    if rc not in ok:
+        raise JJError(rc, where)
+    return rc
+
+
+def _ptr(x) -> Optional[int]:
+    """Raw address of a torch tensor, a numpy array or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover - torch is plumbing only
+            return None
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def jjacobi_schedule(nbl: int, order: int, sweep: int = 1) -> np.ndarray:
+    """Block pairs of one sweep, [steps, nbl/2, 2] (Algs. 4.1-4.3, host)."""
+    lib = load()
+    buf = np.zeros(2 * nbl * (nbl // 2) + 2, dtype=np.int32)
+    steps = lib.jjacobi_schedule(int(nbl), int(order), int(sweep), buf.ctypes.data)
+    if steps < 0:
+        raise JJError(JJ_INVALID_ARG, "jjacobi_schedule")
+    return buf[: steps * nbl].reshape(steps, nbl // 2, 2).copy()
+
+
+def jjacobi_default_params(m: int, n: int, dtype: int) -> jj_params:
+    p = jj_params()
+    load().jjacobi_default_params(ctypes.byref(p), int(m), int(n), int(dtype))
+    return p
+
+
+class Handle:
+    """Owning wrapper of a jj_handle (jjacobi_create / jjacobi_destroy)."""
+
+    def __init__(self, m: int, n: int, dtype: int, block_width: int = 0,
+                 inner_block_width: int = 0, order: int = JJ_ORDER_ROUND_ROBIN,
+                 gemm: int = JJ_GEMM_FP64, tol: float = 0.0, max_sweeps: int = 0,
+                 inner_max_sweeps: int = 0, ozaki_slices: int = 0, stream=None):
+        lib = load()
+        p = jjacobi_default_params(m, n, dtype)
+        p.block_width = block_width
+        p.inner_block_width = inner_block_width
+        p.order = order
+        p.gemm = gemm
+        p.ozaki_slices = ozaki_slices
+        if tol > 0:
+            p.tol = tol
+        if max_sweeps > 0:
+            p.max_sweeps = max_sweeps
+        if inner_max_sweeps > 0:
+            p.inner_max_sweeps = inner_max_sweeps
+        sp = _stream_ptr(stream)
+        p.cuda_stream = sp
+        self.params = p
+        self.h = ctypes.c_void_p()
+        _check(lib.jjacobi_create(ctypes.byref(self.h), ctypes.byref(p)), "jjacobi_create")
+        self.m, self.n, self.dtype = m, n, dtype
+
+    def close(self):
+        if self.h:
+            load().jjacobi_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def jjacobi_solve(self, G, ldg: int, J: Sequence[int], allow=(JJ_OK,)) -> jj_info:
+        Jc = np.ascontiguousarray(np.asarray(J, dtype=np.int8))
+        info = jj_info()
+        rc = load().jjacobi_solve(self.h, _ptr(G), int(ldg), Jc.ctypes.data, ctypes.byref(info))
+        _check(rc, "jjacobi_solve", allow)
+        return info
+
+    def jjacobi_extract(self, lam, U=None, ldu: int = 0, sort: int = 0) -> None:
+        _check(load().jjacobi_extract(self.h, _ptr(lam), _ptr(U), int(ldu), int(sort)),
+               "jjacobi_extract")
+
+    def jjacobi_solve_host(self, G: np.ndarray, J: Sequence[int], want_U: bool = False,
+                           allow=(JJ_OK,)):
+        """Host buffers in and out (column-major numpy array G)."""
+        Gf = np.asfortranarray(G)
+        Jc = np.ascontiguousarray(np.asarray(J, dtype=np.int8))
+        lam = np.zeros(self.n, dtype=np.float64)
+        U = np.zeros_like(Gf, order="F") if want_U else None
+        info = jj_info()
+        rc = load().jjacobi_solve_host(self.h, Gf.ctypes.data, Gf.shape[0], Jc.ctypes.data,
+                                       lam.ctypes.data, _ptr(U), Gf.shape[0] if want_U else 0,
+                                       ctypes.byref(info))
+        _check(rc, "jjacobi_solve_host", allow)
+        return lam, U, info
+
+
+# ---------------------------------------------------------------------------
+# Building blocks (include/jjacobi_kernels.h)
+# ---------------------------------------------------------------------------
+
+def jjk_column_norms(dtype, G, ld, m, n, d, stream=None):
+    _check(load().jjk_column_norms(dtype, _ptr(G), ld, m, n, _ptr(d), _stream_ptr(stream)),
+           "jjk_column_norms")
+
+
+def jjk_plain_step(dtype, G, ld, m, n, pairs, npairs, J, d, tol, counters, stream=None):
+    _check(load().jjk_plain_step(dtype, _ptr(G), ld, m, n, _ptr(pairs), npairs, _ptr(J), _ptr(d),
+                                 float(tol), _ptr(counters), _stream_ptr(stream)),
+           "jjk_plain_step")
+
+
+def jjk_gram(dtype, gemm, G, ld, m, pairs, npairs, A, kmax, stream=None):
+    _check(load().jjk_gram(dtype, gemm, _ptr(G), ld, m, _ptr(pairs), npairs, _ptr(A), kmax,
+                           _stream_ptr(stream)), "jjk_gram")
+
+
+def jjk_inner(dtype, A, W, kmax, pairs, npairs, J, tol, inner_max_sweeps, inner_block_width,
+              counters, stream=None):
+    _check(load().jjk_inner(dtype, _ptr(A), _ptr(W), kmax, _ptr(pairs), npairs, _ptr(J),
+                            float(tol), inner_max_sweeps, inner_block_width, _ptr(counters),
+                            _stream_ptr(stream)), "jjk_inner")
+
+
+def jjk_update(dtype, gemm, Gs, Gd, ld, m, pairs, npairs, W, kmax, stream=None):
+    _check(load().jjk_update(dtype, gemm, _ptr(Gs), _ptr(Gd), ld, m, _ptr(pairs), npairs,
+                             _ptr(W), kmax, _stream_ptr(stream)), "jjk_update")
+
+
+def jjk_extract(dtype, G, ld, m, n, J, lam, U=None, ldu=0, stream=None):
+    _check(load().jjk_extract(dtype, _ptr(G), ld, m, n, _ptr(J), _ptr(lam), _ptr(U), ldu,
+                              _stream_ptr(stream)), "jjk_extract")

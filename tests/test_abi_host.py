@@ -1,0 +1,98 @@
+"""CPU tests of the C ABI: the library builds, loads and exports every symbol
+the headers declare; the host-side logic (ordering tables, parameters, status
+strings, argument validation) works without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def jj():
+    import __graft_entry__ as g
+
+    g.build()
+    from paper_1008_4166_gb300 import jjacobi
+
+    return jjacobi
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return set(re.findall(r"\b(jj[a-z]*_[a-z_]+)\s*\(", txt))
+
+
+def test_every_declared_symbol_is_exported(jj):
+    lib = jj.load()
+    declared = _declared("jjacobi.h") | _declared("jjacobi_kernels.h")
+    assert declared, "no declarations parsed"
+    assert declared == set(jj.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_version_and_status_strings(jj):
+    lib = jj.load()
+    assert lib.jjacobi_version() == 10000
+    for s in range(8):
+        assert jj.status_string(s).startswith("JJ_")
+    assert jj.status_string(99) == "JJ_UNKNOWN"
+
+
+def test_default_params(jj):
+    p = jj.jjacobi_default_params(100, 80, jj.JJ_C128)
+    assert (p.m, p.n, p.dtype, p.block_width) == (100, 80, jj.JJ_C128, 0)
+    assert p.tol == 128 * 2.0 ** -53 and p.max_sweeps == 60 and p.inner_max_sweeps == 30
+
+
+@pytest.mark.parametrize("nbl", [2, 4, 6, 8, 16, 64, 128, 1000])
+@pytest.mark.parametrize("order", [0, 1])
+def test_schedule_matches_oracle(jj, nbl, order):
+    for sweep in (1, 2, 3):
+        got = jj.jjacobi_schedule(nbl, order, sweep)
+        ref = oracle.schedule(nbl, order, sweep)
+        assert got.shape == ref.shape
+        assert np.array_equal(got, ref)
+
+
+def test_schedule_invalid(jj):
+    with pytest.raises(jj.JJError):
+        jj.jjacobi_schedule(5, 0, 1)
+    with pytest.raises(jj.JJError):
+        jj.jjacobi_schedule(4, 2, 1)
+
+
+def test_create_rejects_bad_params(jj):
+    lib = jj.load()
+    h = ctypes.c_void_p()
+    p = jj.jjacobi_default_params(10, 20, jj.JJ_F64)  # m < n
+    assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(p)) == jj.JJ_INVALID_ARG
+    assert not h
+    p = jj.jjacobi_default_params(10, 10, 7)
+    assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(p)) == jj.JJ_INVALID_ARG
+    assert lib.jjacobi_create(None, ctypes.byref(p)) == jj.JJ_INVALID_ARG
+    lib.jjacobi_destroy(None)  # no-op
+
+
+def test_kernel_entry_points_validate_arguments(jj):
+    lib = jj.load()
+    assert lib.jjk_gram(9, 0, None, 1, 1, None, 0, None, 1, None) == jj.JJ_INVALID_ARG
+    assert lib.jjk_extract(0, None, 1, 1, 1, None, None, None, 0, None) == jj.JJ_INVALID_ARG
+    assert lib.jjacobi_extract(None, None, None, 0, 0) == jj.JJ_INVALID_ARG
+
+
+def test_product_does_not_import_oracle():
+    """The product package and its sources never reference the oracle."""
+    pkg = os.path.join(ROOT, "paper_1008_4166_gb300")
+    for dp, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                txt = open(os.path.join(dp, f), errors="replace").read()
+                assert "oracle" not in txt.lower() or f == "__init__.py" and "oracle" not in txt, f
