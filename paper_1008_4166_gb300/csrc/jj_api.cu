@@ -29,6 +29,10 @@ struct jj_ctx {
     double *Gw[2] = {nullptr, nullptr};
     double *Ablk = nullptr, *Wblk = nullptr;
     double *d_norm = nullptr;
+    bool ozaki = false;                 // Gram and update on the tensor cores (fp16 digits)
+    int oz_slices_gram = 9, oz_slices_update = 8;
+    int32_t *d_cexp = nullptr;          // column exponents (Ozaki Gram)
+    unsigned long long *d_ozacc = nullptr;  // int128 Gram accumulators
 
     int32_t *d_perm = nullptr;    // work column -> caller column
     int32_t *d_rank = nullptr;    // extraction with sorting: column -> rank of its lambda
@@ -78,6 +82,8 @@ void free_ctx(jj_ctx *c) {
     cudaFree(c->Gw[1]);
     cudaFree(c->Ablk);
     cudaFree(c->Wblk);
+    cudaFree(c->d_cexp);
+    cudaFree(c->d_ozacc);
     cudaFree(c->d_norm);
     cudaFree(c->d_perm);
     cudaFree(c->d_rank);
@@ -112,14 +118,28 @@ int enqueue_sweep(jj_ctx *c, int start_buf, int *launches) {
         int cur = start_buf;
         for (int t = 0; t < c->steps; ++t) {
             const int32_t *pr = c->d_pairs + (size_t)t * c->npairs * 4;
-            JJ_CUDA(launch_gram(c->cplx, c->p.gemm, c->Gw[cur], c->ldw, c->m, pr, c->npairs,
-                                c->Ablk, c->kmax, st));
+            if (c->ozaki) {
+                JJ_CUDA(launch_colexp(c->cplx, c->Gw[cur], c->ldw, c->m, c->n, c->d_cexp, st));
+                JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw[cur], c->ldw, c->m, pr, c->npairs,
+                                          c->Ablk, c->kmax, c->d_cexp, c->d_ozacc,
+                                          c->oz_slices_gram, c->d_cnt, st));
+                L += 3;
+            } else {
+                JJ_CUDA(launch_gram(c->cplx, c->p.gemm, c->Gw[cur], c->ldw, c->m, pr, c->npairs,
+                                    c->Ablk, c->kmax, st));
+                L += 1;
+            }
             JJ_CUDA(launch_inner(c->cplx, c->Ablk, c->Wblk, c->kmax, pr, c->npairs, c->d_Jw,
                                  c->tol, c->inner_max_sweeps, c->p.inner_block_width, c->d_cnt,
                                  st));
-            JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m,
-                                  pr, c->npairs, c->Wblk, c->kmax, st));
-            L += 3;
+            if (c->ozaki)
+                JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m, pr,
+                                            c->npairs, c->Wblk, c->kmax, c->oz_slices_update,
+                                            c->d_cnt, st));
+            else
+                JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m,
+                                      pr, c->npairs, c->Wblk, c->kmax, st));
+            L += 2;
             cur ^= 1;
         }
     }
@@ -279,6 +299,20 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
         const size_t bb = (size_t)c->npairs * c->kmax * c->kmax * c->E * sizeof(double);
         if (cudaMalloc(&c->Ablk, bb) != cudaSuccess) return fail(JJ_CUDA_ERROR);
         if (cudaMalloc(&c->Wblk, bb) != cudaSuccess) return fail(JJ_CUDA_ERROR);
+        const bool oz_ok = ozaki_supported(c->cplx, c->kmax);
+        if (p->gemm == JJ_GEMM_OZAKI_FP16 && !oz_ok) return fail(JJ_INVALID_ARG);
+        c->ozaki = oz_ok && (p->gemm == JJ_GEMM_OZAKI_FP16 || p->gemm == JJ_GEMM_AUTO);
+        if (c->ozaki) {
+            if (p->ozaki_slices > 0) {
+                if (p->ozaki_slices > 9) return fail(JJ_INVALID_ARG);
+                c->oz_slices_gram = p->ozaki_slices;
+                c->oz_slices_update = p->ozaki_slices < 8 ? p->ozaki_slices : 8;
+            }
+            if (cudaMalloc(&c->d_cexp, n * sizeof(int32_t)) != cudaSuccess ||
+                cudaMalloc(&c->d_ozacc, ozaki_gram_workspace_bytes(c->npairs, c->kmax, c->cplx)) !=
+                    cudaSuccess)
+                return fail(JJ_CUDA_ERROR);
+        }
     } else {
         if (cudaMalloc(&c->d_norm, n * sizeof(double)) != cudaSuccess) return fail(JJ_CUDA_ERROR);
     }
@@ -481,8 +515,36 @@ int jjk_gram(int32_t dtype, int32_t gemm, const void *G, int64_t ld, int64_t m,
              const int32_t *pairs, int32_t npairs, double *A, int32_t kmax, void *stream) {
     if (!dt_ok(dtype) || !G || !pairs || !A || ld < m || m < 1 || kmax < 1 || npairs < 0)
         return JJ_INVALID_ARG;
-    JJ_CUDA(launch_gram(dtype == JJ_C128, gemm, (const double *)G, ld, m, pairs, npairs, A, kmax,
-                        (cudaStream_t)stream));
+    const bool cplx = dtype == JJ_C128;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (gemm == JJ_GEMM_OZAKI_FP16) {
+        if (!ozaki_supported(cplx, kmax)) return JJ_INVALID_ARG;
+        // Scratch from the stream-ordered allocator: column exponents of every
+        // column the pairs touch and the int128 accumulators.
+        int64_t ncols = 0;
+        {
+            std::vector<int32_t> hp((size_t)npairs * 4);
+            JJ_CUDA(cudaMemcpyAsync(hp.data(), pairs, hp.size() * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st));
+            JJ_CUDA(cudaStreamSynchronize(st));
+            for (int q = 0; q < npairs; ++q)
+                ncols = std::max<int64_t>(ncols, std::max(hp[4 * q] + hp[4 * q + 1],
+                                                          hp[4 * q + 2] + hp[4 * q + 3]));
+        }
+        int32_t *cexp = nullptr;
+        unsigned long long *acc = nullptr;
+        JJ_CUDA(cudaMallocAsync((void **)&cexp, std::max<int64_t>(ncols, 1) * sizeof(int32_t), st));
+        JJ_CUDA(cudaMallocAsync((void **)&acc, ozaki_gram_workspace_bytes(npairs, kmax, cplx), st));
+        cudaError_t e = launch_colexp(cplx, (const double *)G, ld, m, ncols, cexp, st);
+        if (e == cudaSuccess)
+            e = launch_gram_ozaki(cplx, (const double *)G, ld, m, pairs, npairs, A, kmax, cexp, acc,
+                                  ozaki_default_slices(true), nullptr, st);
+        cudaFreeAsync(cexp, st);
+        cudaFreeAsync(acc, st);
+        JJ_CUDA(e);
+        return JJ_OK;
+    }
+    JJ_CUDA(launch_gram(cplx, gemm, (const double *)G, ld, m, pairs, npairs, A, kmax, st));
     return JJ_OK;
 }
 
@@ -502,8 +564,16 @@ int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld
                void *stream) {
     if (!dt_ok(dtype) || !Gs || !Gd || !pairs || !W || ld < m || m < 1 || kmax < 1 || npairs < 0)
         return JJ_INVALID_ARG;
-    JJ_CUDA(launch_update(dtype == JJ_C128, gemm, (const double *)Gs, (double *)Gd, ld, m, pairs,
-                          npairs, W, kmax, (cudaStream_t)stream));
+    const bool cplx = dtype == JJ_C128;
+    if (gemm == JJ_GEMM_OZAKI_FP16) {
+        if (!ozaki_supported(cplx, kmax)) return JJ_INVALID_ARG;
+        JJ_CUDA(launch_update_ozaki(cplx, (const double *)Gs, (double *)Gd, ld, m, pairs, npairs, W,
+                                    kmax, ozaki_default_slices(false), nullptr,
+                                    (cudaStream_t)stream));
+        return JJ_OK;
+    }
+    JJ_CUDA(launch_update(cplx, gemm, (const double *)Gs, (double *)Gd, ld, m, pairs, npairs, W,
+                          kmax, (cudaStream_t)stream));
     return JJ_OK;
 }
 

@@ -406,6 +406,268 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
     }
 }
 
+// ---------------------------------------------------------------------------
+// Inner solve with R and W resident in shared memory (pivot order k <= KMAX).
+// Cholesky (right-looking, upper) in place, then one-sided J-Jacobi sweeps in
+// the standard round-robin parallel order: each warp owns one column pair of
+// an inner step (lane l holds rows l, l+32, ...), forms the dot product with
+// shuffles, lane 0 computes the rotation (Alg. 3.1) and the warp rotates the R
+// and W columns. A block barrier separates inner steps.
+// ---------------------------------------------------------------------------
+constexpr int ST = 512;  // threads per block
+constexpr int SW = ST / 32;
+
+template <bool CPLX, int ROWS>
+__global__ void __launch_bounds__(ST) inner_smem_kernel(
+    double *__restrict__ A, double *__restrict__ Wb, int kmax, const int32_t *__restrict__ pairs,
+    const int8_t *__restrict__ J, double tol, int max_sweeps,
+    unsigned long long *__restrict__ counters) {
+    constexpr int E = CPLX ? 2 : 1;
+    extern __shared__ double2 smem4[];
+    double *sm = reinterpret_cast<double *>(smem4);
+    const int32_t *pd = pairs + 4 * blockIdx.x;
+    const int k = pd[1] + pd[3];
+    const int ldr = k;  // smem leading dimension (entries)
+    double *R = sm;                              // k x k entries
+    double *W = R + (size_t)k * ldr * E;         // k x k entries
+    double *dsh = W + (size_t)k * ldr * E;       // k
+    double *qsh = dsh + k;                       // SW x 8 rotation broadcast
+    int *jsh = reinterpret_cast<int *>(qsh + SW * 8);
+    __shared__ int s_rot, s_fail;
+    __shared__ double s_piv;
+    __shared__ double s_max[SW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double *Ag = A + (int64_t)blockIdx.x * kmax * kmax * E;
+    for (int a = tid; a < k; a += ST) jsh[a] = J[pivot_col(pd, a)];
+    // load the upper triangle of A_P, zero below
+    for (int t = tid; t < k * k; t += ST) {
+        const int a = t % k, b = t / k;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            R[((size_t)b * ldr + a) * E + e] = a <= b ? Ag[((int64_t)b * kmax + a) * E + e] : 0.0;
+    }
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    // Cholesky A = R^* R (upper), right-looking
+    for (int j = 0; j < k; ++j) {
+        if (tid == 0) {
+            const double ajj = R[((size_t)j * ldr + j) * E];
+            if (!(ajj > 0.0) || !isfinite(ajj)) {
+                s_fail = 1;
+                s_piv = 1.0;
+            } else {
+                s_piv = sqrt(ajj);
+            }
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const double rjj = s_piv, inv = 1.0 / rjj;
+        for (int l = j + 1 + tid; l < k; l += ST) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) R[((size_t)l * ldr + j) * E + e] *= inv;
+        }
+        if (tid == 0) {
+            R[((size_t)j * ldr + j) * E] = rjj;
+            if (CPLX) R[((size_t)j * ldr + j) * E + 1] = 0.0;
+        }
+        __syncthreads();
+        const int rem = k - j - 1;
+        // trailing update: column c2 of the remaining block handled by threads
+        for (int t = tid; t < rem * rem; t += ST) {
+            const int c1 = j + 1 + t % rem, c2 = j + 1 + t / rem;
+            if (c1 > c2) continue;
+            if (CPLX) {
+                const double ur = R[((size_t)c1 * ldr + j) * 2], ui = R[((size_t)c1 * ldr + j) * 2 + 1];
+                const double vr = R[((size_t)c2 * ldr + j) * 2], vi = R[((size_t)c2 * ldr + j) * 2 + 1];
+                double *dst = R + ((size_t)c2 * ldr + c1) * 2;
+                dst[0] -= fma(ur, vr, ui * vi);
+                dst[1] -= fma(ur, vi, -ui * vr);
+            } else {
+                R[(size_t)c2 * ldr + c1] -= R[(size_t)c1 * ldr + j] * R[(size_t)c2 * ldr + j];
+            }
+        }
+        __syncthreads();
+    }
+    double *Rg = A + (int64_t)blockIdx.x * kmax * kmax * E;
+    double *Wg = Wb + (int64_t)blockIdx.x * kmax * kmax * E;
+    if (s_fail) {
+        if (tid == 0) atomicOr(&counters[kCntErr], kErrNotPosdef);
+        for (int t = tid; t < k * k; t += ST) {
+            const int a = t % k, b = t / k;
+            Wg[((int64_t)b * kmax + a) * E] = a == b ? 1.0 : 0.0;
+            if (CPLX) Wg[((int64_t)b * kmax + a) * E + 1] = 0.0;
+        }
+        return;
+    }
+    // zero the strictly lower triangle of R (left over from the upper loads), W = I
+    for (int t = tid; t < k * k; t += ST) {
+        const int a = t % k, b = t / k;
+        if (a > b) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) R[((size_t)b * ldr + a) * E + e] = 0.0;
+        }
+        W[((size_t)b * ldr + a) * E] = a == b ? 1.0 : 0.0;
+        if (CPLX) W[((size_t)b * ldr + a) * E + 1] = 0.0;
+    }
+    __syncthreads();
+    const int npl = k + (k & 1);
+    unsigned long long total_rot = 0;
+    double maxoff = 0.0;
+    double *q = qsh + warp * 8;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        for (int c = warp; c < k; c += SW) {
+            double acc = 0.0;
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                const int l = lane + 32 * i;
+                if (l < k) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const double v = R[((size_t)c * ldr + l) * E + e];
+                        acc = fma(v, v, acc);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) dsh[c] = acc;
+        }
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        maxoff = 0.0;
+        int my_rot = 0;
+        for (int step = 0; step < npl - 1; ++step) {
+            for (int qi = warp; qi < npl / 2; qi += SW) {
+                int a, b;
+                const int P = npl - 1;
+                if (qi == 0) {
+                    a = P;
+                    b = step;
+                } else {
+                    a = (step + qi) % P;
+                    b = (step - qi + P) % P;
+                }
+                if (a >= k || b >= k) continue;
+                if (a > b) {
+                    const int t = a;
+                    a = b;
+                    b = t;
+                }
+                double xr[ROWS], xi[ROWS], yr[ROWS], yi[ROWS];
+                double sr = 0.0, si = 0.0;
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i) {
+                    const int l = lane + 32 * i;
+                    if (l < k) {
+                        if (CPLX) {
+                            const double2 u = *reinterpret_cast<const double2 *>(R + ((size_t)a * ldr + l) * 2);
+                            const double2 v = *reinterpret_cast<const double2 *>(R + ((size_t)b * ldr + l) * 2);
+                            xr[i] = u.x; xi[i] = u.y; yr[i] = v.x; yi[i] = v.y;
+                            sr = fma(xr[i], yr[i], fma(xi[i], yi[i], sr));
+                            si = fma(xr[i], yi[i], fma(-xi[i], yr[i], si));
+                        } else {
+                            xr[i] = R[(size_t)a * ldr + l];
+                            yr[i] = R[(size_t)b * ldr + l];
+                            sr = fma(xr[i], yr[i], sr);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                    if (CPLX) si += __shfl_xor_sync(0xffffffffu, si, o);
+                }
+                if (lane == 0) {
+                    const double da = dsh[a], db = dsh[b];
+                    const double absa = CPLX ? sqrt(sr * sr + si * si) : fabs(sr);
+                    const double rel = absa / sqrt(da * db);
+                    double flag = 0.0;
+                    if (!isfinite(rel)) {
+                        atomicOr(&counters[kCntErr], kErrNonfinite);
+                    } else {
+                        maxoff = fmax(maxoff, rel);
+                        if (rel > tol) {
+                            Rot Q;
+                            if (rotation(da, db, sr, si, jsh[a] * jsh[b], CPLX, Q)) {
+                                q[0] = Q.ce_re; q[1] = Q.ce_im; q[2] = Q.se_re; q[3] = Q.se_im;
+                                q[4] = Q.c; q[5] = Q.hs;
+                                dsh[a] = Q.dr;
+                                dsh[b] = Q.ds;
+                                flag = 1.0;
+                                ++my_rot;
+                            } else {
+                                atomicOr(&counters[kCntErr], kErrNotPosdef);
+                            }
+                        }
+                    }
+                    q[6] = flag;
+                }
+                __syncwarp();
+                if (q[6] == 0.0) {
+                    __syncwarp();
+                    continue;
+                }
+                Rot Q;
+                Q.ce_re = q[0]; Q.ce_im = q[1]; Q.se_re = q[2]; Q.se_im = q[3]; Q.c = q[4]; Q.hs = q[5];
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < ROWS; ++i) {
+                    const int l = lane + 32 * i;
+                    if (l < k) {
+                        if (CPLX) {
+                            rot_apply_c(Q, xr[i], xi[i], yr[i], yi[i]);
+                            *reinterpret_cast<double2 *>(R + ((size_t)a * ldr + l) * 2) = make_double2(xr[i], xi[i]);
+                            *reinterpret_cast<double2 *>(R + ((size_t)b * ldr + l) * 2) = make_double2(yr[i], yi[i]);
+                            double2 u = *reinterpret_cast<const double2 *>(W + ((size_t)a * ldr + l) * 2);
+                            double2 v = *reinterpret_cast<const double2 *>(W + ((size_t)b * ldr + l) * 2);
+                            rot_apply_c(Q, u.x, u.y, v.x, v.y);
+                            *reinterpret_cast<double2 *>(W + ((size_t)a * ldr + l) * 2) = u;
+                            *reinterpret_cast<double2 *>(W + ((size_t)b * ldr + l) * 2) = v;
+                        } else {
+                            rot_apply_r(Q, xr[i], yr[i]);
+                            R[(size_t)a * ldr + l] = xr[i];
+                            R[(size_t)b * ldr + l] = yr[i];
+                            double u = W[(size_t)a * ldr + l], v = W[(size_t)b * ldr + l];
+                            rot_apply_r(Q, u, v);
+                            W[(size_t)a * ldr + l] = u;
+                            W[(size_t)b * ldr + l] = v;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (lane == 0 && my_rot) atomicAdd(&s_rot, my_rot);
+        __syncthreads();
+        const int rot = s_rot;
+        total_rot += (unsigned long long)rot;
+        __syncthreads();
+        if (rot == 0) break;
+    }
+    // write back R~ and W
+    for (int t = tid; t < k * k; t += ST) {
+        const int a = t % k, b = t / k;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            Rg[((int64_t)b * kmax + a) * E + e] = R[((size_t)b * ldr + a) * E + e];
+            Wg[((int64_t)b * kmax + a) * E + e] = W[((size_t)b * ldr + a) * E + e];
+        }
+    }
+    if (lane == 0) s_max[warp] = maxoff;
+    __syncthreads();
+    if (tid == 0) {
+        double mo = 0.0;
+        for (int w = 0; w < SW; ++w) mo = fmax(mo, s_max[w]);
+        atomic_max_nonneg(&counters[kCntMaxOff], mo);
+        if (total_rot) atomicAdd(&counters[kCntRot], total_rot);
+    }
+}
+
+size_t inner_smem_bytes(bool cplx, int kmax) {
+    const int E = cplx ? 2 : 1;
+    return sizeof(double) * ((size_t)2 * kmax * kmax * E + kmax + SW * 8) + sizeof(int) * kmax + 64;
+}
+
 }  // namespace
 
 cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_t m,
@@ -440,6 +702,31 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
                          int inner_block, unsigned long long *counters, cudaStream_t st) {
     (void)inner_block;
     if (npairs <= 0) return cudaSuccess;
+    // Shared-memory resident form when R and W fit (227 KB per block).
+    const size_t smb = inner_smem_bytes(cplx, kmax);
+    if (smb <= 227 * 1024 && kmax <= 128) {
+#define JJ_INNER_SMEM(C, RW)                                                                  \
+    do {                                                                                      \
+        auto kern = inner_smem_kernel<C, RW>;                                                 \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smb);                                       \
+        if (e != cudaSuccess) return e;                                                       \
+        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters); \
+        return cudaGetLastError();                                                            \
+    } while (0)
+        const int rows = (kmax + 31) / 32;
+        if (cplx) {
+            if (rows <= 1) JJ_INNER_SMEM(true, 1);
+            if (rows <= 2) JJ_INNER_SMEM(true, 2);
+            if (rows <= 3) JJ_INNER_SMEM(true, 3);
+        } else {
+            if (rows <= 1) JJ_INNER_SMEM(false, 1);
+            if (rows <= 2) JJ_INNER_SMEM(false, 2);
+            if (rows <= 3) JJ_INNER_SMEM(false, 3);
+            if (rows <= 4) JJ_INNER_SMEM(false, 4);
+        }
+#undef JJ_INNER_SMEM
+    }
     const size_t sh = (size_t)kmax * sizeof(double) + (size_t)kmax * sizeof(int);
     if (cplx)
         inner_kernel<true><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters);

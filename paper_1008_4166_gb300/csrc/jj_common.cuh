@@ -124,6 +124,20 @@ cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int
                           int64_t m, const int32_t *pairs, int npairs, const double *W,
                           int kmax, cudaStream_t st);
 
+// Split-precision (fp16 digit) forms on the tensor cores (jj_ozaki.cu).
+int ozaki_default_slices(bool gram);
+bool ozaki_supported(bool cplx, int kmax);
+size_t ozaki_gram_workspace_bytes(int npairs, int kmax, bool cplx);
+cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int64_t n,
+                          int32_t *cexp, cudaStream_t st);
+cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
+                              const int32_t *pairs, int npairs, double *A, int kmax,
+                              const int32_t *cexp, unsigned long long *acc, int slices,
+                              unsigned long long *counters, cudaStream_t st);
+cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
+                                const int32_t *pairs, int npairs, const double *W, int kmax,
+                                int slices, unsigned long long *counters, cudaStream_t st);
+
 // Host-side ordering tables (jj_schedule.cpp).
 int schedule_pairs(int nbl, int order, int sweep, int32_t *pairs);
 

@@ -1,0 +1,746 @@
+// Split-precision (Ozaki scheme I) Gram and update on the tcgen05 tensor cores.
+//
+// Both dense contractions of the blocked method -- the pivot Gram
+// A_P = [G_i G_j]^* [G_i G_j] (3.6) and the update [G_i G_j] W_P (2.9) -- run as
+// sums of exact fp16 x fp16 -> fp32 products on the tensor cores:
+//
+//   * Real form. A complex pivot X = Xr + i Xi (m x k) is handled as the real
+//     m x 2k matrix [Xr Xi]; its Gram C = [Xr Xi]^T [Xr Xi] gives
+//     Re A = C11 + C22, Im A = C12 - C21, and the update is
+//     [Yr Yi] = [Xr Xi] [[Wr, Wi], [-Wi, Wr]].
+//   * Splitting (error-free slicing of Ozaki, Ogita, Oishi and Rump, 2012, in
+//     the fixed-point form used for tensor cores by Mukunoki, Ozaki, Ogita and
+//     Imamura, 2020): every FP64 entry x of a vector with common exponent e
+//     (all |x| < 2^e) is written as x = 2^e sum_{t=1..s} 2^{-7t} d_t + r with
+//     integer digits |d_t| <= 127 and 0 <= |r| < 2^{e - 7s}. The digits are
+//     taken from the bits of x with integer shifts only (no FP64 arithmetic)
+//     and stored as fp16, which holds them exactly.
+//   * Products of digit matrices A_t^T B_u are exact integers; all products of
+//     one diagonal d = t + u (same weight 2^{-7d}) accumulate in one fp32 TMEM
+//     accumulator, exactly, as long as (#products) * K * 127^2 < 2^24.
+//   * Each diagonal's fp32 sum is converted to an integer and added, shifted
+//     by its weight, into integer fixed-point accumulators: int128 for the Gram
+//     (every product kept exactly; the Gram must resolve off-diagonals far
+//     below its largest entries), int64 for the update. One FP64 conversion
+//     and one scaling per output entry end the computation.
+//
+// Shared-memory operands use the canonical K-major SWIZZLE_128B layout:
+// 128-byte rows (64 fp16 along K), 8-row groups 1024 bytes apart, the 16-byte
+// chunks of row r XOR-ed with r mod 8. They are written by the producer
+// threads (the digits are computed, not copied), then fenced to the async
+// proxy before the single issuing thread launches tcgen05.mma.
+#include <cuda_fp16.h>
+
+#include "jj_common.cuh"
+
+namespace jj {
+
+constexpr int kBeta = 7;          // bits per digit
+constexpr int kOzMaxSlices = 9;   // 63 bits
+constexpr int kOzMaxK2 = 64;      // real width 2k (complex) or k (real) handled here
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);  // start address
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused, swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 8-row groups
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
+    return d;
+}
+
+__device__ __forceinline__ uint32_t sw128_off(int row, int kbyte) {
+    return (uint32_t)(row * 128 + ((((kbyte >> 4) ^ (row & 7))) << 4) + (kbyte & 15));
+}
+
+// fp16 x fp16 -> fp32, K-major A and B, dense.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+
+// Bounded wait on an mbarrier phase; false when the limit is reached.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long i = 0; i < (1L << 28); ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst_smem),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
+}
+
+// 32 lanes x 8 consecutive 32-bit columns (one lane per thread of the warp).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Digits
+// ---------------------------------------------------------------------------
+// Exponent e with |x| < 2^e for the magnitude bit pattern `mag` (a non-negative
+// double's bits); zero and subnormals give the smallest normal exponent.
+__device__ __forceinline__ int exp_of_bits(unsigned long long mag) {
+    const int E = (int)((mag >> 52) & 0x7FF);
+    return E == 0 ? -1021 : E - 1022;
+}
+
+// q = floor(|x| 2^(63-e)) for |x| < 2^e, by shifting the 53-bit significand.
+__device__ __forceinline__ unsigned long long fixed63(double x, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return 0ull;  // zero / subnormal: below every digit kept here
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E - 1012 - e;  // <= 10 because |x| < 2^e
+    if (sh >= 0) return mant << sh;
+    if (sh <= -64) return 0ull;
+    return mant >> (-sh);
+}
+
+// Digit t (1-based) of the fixed-point value, with the sign of x.
+__device__ __forceinline__ __half digit(unsigned long long q, bool neg, int t) {
+    const int d = (int)((q >> (63 - kBeta * t)) & 127ull);
+    return __int2half_rn(neg ? -d : d);
+}
+
+// ---------------------------------------------------------------------------
+// Column exponents of the work matrix: e_c with max_l max(|Re|, |Im|) < 2^e_c.
+// ---------------------------------------------------------------------------
+template <bool CPLX>
+__global__ void __launch_bounds__(256) colexp_kernel(const double *__restrict__ G, int64_t ld,
+                                                      int64_t m, int32_t *__restrict__ cexp) {
+    __shared__ unsigned long long sh[8];
+    const int64_t c = blockIdx.x;
+    unsigned long long mx = 0;
+    const double *g = G + c * ld * (CPLX ? 2 : 1);
+    const int64_t cnt = m * (CPLX ? 2 : 1);
+    for (int64_t i = threadIdx.x; i < cnt; i += 256) {
+        const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(g[i]));
+        mx = v > mx ? v : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) mx = sh[w] > mx ? sh[w] : mx;
+        cexp[c] = exp_of_bits(mx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gram: one block per (chunk group of rows, pair). The pivot's K2 real columns
+// are the 64 rows of the A operand (M = 64) and, the Gram being X^T X, the N
+// rows of the same shared-memory tile serve as the B operand. Rows of G are
+// taken 64 at a time (K = 64 per chunk); every diagonal group of digit
+// products is accumulated in a TMEM buffer (two buffers: the tensor cores fill
+// one while the block drains the other) and added into int128 accumulators.
+// At the end each block adds its int128 partial sums atomically into the
+// global accumulator (lo, hi words with an explicit carry).
+// ---------------------------------------------------------------------------
+constexpr int GZ_THREADS = 256;
+constexpr int GZ_KC = 64;                 // rows of G per chunk (K of one MMA group)
+constexpr int GZ_SLICE_BYTES = 64 * 128;  // 64 operand rows x 128 bytes
+
+struct Acc128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+__device__ __forceinline__ void add128_shifted(Acc128 &a, long long v, int sh) {
+    // a += v * 2^sh, 0 <= sh < 127, |v| < 2^40
+    unsigned long long lo_add;
+    long long hi_add;
+    if (sh == 0) {
+        lo_add = (unsigned long long)v;
+        hi_add = v >> 63;
+    } else if (sh < 64) {
+        lo_add = (unsigned long long)v << sh;
+        hi_add = v >> (64 - sh);
+    } else {
+        lo_add = 0ull;
+        hi_add = v << (sh - 64);
+    }
+    const unsigned long long lo = a.lo + lo_add;
+    a.hi += hi_add + (lo < lo_add ? 1 : 0);
+    a.lo = lo;
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
+    const double *__restrict__ G, int64_t ld, int64_t m, const int32_t *__restrict__ pairs,
+    const int32_t *__restrict__ cexp, unsigned long long *__restrict__ acc_out, int k2max,
+    int slices, int rows_per_block, unsigned long long *__restrict__ counters) {
+    extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) unsigned long long bar_full[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int sexp[kOzMaxK2];
+    __shared__ int8_t grp_t[kOzMaxSlices * kOzMaxSlices], grp_u[kOzMaxSlices * kOzMaxSlices];
+    __shared__ int grp_start[2 * kOzMaxSlices + 2], grp_shift[2 * kOzMaxSlices + 2];
+    __shared__ int s_ngroups, s_abort;
+
+    const int32_t *pd = pairs + 4 * blockIdx.y;
+    const int k = pd[1] + pd[3];
+    const int K2 = CPLX ? 2 * k : k;
+    const int NP = (K2 + 15) & ~15;  // N of the MMA (multiple of 16)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s = slices;
+    const int64_t row0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t row1 = min((int64_t)m, row0 + rows_per_block);
+
+    // group table: diagonals d = 2..s+1, products (t, u) with t + u = d
+    if (tid == 0) {
+        int g = 0, p = 0;
+        for (int d = 2; d <= s + 1; ++d) {
+            grp_start[g] = p;
+            grp_shift[g] = kBeta * (s + 1 - d);
+            for (int t = 1; t <= s; ++t) {
+                const int u = d - t;
+                if (u < 1 || u > s) continue;
+                grp_t[p] = (int8_t)t;
+                grp_u[p] = (int8_t)u;
+                ++p;
+            }
+            ++g;
+        }
+        grp_start[g] = p;
+        s_ngroups = g;
+        s_abort = 0;
+    }
+    for (int a = tid; a < K2; a += GZ_THREADS) {
+        const int c = CPLX ? (a < k ? a : a - k) : a;
+        sexp[a] = cexp[c < pd[1] ? pd[0] + c : pd[2] + (c - pd[1])];
+    }
+    if (warp == 0) tmem_alloc(su32(&tmem_base_sh), 128);
+    if (tid == 0) {
+        mbar_init(su32(&bar_full[0]), 1);
+        mbar_init(su32(&bar_full[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    // zero the padded operand rows once (rows K2..63 stay zero for every chunk)
+    for (int i = tid; i < s * GZ_SLICE_BYTES / 16; i += GZ_THREADS)
+        reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    const int ngroups = s_ngroups;
+    const uint32_t idesc = idesc_f16(64, NP);
+
+    // accumulators: this thread owns TMEM lane (warp%4)*32 + lane -> output row
+    // r = (lane < 16) ? (warp%4)*16 + lane : none, and columns [half*32, half*32+32)
+    const int quad = warp & 3, half = warp >> 2;
+    const int orow = quad * 16 + lane;
+    const bool owns = lane < 16 && orow < K2;
+    Acc128 acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        acc[j].lo = 0ull;
+        acc[j].hi = 0;
+    }
+    uint32_t phase[2] = {0u, 0u};
+    int issued = 0;  // groups issued over the whole block life (buffer = issued & 1)
+    const uint32_t sbase = su32(sm);
+
+    auto issue_group = [&](int g, int buf) {
+        const uint32_t dt = tmem + (uint32_t)(buf * 64);
+        bool first = true;
+        for (int p = grp_start[g]; p < grp_start[g + 1]; ++p) {
+            const uint32_t a0 = sbase + (uint32_t)((grp_t[p] - 1) * GZ_SLICE_BYTES);
+            const uint32_t b0 = sbase + (uint32_t)((grp_u[p] - 1) * GZ_SLICE_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < GZ_KC / 16; ++ks) {
+                mma_f16(dt, desc_sw128(a0 + ks * 32), desc_sw128(b0 + ks * 32), idesc,
+                        first ? 0u : 1u);
+                first = false;
+            }
+        }
+        mma_commit(su32(&bar_full[buf]));
+    };
+
+    for (int64_t c0 = row0; c0 < row1; c0 += GZ_KC) {
+        // --- digits of rows [c0, c0 + 64) of the K2 real columns -> smem -------
+        // thread -> (column a, row pair): rows l, l+1 packed into one 32-bit store
+        const int nrow = (int)min((int64_t)GZ_KC, row1 - c0);
+        for (int idx = tid; idx < K2 * (GZ_KC / 2); idx += GZ_THREADS) {
+            const int a = idx / (GZ_KC / 2);
+            const int lp = (idx % (GZ_KC / 2)) * 2;
+            const int c = CPLX ? (a < k ? a : a - k) : a;
+            const int64_t col = c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
+            const int e = sexp[a];
+            double x0 = 0.0, x1 = 0.0;
+            if (lp < nrow) x0 = CPLX ? G[(col * ld + c0 + lp) * 2 + (a < k ? 0 : 1)] : G[col * ld + c0 + lp];
+            if (lp + 1 < nrow)
+                x1 = CPLX ? G[(col * ld + c0 + lp + 1) * 2 + (a < k ? 0 : 1)] : G[col * ld + c0 + lp + 1];
+            const unsigned long long q0 = fixed63(x0, e), q1 = fixed63(x1, e);
+            const bool n0 = x0 < 0.0, n1 = x1 < 0.0;
+            const uint32_t off = sw128_off(a, lp * 2);
+            for (int t = 1; t <= s; ++t) {
+                const __half2 h = __halves2half2(digit(q0, n0, t), digit(q1, n1, t));
+                *reinterpret_cast<__half2 *>(sm + (t - 1) * GZ_SLICE_BYTES + off) = h;
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // --- products and flushes ----------------------------------------------
+        if (tid == 0) {
+            issue_group(0, issued & 1);
+            if (ngroups > 1) issue_group(1, (issued + 1) & 1);
+        }
+        for (int g = 0; g < ngroups; ++g) {
+            const int buf = (issued + g) & 1;
+            if (!mbar_wait(su32(&bar_full[buf]), phase[buf])) {
+                if (lane == 0) s_abort = 1;
+            }
+            phase[buf] ^= 1u;
+            tc_fence_after();
+            if (!s_abort) {
+                const int sh = grp_shift[g];
+#pragma unroll
+                for (int j0 = 0; j0 < 32; j0 += 8) {
+                    uint32_t v[8];
+                    tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 64 + half * 32 + j0), v);
+                    tmem_wait_ld();
+                    if (owns) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const long long iv = (long long)__float2ll_rn(__uint_as_float(v[j]));
+                            add128_shifted(acc[j0 + j], iv, sh);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0 && g + 2 < ngroups && !s_abort) {
+                tc_fence_after();
+                issue_group(g + 2, buf);
+            }
+        }
+        issued += ngroups;
+        if (s_abort) break;
+        __syncthreads();
+    }
+    if (s_abort) {
+        if (tid == 0 && counters) atomicOr(&counters[kCntErr], kErrTimeout);
+    } else if (owns) {
+        // add the partial sums: acc_out[pair][col b][row a] = {lo, hi}
+        unsigned long long *dst = acc_out + (size_t)blockIdx.y * k2max * k2max * 2;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int b = half * 32 + j;
+            if (b < K2) {
+                unsigned long long *w = dst + ((size_t)b * k2max + orow) * 2;
+                const unsigned long long old = atomicAdd(w, acc[j].lo);
+                const unsigned long long carry = (old + acc[j].lo < old) ? 1ull : 0ull;
+                atomicAdd(w + 1, (unsigned long long)acc[j].hi + carry);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// int128 fixed-point Gram -> FP64 A_P (complex: Re = C11 + C22, Im = C12 - C21),
+// value = acc * 2^(e_a + e_b - 7 (s + 1)); both triangles written.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) gram_fixed_to_double_kernel(
+    const unsigned long long *__restrict__ acc, const int32_t *__restrict__ pairs,
+    const int32_t *__restrict__ cexp, double *__restrict__ A, int kmax, int k2max, int slices) {
+    const int32_t *pd = pairs + 4 * blockIdx.y;
+    const int k = pd[1] + pd[3];
+    const int idx = blockIdx.x * 256 + threadIdx.x;
+    if (idx >= k * k) return;
+    const int a = idx % k, b = idx / k;
+    const unsigned long long *P = acc + (size_t)blockIdx.y * k2max * k2max * 2;
+    auto ld128 = [&](int r, int c, unsigned long long &lo, long long &hi) {
+        lo = P[((size_t)c * k2max + r) * 2];
+        hi = (long long)P[((size_t)c * k2max + r) * 2 + 1];
+    };
+    auto add = [](unsigned long long &lo, long long &hi, unsigned long long lo2, long long hi2, bool sub) {
+        if (sub) {  // negate (lo2, hi2)
+            lo2 = ~lo2 + 1ull;
+            hi2 = ~hi2 + (lo2 == 0ull ? 1 : 0);
+        }
+        const unsigned long long l = lo + lo2;
+        hi = hi + hi2 + (l < lo ? 1 : 0);
+        lo = l;
+    };
+    auto to_double = [](unsigned long long lo, long long hi) {
+        // hi * 2^64 + lo (lo unsigned), rounded to double
+        return fma((double)hi, 18446744073709551616.0, (double)lo);
+    };
+    const int ca = a < pd[1] ? pd[0] + a : pd[2] + (a - pd[1]);
+    const int cb = b < pd[1] ? pd[0] + b : pd[2] + (b - pd[1]);
+    const int ex = cexp[ca] + cexp[cb] - kBeta * (slices + 1);
+    const double scale = ldexp(1.0, ex);
+    double *Ap = A + (size_t)blockIdx.y * kmax * kmax * (CPLX ? 2 : 1);
+    if (CPLX) {
+        unsigned long long rl, l2;
+        long long rh, h2;
+        ld128(a, b, rl, rh);
+        ld128(a + k, b + k, l2, h2);
+        add(rl, rh, l2, h2, false);
+        unsigned long long il;
+        long long ih;
+        ld128(a, b + k, il, ih);
+        ld128(a + k, b, l2, h2);
+        add(il, ih, l2, h2, true);
+        Ap[((size_t)b * kmax + a) * 2] = to_double(rl, rh) * scale;
+        Ap[((size_t)b * kmax + a) * 2 + 1] = to_double(il, ih) * scale;
+    } else {
+        unsigned long long rl;
+        long long rh;
+        ld128(a, b, rl, rh);
+        Ap[(size_t)b * kmax + a] = to_double(rl, rh) * scale;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Update: one block per (128-row tile, pair). A operand: digits of the rows of
+// X = [Xr Xi] (per-row exponent, computed here); B operand: digits of the
+// columns of W2 = [[Wr, Wi], [-Wi, Wr]] (per-column exponent). All diagonal
+// groups (s of them, N columns each) live in TMEM at once; one commit, one
+// drain into int64 fixed-point accumulators, then Y = acc * 2^(r_l + w_j - F).
+// ---------------------------------------------------------------------------
+constexpr int UZ_THREADS = 256;
+constexpr int UZ_M = 128;
+constexpr int UZ_ASLICE = UZ_M * 128;       // 128 rows x 128 B
+constexpr int UZ_BSLICE = kOzMaxK2 * 128;   // 64 rows x 128 B
+constexpr int UZ_F = 56;                    // fixed-point fraction bits of the update
+
+template <bool CPLX>
+__global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
+    const double *__restrict__ Gs, double *__restrict__ Gd, int64_t ld, int64_t m,
+    const int32_t *__restrict__ pairs, const double *__restrict__ Wb, int kmax, int slices,
+    unsigned long long *__restrict__ counters) {
+    extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = sm;                               // slices x 128 x 128 B
+    uint8_t *sB = sm + slices * UZ_ASLICE;          // slices x 64 x 128 B
+    __shared__ __align__(8) unsigned long long bar_done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int rexp[UZ_M];
+    __shared__ int wexp[kOzMaxK2];
+    __shared__ unsigned long long rmax_sh[UZ_M];
+    __shared__ int s_abort;
+
+    const int32_t *pd = pairs + 4 * blockIdx.y;
+    const int k = pd[1] + pd[3];
+    const int K2 = CPLX ? 2 * k : k;
+    const int NP = (K2 + 15) & ~15;
+    const int KP = NP;  // K of the MMA (K2 padded to 16)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s = slices;
+    const int64_t l0 = (int64_t)blockIdx.x * UZ_M;
+    const double *Wp = Wb + (size_t)blockIdx.y * kmax * kmax * (CPLX ? 2 : 1);
+    auto gcol = [&](int c) -> int64_t {
+        return c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
+    };
+    // X[l][a]: a < k real part of pivot column a, a >= k imaginary part
+    auto xval = [&](int64_t l, int a) -> double {
+        if (CPLX) {
+            const int c = a < k ? a : a - k;
+            return Gs[(gcol(c) * ld + l) * 2 + (a < k ? 0 : 1)];
+        }
+        return Gs[gcol(a) * ld + l];
+    };
+    // W2[a][j]
+    auto w2val = [&](int a, int j) -> double {
+        if (CPLX) {
+            const int ar = a < k ? a : a - k, jr = j < k ? j : j - k;
+            const double re = Wp[((size_t)jr * kmax + ar) * 2], im = Wp[((size_t)jr * kmax + ar) * 2 + 1];
+            if (a < k) return j < k ? re : im;  // top: [Wr Wi]
+            return j < k ? -im : re;            // bottom: [-Wi Wr]
+        }
+        return Wp[(size_t)j * kmax + a];
+    };
+
+    if (warp == 0) tmem_alloc(su32(&tmem_base_sh), 512);
+    if (tid == 0) {
+        mbar_init(su32(&bar_done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_abort = 0;
+    }
+    // zero operand tiles (padding rows/columns must be zero)
+    for (int i = tid; i < s * (UZ_ASLICE + UZ_BSLICE) / 16; i += UZ_THREADS)
+        reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    // column exponents of W2 (the same for j and j + k in the complex form)
+    for (int j = warp; j < K2; j += UZ_THREADS / 32) {
+        unsigned long long mx = 0;
+        for (int a = lane; a < K2; a += 32) {
+            const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(w2val(a, j)));
+            mx = v > mx ? v : mx;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = t > mx ? t : mx;
+        }
+        if (lane == 0) wexp[j] = exp_of_bits(mx);
+    }
+    // row exponents of X: two threads per row (halves of the columns)
+    {
+        const int r = tid & (UZ_M - 1), hf = tid >> 7;
+        const int64_t l = l0 + r;
+        unsigned long long mx = 0;
+        if (l < m)
+            for (int a = hf; a < K2; a += 2) {
+                const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(xval(l, a)));
+                mx = v > mx ? v : mx;
+            }
+        if (hf == 1) rmax_sh[r] = mx;
+        __syncthreads();
+        if (hf == 0) {
+            const unsigned long long o = rmax_sh[r];
+            rexp[r] = exp_of_bits(o > mx ? o : mx);
+        }
+    }
+    __syncthreads();
+    // digits of W2 columns: B operand row j, K position a
+    for (int idx = tid; idx < K2 * K2; idx += UZ_THREADS) {
+        const int a = idx % K2, j = idx / K2;
+        const double x = w2val(a, j);
+        const unsigned long long q = fixed63(x, wexp[j]);
+        const uint32_t off = sw128_off(j, a * 2);
+        for (int t = 1; t <= s; ++t)
+            *reinterpret_cast<__half *>(sB + (t - 1) * UZ_BSLICE + off) = digit(q, x < 0.0, t);
+    }
+    // digits of X rows: A operand row r, K position a (consecutive threads take
+    // consecutive rows of one column: coalesced loads)
+    for (int idx = tid; idx < UZ_M * K2; idx += UZ_THREADS) {
+        const int r = idx % UZ_M, a = idx / UZ_M;
+        const int64_t l = l0 + r;
+        const double x = l < m ? xval(l, a) : 0.0;
+        const unsigned long long q = fixed63(x, rexp[r]);
+        const uint32_t off = sw128_off(r, a * 2);
+        for (int t = 1; t <= s; ++t)
+            *reinterpret_cast<__half *>(sA + (t - 1) * UZ_ASLICE + off) = digit(q, x < 0.0, t);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    if (tid == 0) {
+        const uint32_t idesc = idesc_f16(UZ_M, NP);
+        const uint32_t a_base = su32(sA), b_base = su32(sB);
+        for (int d = 2; d <= s + 1; ++d) {
+            const uint32_t dt = tmem + (uint32_t)((d - 2) * NP);
+            bool first = true;
+            for (int t = 1; t <= s; ++t) {
+                const int u = d - t;
+                if (u < 1 || u > s) continue;
+                for (int ks = 0; ks < KP / 16; ++ks) {
+                    mma_f16(dt, desc_sw128(a_base + (t - 1) * UZ_ASLICE + ks * 32),
+                            desc_sw128(b_base + (u - 1) * UZ_BSLICE + ks * 32), idesc, first ? 0u : 1u);
+                    first = false;
+                }
+            }
+        }
+        mma_commit(su32(&bar_done));
+    }
+    __syncwarp();
+    if (!mbar_wait(su32(&bar_done), 0)) {
+        if (lane == 0) s_abort = 1;
+    }
+    tc_fence_after();
+    __syncthreads();
+    if (!s_abort) {
+        // thread: TMEM lane quadrant warp%4 (rows), column half warp/4
+        const int quad = warp & 3, hfc = warp >> 2;
+        const int r = quad * 32 + lane;
+        const int64_t l = l0 + r;
+        const int jbase = hfc * 32;
+        long long acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0;
+        for (int d = 2; d <= s + 1; ++d) {
+            const int sh = UZ_F - kBeta * d;  // may be negative for the lowest digits
+#pragma unroll
+            for (int j0 = 0; j0 < 32; j0 += 8) {
+                if (jbase + j0 >= NP) break;
+                uint32_t v[8];
+                tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((d - 2) * NP + jbase + j0), v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const long long iv = __float2ll_rn(__uint_as_float(v[j]));
+                    if (sh >= 0)
+                        acc[j0 + j] += iv << sh;
+                    else
+                        acc[j0 + j] += (iv + (1ll << (-sh - 1))) >> (-sh);
+                }
+            }
+        }
+        if (l < m) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int jj = jbase + j;
+                if (jj < K2) {
+                    const double y = ldexp((double)acc[j], rexp[r] + wexp[jj] - UZ_F);
+                    if (CPLX) {
+                        const int c = jj < k ? jj : jj - k;
+                        Gd[(gcol(c) * ld + l) * 2 + (jj < k ? 0 : 1)] = y;
+                    } else {
+                        Gd[gcol(jj) * ld + l] = y;
+                    }
+                }
+            }
+        }
+    } else if (tid == 0 && counters) {
+        atomicOr(&counters[kCntErr], kErrTimeout);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+int ozaki_default_slices(bool gram) { return gram ? 9 : 8; }
+
+bool ozaki_supported(bool cplx, int kmax) { return (cplx ? 2 * kmax : kmax) <= kOzMaxK2; }
+
+size_t ozaki_gram_workspace_bytes(int npairs, int kmax, bool cplx) {
+    const int k2 = cplx ? 2 * kmax : kmax;
+    return (size_t)npairs * k2 * k2 * 2 * sizeof(unsigned long long);
+}
+
+cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int64_t n,
+                          int32_t *cexp, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (cplx)
+        colexp_kernel<true><<<(unsigned)n, 256, 0, st>>>(G, ld, m, cexp);
+    else
+        colexp_kernel<false><<<(unsigned)n, 256, 0, st>>>(G, ld, m, cexp);
+    return cudaGetLastError();
+}
+
+// Gram by digit products: cexp must hold the column exponents of G (launch_colexp);
+// acc (ozaki_gram_workspace_bytes) is zeroed here; A receives the FP64 blocks.
+cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
+                              const int32_t *pairs, int npairs, double *A, int kmax,
+                              const int32_t *cexp, unsigned long long *acc, int slices,
+                              unsigned long long *counters, cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    const int k2max = cplx ? 2 * kmax : kmax;
+    if (k2max > kOzMaxK2 || slices < 1 || slices > kOzMaxSlices) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(acc, 0, ozaki_gram_workspace_bytes(npairs, kmax, cplx), st);
+    if (e != cudaSuccess) return e;
+    // rows per block: enough blocks to fill the GPU, a multiple of the chunk
+    int rpb = GZ_KC * 8;
+    while (rpb > GZ_KC && (int64_t)npairs * ((m + rpb - 1) / rpb) < 2 * 152) rpb /= 2;
+    dim3 grid((unsigned)((m + rpb - 1) / rpb), npairs);
+    const size_t smem = (size_t)slices * GZ_SLICE_BYTES + 1024;
+    if (cplx) {
+        if ((e = set_smem(gram_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
+        gram_ozaki_kernel<true><<<grid, GZ_THREADS, smem, st>>>(G, ld, m, pairs, cexp, acc, k2max,
+                                                                 slices, rpb, counters);
+    } else {
+        if ((e = set_smem(gram_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
+        gram_ozaki_kernel<false><<<grid, GZ_THREADS, smem, st>>>(G, ld, m, pairs, cexp, acc, k2max,
+                                                                  slices, rpb, counters);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 g2((unsigned)((kmax * kmax + 255) / 256), npairs);
+    if (cplx)
+        gram_fixed_to_double_kernel<true><<<g2, 256, 0, st>>>(acc, pairs, cexp, A, kmax, k2max, slices);
+    else
+        gram_fixed_to_double_kernel<false><<<g2, 256, 0, st>>>(acc, pairs, cexp, A, kmax, k2max, slices);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
+                                const int32_t *pairs, int npairs, const double *W, int kmax,
+                                int slices, unsigned long long *counters, cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    const int k2max = cplx ? 2 * kmax : kmax;
+    // all s diagonal groups of N <= 64 columns must fit the 512 TMEM columns
+    if (k2max > kOzMaxK2 || slices < 1 || slices > 8) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)slices * (UZ_ASLICE + UZ_BSLICE) + 1024;
+    dim3 grid((unsigned)((m + UZ_M - 1) / UZ_M), npairs);
+    cudaError_t e;
+    if (cplx) {
+        if ((e = set_smem(update_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
+        update_ozaki_kernel<true><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
+                                                                   slices, counters);
+    } else {
+        if ((e = set_smem(update_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
+        update_ozaki_kernel<false><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
+                                                                    slices, counters);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace jj

@@ -114,6 +114,8 @@ def random_rotation_draws(n: int, J: np.ndarray, count: int, smax: float,
                           rng: np.random.Generator, cplx: bool):
     """Draw `count` random plane rotations: (r, s, hyperbolic?, angle-or-sinh, phase)."""
     out = []
+    if n < 2:
+        return out
     for _ in range(count):
         r = int(rng.integers(0, n))
         s = int(rng.integers(0, n - 1))

@@ -44,3 +44,13 @@ def reconstruction_residual(G: np.ndarray, J, lam, U) -> float:
     U = np.asarray(U).astype(G.dtype)
     Hr = (U * np.asarray(lam, dtype=np.float64)[None, :]) @ U.conj().T
     return float(np.linalg.norm(H - Hr) / np.linalg.norm(G) ** 2)
+
+
+def pivot_rel_tol(R, k=None, factor: float = 8.0) -> float:
+    """Tolerance for eigenvalues of one pivot pencil (R^* R, J_P) when the two
+    sides start from Cholesky factors that differ by the Cholesky backward
+    error |E_ij| <= c k u sqrt(a_ii a_jj): that perturbation moves the pencil's
+    eigenvalues by up to ~ k u kappa(A_s) with kappa(A_s) = kappa(R_s)^2."""
+    k = R.shape[1] if k is None else k
+    ks = kappa_scaled(R)
+    return max(eig_rel_tol(R), factor * k * U64 * ks * ks)

@@ -47,7 +47,8 @@ def solve_gpu(G: np.ndarray, J, block_width=0, gemm=0, order=0, max_sweeps=0, al
     m, n = G.shape
     with jj.Handle(m, n, dtype_of(G), block_width=block_width, gemm=gemm, order=order,
                    max_sweeps=max_sweeps, **kw) as h:
-        info = h.jjacobi_solve(Gd, Gd.stride(1), J, allow=allow)
+        ld = Gd.stride(1) if n > 1 else m  # a single column has no meaningful stride
+        info = h.jjacobi_solve(Gd, ld, J, allow=allow)
         lam = torch.empty(n, dtype=torch.float64, device="cuda")
         U = None
         if want_U:

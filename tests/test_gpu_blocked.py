@@ -5,7 +5,8 @@ import pytest
 
 import oracle
 import synth
-from tests._util import U64, eig_rel_tol, max_rel_err, orth_residual, reconstruction_residual
+from tests._util import (U64, eig_rel_tol, max_rel_err, orth_residual, pivot_rel_tol,
+                         reconstruction_residual)
 from tests.gpu_util import col_rel_err, dtype_of, from_dev, require_gpu, solve_gpu, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -46,8 +47,9 @@ def test_gram_matches_oracle(cplx, gemm, m):
     G = rng.standard_normal((m, n)) + (1j * rng.standard_normal((m, n)) if cplx else 0)
     G *= 10.0 ** rng.uniform(-4, 4, size=(m, 1))  # graded rows
     G = np.asfortranarray(G)
-    pairs = _random_pairs(n, rng, 4, 9, 20)
-    kmax = 40
+    hi = 16 if (gemm == 1 and cplx) else 20  # the digit form takes real widths <= 64
+    pairs = _random_pairs(n, rng, 4, 9, hi)
+    kmax = 2 * hi
     Gd = to_dev(G)
     pd = torch.from_numpy(pairs).cuda()
     A = torch.zeros(len(pairs) * kmax * kmax * (2 if cplx else 1), dtype=torch.float64,
@@ -72,11 +74,12 @@ def test_update_matches_oracle(cplx, gemm):
     jj = require_gpu()
     import torch
     rng = np.random.default_rng(3 + cplx + 10 * gemm)
-    m, n, kmax = 517, 120, 48
+    hi = 16 if (gemm == 1 and cplx) else 24  # the digit form takes real widths <= 64
+    m, n, kmax = 517, 120, 2 * hi
     G = rng.standard_normal((m, n)) + (1j * rng.standard_normal((m, n)) if cplx else 0)
     G *= 10.0 ** rng.uniform(-3, 3, size=(m, 1))
     G = np.asfortranarray(G)
-    pairs = _random_pairs(n, rng, 2, 13, 24)
+    pairs = _random_pairs(n, rng, 2, 11, hi)
     Ws = []
     Wbuf = np.zeros((len(pairs), kmax, kmax), dtype=G.dtype)
     for q, p in enumerate(pairs):
@@ -143,10 +146,18 @@ def test_inner_matches_oracle(cplx):
         Jm = np.diag(JP.astype(np.float64))
         wmax = np.abs(W).max()
         assert np.abs(W.conj().T @ Jm @ W - Jm).max() <= 1e4 * U64 * wmax ** 2
-        assert col_rel_err(Rt[q, :k, :k], R @ W) <= 1e3 * U64 * wmax
+        # The GPU's Cholesky factor, recovered as R~ W^{-1} = R~ J W^* J, is upper
+        # triangular and reproduces A_P to the Cholesky backward error (its forward
+        # error against LAPACK's factor grows with cond(A_P), so it is not compared).
+        Rg = Rt[q, :k, :k] @ (Jm @ W.conj().T @ Jm)
+        AP = R.conj().T @ R
+        dd = np.sqrt(np.abs(np.diag(AP)))
+        scale = np.abs(Rt[q, :k, :k]).max() * wmax
+        assert np.abs(np.tril(Rg, -1)).max() <= 1e4 * U64 * scale
+        assert np.max(np.abs(Rg.conj().T @ Rg - AP) / np.outer(dd, dd)) <= 1e4 * U64 * wmax ** 2
         lam_gpu = JP * np.linalg.norm(Rt[q, :k, :k], axis=0) ** 2
         ref = oracle.inner_solve(R, JP)
-        assert max_rel_err(lam_gpu, ref["lam"]) <= eig_rel_tol(R)
+        assert max_rel_err(lam_gpu, ref["lam"]) <= pivot_rel_tol(R)
         U = Rt[q, :k, :k] / np.linalg.norm(Rt[q, :k, :k], axis=0)
         assert orth_residual(U) <= 8 * oracle.TOL_DEFAULT
 
@@ -223,6 +234,10 @@ def test_one_parallel_step_through_building_blocks(gemm):
     lam_gpu = P.J * np.linalg.norm(out, axis=0) ** 2
     for p in pairs:
         cols = np.r_[p[0]:p[0] + p[1], p[2]:p[2] + p[3]]
-        assert max_rel_err(lam_gpu[cols], lam_ref[cols]) <= eig_rel_tol(P.G)
+        R0 = oracle.cholesky_upper(oracle.gram(P.G[:, cols]))
+        assert max_rel_err(lam_gpu[cols], lam_ref[cols]) <= pivot_rel_tol(R0)
+        # After one step the pivot columns are orthogonal up to the Gram and
+        # Cholesky errors carried through W_P, as in the oracle's own step.
         U = out[:, cols] / np.linalg.norm(out[:, cols], axis=0)
-        assert orth_residual(U) <= 8 * oracle.TOL_DEFAULT
+        Ur = ref["Gt"][:, cols] / np.linalg.norm(ref["Gt"][:, cols], axis=0)
+        assert orth_residual(U) <= max(8 * oracle.TOL_DEFAULT, 10 * orth_residual(Ur))
