@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 one-sided J-Jacobi solver (one JSON line on stdout).
+
+A step is one complete solve of the hot path on one synthetic input: J sort,
+parallel-ordered sweeps of the blocked full-block method (Gram, Cholesky +
+inner J-Jacobi with accumulated W, update, convergence count) until a sweep
+applies no rotation, then eigenpair extraction. The headline workload is the
+graded complex128 problem of order 4096 (G = D1 B D2, B = Q |Lambda|^{1/2} W,
+J = diag(+I_2560, -I_1536)).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--block-width B] [--gemm ozaki|fp64] [--no-plain]
+
+--impl reference times the CPU oracle (the plain one-sided J-Jacobi, in C,
+single-threaded) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "graded_c128_n4096_b64"
+METRIC = "time-to-solution & GFLOP/s, blocked J-Jacobi n=4096 c128, vs plain form at rel-err≤1e-12"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flops x max SM clock
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def blocked_flops(n: int, m: int, cplx: bool, info: dict) -> float:
+    """Algorithmic FP64-equivalent flops of one blocked solve.
+
+    Per pair and step: Gram k(k+1)/2 * m MACs (Hermitian half), update m k^2 MACs;
+    per applied inner rotation 5 k MACs (dot, R and W column pairs). A complex MAC
+    is 8 real flops, a real MAC 2."""
+    mac = 8.0 if cplx else 2.0
+    nbl = info["nbl"]
+    k = 2.0 * n / nbl
+    pair_steps = info["sweeps"] * info["steps_per_sweep"] * (nbl // 2)
+    gemm = pair_steps * (k * (k + 1) / 2 * m + m * k * k)
+    inner = info["rotations"] * 5.0 * k
+    return mac * (gemm + inner)
+
+
+def plain_flops(n: int, m: int, cplx: bool, sweeps: int) -> float:
+    """Algorithmic flops of the plain method: per pair and sweep one dot product
+    and one column-pair rotation (3 m MACs)."""
+    mac = 8.0 if cplx else 2.0
+    return mac * sweeps * n * (n - 1) / 2 * 3.0 * m
+
+
+def cpu_baseline(P, budget_s: float = 15.0):
+    """The oracle on a bounded sample: one row-cyclic sweep of the plain method on
+    the leading ncol columns of G (all m rows), ncol grown until about budget_s
+    of CPU time. Returns GFLOP/s of plain-method work, and the sample."""
+    import numpy as np
+
+    import oracle
+
+    ncol = 32
+    best = None
+    while True:
+        Gs = np.asfortranarray(P.G[:, :ncol])
+        t0 = time.perf_counter()
+        oracle.solve_plain(Gs, P.J[:ncol], max_sweeps=1)
+        dt = time.perf_counter() - t0
+        fl = plain_flops(ncol, P.m, True, 1) * 1.0
+        best = (fl / dt / 1e9, ncol, dt)
+        if dt > budget_s / 3 or ncol >= P.n:
+            break
+        ncol = min(P.n, ncol * 2)
+    return best
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    import synth
+
+    P = synth.make_workload(WORKLOAD, precision="f64")
+    vals = []
+    for i in range(args.warmup + args.steps):
+        g, ncol, dt = cpu_baseline(P, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            vals.append((g, ncol, dt))
+    v = statistics.median(x[0] for x in vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.median(x[2] for x in vals) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": P.n, "m": P.m, "form": "plain oracle sample"},
+        "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one row-cyclic plain sweep on the leading {vals[0][1]} "
+                                   f"columns (all {P.m} rows) of the n={P.n} graded input"},
+        "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1008_4166_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def kernel_breakdown(jj, torch, P, bw, gemm, stream, nsteps=8):
+    """Per-kernel device time of the first nsteps parallel steps, through the
+    building-block entry points, timed with CUDA events on the launching stream."""
+    import numpy as np
+
+    n, m = P.n, P.m
+    nbl = 2 * ((n + 2 * bw - 1) // (2 * bw))
+    sizes = [n // nbl + (1 if l < n % nbl else 0) for l in range(nbl)]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    tab = jj.jjacobi_schedule(nbl, 0, 1)
+    kmax = 2 * max(sizes)
+    with torch.cuda.stream(stream):
+        Gs = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()
+        Gd = torch.zeros_like(Gs)
+        A = torch.zeros(nbl // 2 * kmax * kmax * 2, dtype=torch.float64, device="cuda")
+        W = torch.zeros_like(A)
+        Jd = torch.from_numpy(P.J.astype(np.int8)).cuda()
+        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        t = {"gram": 0.0, "inner": 0.0, "update": 0.0}
+        for s in range(min(nsteps, len(tab))):
+            pairs = np.array([[offs[i], sizes[i], offs[j], sizes[j]] for i, j in tab[s]],
+                             dtype=np.int32)
+            pd = torch.from_numpy(pairs).cuda()
+            stream.synchronize()
+            ev[0].record(stream)
+            jj.jjk_gram(1, gemm, Gs, Gs.stride(1), m, pd, len(pairs), A, kmax, stream=stream)
+            ev[1].record(stream)
+            jj.jjk_inner(1, A, W, kmax, pd, len(pairs), Jd, 0.0, 30, 0, cnt, stream=stream)
+            ev[2].record(stream)
+            jj.jjk_update(1, gemm, Gs, Gd, Gs.stride(1), m, pd, len(pairs), W, kmax, stream=stream)
+            ev[3].record(stream)
+            stream.synchronize()
+            t["gram"] += ev[0].elapsed_time(ev[1])
+            t["inner"] += ev[1].elapsed_time(ev[2])
+            t["update"] += ev[2].elapsed_time(ev[3])
+            Gs, Gd = Gd, Gs
+        steps = min(nsteps, len(tab))
+        rot = int(cnt[0])
+    per = {k: v / steps for k, v in t.items()}
+    return per, dict(npairs=nbl // 2, k=kmax, m=m, steps=steps, rotations=rot)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    rank, world, local = _dist()
+    __graft_entry__.build()
+    from paper_1008_4166_gb300 import jjacobi as jj
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    P = synth.make_workload(WORKLOAD, precision="f64")
+    n, m = P.n, P.m
+    gemm = jj.JJ_GEMM_OZAKI_FP16 if args.gemm == "ozaki" else jj.JJ_GEMM_FP64
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        G0 = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()  # column-major
+        Gw = torch.empty_like(G0)
+        lam = torch.empty(n, dtype=torch.float64, device="cuda")
+    h = jj.Handle(m, n, jj.JJ_C128, block_width=args.block_width, gemm=gemm, stream=stream)
+
+    def step():
+        Gw.copy_(G0)
+        info = h.jjacobi_solve(Gw, Gw.stride(1), P.J, allow=(jj.JJ_OK,))
+        h.jjacobi_extract(lam, None, 0, 0)
+        return info
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            info = step()
+    stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    with torch.cuda.stream(stream):
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(step().as_dict())
+        e1.record(stream)
+    stream.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    info = infos[-1]
+    flops = blocked_flops(n, m, True, info)
+    value = flops * world / (ms * 1e-3) / 1e9
+    launches = sum(x["kernel_launches"] + 1 for x in infos)  # + extraction kernel
+    lam_blocked = lam.cpu().numpy().copy()
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    Gh = torch.from_numpy(np.ascontiguousarray(P.G.T)).pin_memory().numpy().T
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        lam_h, _, _ = h.jjacobi_solve_host(Gh, P.J, want_U=False)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": flops / e2e_s / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int(m * n * 16), "d2h_bytes_per_step": int(n * 8)}
+
+    # per-kernel breakdown and roofline of the dominant kernel
+    per, geo = kernel_breakdown(jj, torch, P, args.block_width, gemm, stream)
+    dom = max(per, key=per.get)
+    peaks = _peaks()
+    cplx_mac = 8.0
+    npairs, k = geo["npairs"], geo["k"]
+    if dom == "inner":
+        rot_per_step = geo["rotations"] / geo["steps"]
+        achieved = rot_per_step * 5.0 * k * cplx_mac / (per["inner"] * 1e-3) / 1e12
+        roof = {"kernel": "inner_smem_kernel", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 x 2070 MHz (derived)"}
+    else:
+        tflops_fp16 = peaks.get("bf16_tflops", 1900.0)
+        if gemm == jj.JJ_GEMM_OZAKI_FP16:
+            # executed fp16 tensor flops: digit products x real GEMM size
+            s_g, s_u = 9, 8
+            if dom == "gram":
+                prods = sum(1 for d in range(2, s_g + 2) for t in range(1, s_g + 1)
+                            if 1 <= d - t <= s_g and t <= d - t)
+                fl = npairs * prods * 2.0 * 64 * 64 * m
+            else:
+                prods = sum(1 for d in range(2, s_u + 2) for t in range(1, s_u + 1) if 1 <= d - t <= s_u)
+                fl = npairs * prods * 2.0 * m * 64 * 64
+            achieved = fl / (per[dom] * 1e-3) / 1e12
+            roof = {"kernel": dom + "_ozaki_kernel", "bound": "tensor", "achieved": achieved,
+                    "peak": tflops_fp16, "unit": "TFLOP/s",
+                    "peak_source": "measured bf16 burst (fp16 has the same dense rate)"}
+        else:
+            fl = npairs * (k * (k + 1) / 2 * m if dom == "gram" else m * k * k) * cplx_mac
+            roof = {"kernel": dom + "_fp64_kernel", "bound": "alu",
+                    "achieved": fl / (per[dom] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "FP64 derived"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        ent = tr.get(roof["kernel"])
+        if ent and ent.get("src_hash") == src_hash():
+            roof["traffic"] = ent["bytes_per_launch"]
+    except Exception:
+        pass
+    roof["ms_per_launch"] = per[dom]
+    roof["kernel_ms_per_step"] = per
+
+    # the plain form on the same input, same accuracy target
+    plain = None
+    if args.plain and rank == 0:
+        hp = jj.Handle(m, n, jj.JJ_C128, block_width=0, stream=stream)
+        with torch.cuda.stream(stream):
+            Gw.copy_(G0)
+            ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ep0.record(stream)
+            pinfo = hp.jjacobi_solve(Gw, Gw.stride(1), P.J)
+            ep1.record(stream)
+            hp.jjacobi_extract(lam, None, 0, 0)
+        stream.synchronize()
+        lam_plain = lam.cpu().numpy()
+        pi = pinfo.as_dict()
+        rel = float(np.max(np.abs(np.sort(lam_blocked) - np.sort(lam_plain)) / np.abs(np.sort(lam_plain))))
+        plain = {"time_to_solution_s": ep0.elapsed_time(ep1) / 1e3, "sweeps": pi["sweeps"],
+                 "gflops": plain_flops(n, m, True, pi["sweeps"]) / (ep0.elapsed_time(ep1) * 1e-3) / 1e9,
+                 "speedup_blocked_vs_plain": (ep0.elapsed_time(ep1)) / ms,
+                 "max_rel_eig_diff_blocked_vs_plain": rel}
+        hp.close()
+    h.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        g, ncol, dt = cpu_baseline(P, budget_s=15.0)
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"one row-cyclic plain sweep on the leading {ncol} columns (all {m} rows) "
+                         f"of the n={n} graded input, {dt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": m, "n": n, "block_width": args.block_width,
+                       "gemm": args.gemm, "order": "round_robin", "sweeps": info["sweeps"],
+                       "steps_per_sweep": info["steps_per_sweep"],
+                       "time_to_solution_s": ms / 1e3,
+                       "l2": "inputs larger than L2 (G = 256 MiB, 2 work copies)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "plain": plain,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--block-width", type=int, default=16)
+    ap.add_argument("--gemm", default="ozaki", choices=["ozaki", "fp64"])
+    ap.add_argument("--no-plain", dest="plain", action="store_false")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=6.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

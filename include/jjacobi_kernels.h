@@ -70,6 +70,27 @@ int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld
 int jjk_extract(int32_t dtype, const void *G, int64_t ld, int64_t m, int64_t n,
                 const int8_t *J, double *lambda, void *U, int64_t ldu, void *stream);
 
+/* The Gram of jjk_gram with gemm = JJ_GEMM_OZAKI_FP16, for callers that cannot
+ * allocate device memory (the paper has no counterpart: this is a property of
+ * the library, not of the method). Such callers include code running inside a
+ * host callback or a driver hook where allocation calls are not allowed, and
+ * real-time loops that must not enter an allocator after start-up. jjk_gram
+ * takes its scratch from the stream-ordered allocator; this call takes it from
+ * one fixed array of device memory inside the library instead (about 8.3 MiB,
+ * held by every GPU that loads the library until the process exits).
+ *   Limits: npairs * (2 kmax)^2 * 16 bytes (complex) or npairs * kmax^2 * 16
+ *   bytes (real) must not exceed 8 MiB, real pivot width (2 kmax complex,
+ *   kmax real) <= 64, and ncols <= 65536; larger sizes return JJ_INVALID_ARG.
+ *   ncols: number of columns of G; every column a pair names must be < ncols.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current) and should come before any stream capture.
+ *   Every call shares the one array and clears the part it uses before use;
+ *   two calls whose work overlaps on the GPU (different streams, or different
+ *   host threads without ordering) race on it. No cudaMalloc, cudaFree or
+ *   other allocating routine is called. */
+int jjk_gram_noalloc(int32_t dtype, const void *G, int64_t ld, int64_t m, const int32_t *pairs,
+                     int32_t npairs, double *A, int32_t kmax, int64_t ncols, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -134,8 +134,8 @@ int enqueue_sweep(jj_ctx *c, int start_buf, int *launches) {
                                  st));
             if (c->ozaki)
                 JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m, pr,
-                                            c->npairs, c->Wblk, c->kmax, c->oz_slices_update,
-                                            c->d_cnt, st));
+                                            c->npairs, c->Wblk, c->kmax, c->d_cexp,
+                                            c->oz_slices_update, c->d_cnt, st));
             else
                 JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m,
                                       pr, c->npairs, c->Wblk, c->kmax, st));
@@ -567,9 +567,25 @@ int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld
     const bool cplx = dtype == JJ_C128;
     if (gemm == JJ_GEMM_OZAKI_FP16) {
         if (!ozaki_supported(cplx, kmax)) return JJ_INVALID_ARG;
-        JJ_CUDA(launch_update_ozaki(cplx, (const double *)Gs, (double *)Gd, ld, m, pairs, npairs, W,
-                                    kmax, ozaki_default_slices(false), nullptr,
-                                    (cudaStream_t)stream));
+        cudaStream_t st = (cudaStream_t)stream;
+        int64_t ncols = 0;
+        {
+            std::vector<int32_t> hp((size_t)npairs * 4);
+            JJ_CUDA(cudaMemcpyAsync(hp.data(), pairs, hp.size() * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st));
+            JJ_CUDA(cudaStreamSynchronize(st));
+            for (int q = 0; q < npairs; ++q)
+                ncols = std::max<int64_t>(ncols, std::max(hp[4 * q] + hp[4 * q + 1],
+                                                          hp[4 * q + 2] + hp[4 * q + 3]));
+        }
+        int32_t *cexp = nullptr;
+        JJ_CUDA(cudaMallocAsync((void **)&cexp, std::max<int64_t>(ncols, 1) * sizeof(int32_t), st));
+        cudaError_t e = launch_colexp(cplx, (const double *)Gs, ld, m, ncols, cexp, st);
+        if (e == cudaSuccess)
+            e = launch_update_ozaki(cplx, (const double *)Gs, (double *)Gd, ld, m, pairs, npairs, W,
+                                    kmax, cexp, ozaki_default_slices(false), nullptr, st);
+        cudaFreeAsync(cexp, st);
+        JJ_CUDA(e);
         return JJ_OK;
     }
     JJ_CUDA(launch_update(cplx, gemm, (const double *)Gs, (double *)Gd, ld, m, pairs, npairs, W,

@@ -431,8 +431,8 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double *R = sm;                              // k x k entries
     double *W = R + (size_t)k * ldr * E;         // k x k entries
     double *dsh = W + (size_t)k * ldr * E;       // k
-    double *qsh = dsh + k;                       // SW x 8 rotation broadcast
-    int *jsh = reinterpret_cast<int *>(qsh + SW * 8);
+    double *qsh = dsh + kmax;                    // per-step dots and rotation parameters
+    int *jsh = reinterpret_cast<int *>(qsh + 2 * 64 + 7 * 64);
     __shared__ int s_rot, s_fail;
     __shared__ double s_piv;
     __shared__ double s_max[SW];
@@ -511,9 +511,13 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     }
     __syncthreads();
     const int npl = k + (k & 1);
+    const int P = npl - 1;
+    const int nq = npl / 2;  // column pairs per inner step (<= 32 for k <= 64, <= 64 for k <= 128)
     unsigned long long total_rot = 0;
     double maxoff = 0.0;
-    double *q = qsh + warp * 8;
+    // per-step scratch: dot products and rotation parameters of every pair
+    double *sdot = qsh;                       // [nq][2]
+    double *spar = qsh + 2 * 64;              // [nq][7]: ce_re ce_im se_re se_im c hs flag
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int c = warp; c < k; c += SW) {
             double acc = 0.0;
@@ -534,100 +538,110 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         }
         if (tid == 0) s_rot = 0;
         __syncthreads();
-        maxoff = 0.0;
         int my_rot = 0;
-        for (int step = 0; step < npl - 1; ++step) {
-            for (int qi = warp; qi < npl / 2; qi += SW) {
-                int a, b;
-                const int P = npl - 1;
-                if (qi == 0) {
-                    a = P;
-                    b = step;
-                } else {
-                    a = (step + qi) % P;
-                    b = (step - qi + P) % P;
-                }
-                if (a >= k || b >= k) continue;
-                if (a > b) {
-                    const int t = a;
-                    a = b;
-                    b = t;
-                }
-                double xr[ROWS], xi[ROWS], yr[ROWS], yi[ROWS];
+        for (int step = 0; step < P; ++step) {
+            // (1) dot products a_ab = r_a^* r_b: one warp per pair, lanes over rows
+            for (int qi = warp; qi < nq; qi += SW) {
+                int a = qi == 0 ? P : (step + qi) % P;
+                int b = qi == 0 ? step : (step - qi + P) % P;
+                if (a > b) { const int t = a; a = b; b = t; }
                 double sr = 0.0, si = 0.0;
+                if (b < k) {
 #pragma unroll
-                for (int i = 0; i < ROWS; ++i) {
-                    const int l = lane + 32 * i;
-                    if (l < k) {
-                        if (CPLX) {
-                            const double2 u = *reinterpret_cast<const double2 *>(R + ((size_t)a * ldr + l) * 2);
-                            const double2 v = *reinterpret_cast<const double2 *>(R + ((size_t)b * ldr + l) * 2);
-                            xr[i] = u.x; xi[i] = u.y; yr[i] = v.x; yi[i] = v.y;
-                            sr = fma(xr[i], yr[i], fma(xi[i], yi[i], sr));
-                            si = fma(xr[i], yi[i], fma(-xi[i], yr[i], si));
-                        } else {
-                            xr[i] = R[(size_t)a * ldr + l];
-                            yr[i] = R[(size_t)b * ldr + l];
-                            sr = fma(xr[i], yr[i], sr);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    sr += __shfl_xor_sync(0xffffffffu, sr, o);
-                    if (CPLX) si += __shfl_xor_sync(0xffffffffu, si, o);
-                }
-                if (lane == 0) {
-                    const double da = dsh[a], db = dsh[b];
-                    const double absa = CPLX ? sqrt(sr * sr + si * si) : fabs(sr);
-                    const double rel = absa / sqrt(da * db);
-                    double flag = 0.0;
-                    if (!isfinite(rel)) {
-                        atomicOr(&counters[kCntErr], kErrNonfinite);
-                    } else {
-                        maxoff = fmax(maxoff, rel);
-                        if (rel > tol) {
-                            Rot Q;
-                            if (rotation(da, db, sr, si, jsh[a] * jsh[b], CPLX, Q)) {
-                                q[0] = Q.ce_re; q[1] = Q.ce_im; q[2] = Q.se_re; q[3] = Q.se_im;
-                                q[4] = Q.c; q[5] = Q.hs;
-                                dsh[a] = Q.dr;
-                                dsh[b] = Q.ds;
-                                flag = 1.0;
-                                ++my_rot;
+                    for (int i = 0; i < ROWS; ++i) {
+                        const int l = lane + 32 * i;
+                        if (l < k) {
+                            if (CPLX) {
+                                const double2 u = *reinterpret_cast<const double2 *>(R + ((size_t)a * ldr + l) * 2);
+                                const double2 v = *reinterpret_cast<const double2 *>(R + ((size_t)b * ldr + l) * 2);
+                                sr = fma(u.x, v.x, fma(u.y, v.y, sr));
+                                si = fma(u.x, v.y, fma(-u.y, v.x, si));
                             } else {
-                                atomicOr(&counters[kCntErr], kErrNotPosdef);
+                                sr = fma(R[(size_t)a * ldr + l], R[(size_t)b * ldr + l], sr);
                             }
                         }
                     }
-                    q[6] = flag;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                        if (CPLX) si += __shfl_xor_sync(0xffffffffu, si, o);
+                    }
                 }
-                __syncwarp();
-                if (q[6] == 0.0) {
-                    __syncwarp();
-                    continue;
+                if (lane == 0) {
+                    sdot[2 * qi] = sr;
+                    sdot[2 * qi + 1] = si;
                 }
+            }
+            __syncthreads();
+            // (2) rotation parameters of all pairs of the step at once: warp 0,
+            // one lane per pair (the FP64 sequences run once per step, not once
+            // per pair)
+            if (warp == 0) {
+                for (int qi = lane; qi < nq; qi += 32) {
+                    int a = qi == 0 ? P : (step + qi) % P;
+                    int b = qi == 0 ? step : (step - qi + P) % P;
+                    if (a > b) { const int t = a; a = b; b = t; }
+                    double flag = 0.0;
+                    if (b < k) {
+                        const double sr = sdot[2 * qi], si = sdot[2 * qi + 1];
+                        const double da = dsh[a], db = dsh[b];
+                        const double absa = CPLX ? sqrt(sr * sr + si * si) : fabs(sr);
+                        const double rel = absa / sqrt(da * db);
+                        if (!isfinite(rel)) {
+                            atomicOr(&counters[kCntErr], kErrNonfinite);
+                        } else {
+                            maxoff = fmax(maxoff, rel);
+                            if (rel > tol) {
+                                Rot Q;
+                                if (rotation(da, db, sr, si, jsh[a] * jsh[b], CPLX, Q)) {
+                                    double *pp = spar + 7 * qi;
+                                    pp[0] = Q.ce_re; pp[1] = Q.ce_im; pp[2] = Q.se_re; pp[3] = Q.se_im;
+                                    pp[4] = Q.c; pp[5] = Q.hs;
+                                    dsh[a] = Q.dr;
+                                    dsh[b] = Q.ds;
+                                    flag = 1.0;
+                                    ++my_rot;
+                                } else {
+                                    atomicOr(&counters[kCntErr], kErrNotPosdef);
+                                }
+                            }
+                        }
+                    }
+                    spar[7 * qi + 6] = flag;
+                }
+            }
+            __syncthreads();
+            // (3) apply: one warp per pair, lanes over rows of R and W
+            for (int qi = warp; qi < nq; qi += SW) {
+                const double *pp = spar + 7 * qi;
+                if (pp[6] == 0.0) continue;
+                int a = qi == 0 ? P : (step + qi) % P;
+                int b = qi == 0 ? step : (step - qi + P) % P;
+                if (a > b) { const int t = a; a = b; b = t; }
                 Rot Q;
-                Q.ce_re = q[0]; Q.ce_im = q[1]; Q.se_re = q[2]; Q.se_im = q[3]; Q.c = q[4]; Q.hs = q[5];
-                __syncwarp();
+                Q.ce_re = pp[0]; Q.ce_im = pp[1]; Q.se_re = pp[2]; Q.se_im = pp[3]; Q.c = pp[4]; Q.hs = pp[5];
 #pragma unroll
                 for (int i = 0; i < ROWS; ++i) {
                     const int l = lane + 32 * i;
                     if (l < k) {
                         if (CPLX) {
-                            rot_apply_c(Q, xr[i], xi[i], yr[i], yi[i]);
-                            *reinterpret_cast<double2 *>(R + ((size_t)a * ldr + l) * 2) = make_double2(xr[i], xi[i]);
-                            *reinterpret_cast<double2 *>(R + ((size_t)b * ldr + l) * 2) = make_double2(yr[i], yi[i]);
-                            double2 u = *reinterpret_cast<const double2 *>(W + ((size_t)a * ldr + l) * 2);
-                            double2 v = *reinterpret_cast<const double2 *>(W + ((size_t)b * ldr + l) * 2);
+                            double2 u = *reinterpret_cast<const double2 *>(R + ((size_t)a * ldr + l) * 2);
+                            double2 v = *reinterpret_cast<const double2 *>(R + ((size_t)b * ldr + l) * 2);
+                            rot_apply_c(Q, u.x, u.y, v.x, v.y);
+                            *reinterpret_cast<double2 *>(R + ((size_t)a * ldr + l) * 2) = u;
+                            *reinterpret_cast<double2 *>(R + ((size_t)b * ldr + l) * 2) = v;
+                            u = *reinterpret_cast<const double2 *>(W + ((size_t)a * ldr + l) * 2);
+                            v = *reinterpret_cast<const double2 *>(W + ((size_t)b * ldr + l) * 2);
                             rot_apply_c(Q, u.x, u.y, v.x, v.y);
                             *reinterpret_cast<double2 *>(W + ((size_t)a * ldr + l) * 2) = u;
                             *reinterpret_cast<double2 *>(W + ((size_t)b * ldr + l) * 2) = v;
                         } else {
-                            rot_apply_r(Q, xr[i], yr[i]);
-                            R[(size_t)a * ldr + l] = xr[i];
-                            R[(size_t)b * ldr + l] = yr[i];
-                            double u = W[(size_t)a * ldr + l], v = W[(size_t)b * ldr + l];
+                            double u = R[(size_t)a * ldr + l], v = R[(size_t)b * ldr + l];
+                            rot_apply_r(Q, u, v);
+                            R[(size_t)a * ldr + l] = u;
+                            R[(size_t)b * ldr + l] = v;
+                            u = W[(size_t)a * ldr + l];
+                            v = W[(size_t)b * ldr + l];
                             rot_apply_r(Q, u, v);
                             W[(size_t)a * ldr + l] = u;
                             W[(size_t)b * ldr + l] = v;
@@ -637,7 +651,11 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
             }
             __syncthreads();
         }
-        if (lane == 0 && my_rot) atomicAdd(&s_rot, my_rot);
+        if (warp == 0) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) my_rot += __shfl_xor_sync(0xffffffffu, my_rot, o);
+            if (lane == 0 && my_rot) atomicAdd(&s_rot, my_rot);
+        }
         __syncthreads();
         const int rot = s_rot;
         total_rot += (unsigned long long)rot;
@@ -653,6 +671,8 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
             Wg[((int64_t)b * kmax + a) * E + e] = W[((size_t)b * ldr + a) * E + e];
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxoff = fmax(maxoff, __shfl_xor_sync(0xffffffffu, maxoff, o));
     if (lane == 0) s_max[warp] = maxoff;
     __syncthreads();
     if (tid == 0) {
@@ -665,7 +685,8 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
 
 size_t inner_smem_bytes(bool cplx, int kmax) {
     const int E = cplx ? 2 : 1;
-    return sizeof(double) * ((size_t)2 * kmax * kmax * E + kmax + SW * 8) + sizeof(int) * kmax + 64;
+    return sizeof(double) * ((size_t)2 * kmax * kmax * E + kmax + 2 * 64 + 7 * 64) +
+           sizeof(int) * kmax + 64;
 }
 
 }  // namespace

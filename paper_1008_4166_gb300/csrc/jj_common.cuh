@@ -134,9 +134,11 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
                               const int32_t *pairs, int npairs, double *A, int kmax,
                               const int32_t *cexp, unsigned long long *acc, int slices,
                               unsigned long long *counters, cudaStream_t st);
+// cexp: column exponents of Gs (launch_colexp), used for the two-sided scaling.
 cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
                                 const int32_t *pairs, int npairs, const double *W, int kmax,
-                                int slices, unsigned long long *counters, cudaStream_t st);
+                                const int32_t *cexp, int slices, unsigned long long *counters,
+                                cudaStream_t st);
 
 // Host-side ordering tables (jj_schedule.cpp).
 int schedule_pairs(int nbl, int order, int sweep, int32_t *pairs);

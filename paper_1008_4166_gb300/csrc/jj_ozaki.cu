@@ -153,10 +153,47 @@ __device__ __forceinline__ unsigned long long fixed63(double x, int e) {
     return mant >> (-sh);
 }
 
-// Digit t (1-based) of the fixed-point value, with the sign of x.
+// Two digits t (1-based) of two fixed-point values as a packed fp16 pair, with
+// the signs of their sources. A digit d <= 127 is formed exactly as
+// (1024 + d) - 1024 in fp16 ((1024 + d) has the bit pattern 0x6400 | d), and the
+// sign is set on the bit pattern: integer and fp16 ALU work only.
+__device__ __forceinline__ __half2 digits2(unsigned long long q0, bool n0, unsigned long long q1,
+                                          bool n1, int t) {
+    const uint32_t d0 = (uint32_t)((q0 >> (63 - kBeta * t)) & 127ull);
+    const uint32_t d1 = (uint32_t)((q1 >> (63 - kBeta * t)) & 127ull);
+    const uint32_t biased = (0x6400u | d0) | ((0x6400u | d1) << 16);
+    __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&biased), __half2(__half(1024.f), __half(1024.f)));
+    uint32_t bits = *reinterpret_cast<uint32_t *>(&h);
+    bits ^= (n0 ? 0x8000u : 0u) | (n1 ? 0x80000000u : 0u);
+    return *reinterpret_cast<__half2 *>(&bits);
+}
 __device__ __forceinline__ __half digit(unsigned long long q, bool neg, int t) {
-    const int d = (int)((q >> (63 - kBeta * t)) & 127ull);
-    return __int2half_rn(neg ? -d : d);
+    return __low2half(digits2(q, neg, 0ull, false, t));
+}
+
+// v * 2^e as a double, built from the integer's bits (normalize, round to
+// nearest even, assemble exponent and significand): integer ALU work only. Out
+// of the normal range (never for these workloads) it defers to ldexp.
+__device__ __forceinline__ double int_scaled_to_double(long long v, int e) {
+    if (v == 0) return 0.0;
+    const bool neg = v < 0;
+    const unsigned long long u = neg ? (unsigned long long)(-v) : (unsigned long long)v;
+    int lz = __clzll((long long)u);
+    const unsigned long long mm = u << lz;       // leading one at bit 63
+    unsigned long long mant = mm >> 11;          // 53 bits
+    const unsigned long long low = mm & 0x7FFull;
+    if (low > 0x400ull || (low == 0x400ull && (mant & 1ull))) {
+        ++mant;
+        if (mant == (1ull << 53)) {
+            mant >>= 1;
+            --lz;
+        }
+    }
+    const int biased = 63 + e - lz + 1023;
+    if (biased < 1 || biased > 2046) return ldexp((double)v, e);
+    const unsigned long long bits = ((unsigned long long)neg << 63) |
+                                    ((unsigned long long)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -200,30 +237,8 @@ __global__ void __launch_bounds__(256) colexp_kernel(const double *__restrict__ 
 constexpr int GZ_THREADS = 256;
 constexpr int GZ_KC = 64;                 // rows of G per chunk (K of one MMA group)
 constexpr int GZ_SLICE_BYTES = 64 * 128;  // 64 operand rows x 128 bytes
-
-struct Acc128 {
-    unsigned long long lo;
-    long long hi;
-};
-
-__device__ __forceinline__ void add128_shifted(Acc128 &a, long long v, int sh) {
-    // a += v * 2^sh, 0 <= sh < 127, |v| < 2^40
-    unsigned long long lo_add;
-    long long hi_add;
-    if (sh == 0) {
-        lo_add = (unsigned long long)v;
-        hi_add = v >> 63;
-    } else if (sh < 64) {
-        lo_add = (unsigned long long)v << sh;
-        hi_add = v >> (64 - sh);
-    } else {
-        lo_add = 0ull;
-        hi_add = v << (sh - 64);
-    }
-    const unsigned long long lo = a.lo + lo_add;
-    a.hi += hi_add + (lo < lo_add ? 1 : 0);
-    a.lo = lo;
-}
+constexpr int GZ_GMAX = 4;                // digit products per TMEM group
+constexpr int GZ_MAXGROUPS = 32;
 
 template <bool CPLX>
 __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
@@ -236,7 +251,7 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
     __shared__ uint32_t tmem_base_sh;
     __shared__ int sexp[kOzMaxK2];
     __shared__ int8_t grp_t[kOzMaxSlices * kOzMaxSlices], grp_u[kOzMaxSlices * kOzMaxSlices];
-    __shared__ int grp_start[2 * kOzMaxSlices + 2], grp_shift[2 * kOzMaxSlices + 2];
+    __shared__ int grp_start[GZ_MAXGROUPS + 1], grp_shift[GZ_MAXGROUPS];
     __shared__ int s_ngroups, s_abort;
 
     const int32_t *pd = pairs + 4 * blockIdx.y;
@@ -248,20 +263,37 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
     const int64_t row0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t row1 = min((int64_t)m, row0 + rows_per_block);
 
-    // group table: diagonals d = 2..s+1, products (t, u) with t + u = d
+    // Group table. X^T X is symmetric, so with P_tu = A_t^T A_u = P_ut^T only the
+    // products t <= u are formed: off-diagonal ones (t < u) with twice their
+    // weight, squares (t = t) with their weight; the result acc satisfies
+    // acc + acc^T = 2 C exactly. Products of one weight share a TMEM group of at
+    // most GZ_GMAX products, which keeps every fp32 group sum an exact integer
+    // below 2^22 (GZ_GMAX * 64 * 127^2 < 2^22).
     if (tid == 0) {
         int g = 0, p = 0;
         for (int d = 2; d <= s + 1; ++d) {
-            grp_start[g] = p;
-            grp_shift[g] = kBeta * (s + 1 - d);
-            for (int t = 1; t <= s; ++t) {
+            int cnt = 0;
+            for (int t = 1; 2 * t < d; ++t) {
                 const int u = d - t;
-                if (u < 1 || u > s) continue;
+                if (u > s) continue;
+                if (cnt == 0) {
+                    grp_start[g] = p;
+                    grp_shift[g] = kBeta * (s + 1 - d) + 1;
+                    ++g;
+                }
                 grp_t[p] = (int8_t)t;
                 grp_u[p] = (int8_t)u;
                 ++p;
+                if (++cnt == GZ_GMAX) cnt = 0;
             }
-            ++g;
+            if ((d & 1) == 0 && d / 2 <= s) {
+                grp_start[g] = p;
+                grp_shift[g] = kBeta * (s + 1 - d);
+                ++g;
+                grp_t[p] = (int8_t)(d / 2);
+                grp_u[p] = (int8_t)(d / 2);
+                ++p;
+            }
         }
         grp_start[g] = p;
         s_ngroups = g;
@@ -292,11 +324,14 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
     const int quad = warp & 3, half = warp >> 2;
     const int orow = quad * 16 + lane;
     const bool owns = lane < 16 && orow < K2;
-    Acc128 acc[32];
+    // Accumulator of one output: w0 + w1 * 2^32 with signed 64-bit words; a group
+    // sum v (|v| < 2^22) of shift sh adds v * 2^(sh mod 32) to word sh / 32, so no
+    // carry is propagated until the end (each word stays below 2^60).
+    long long w0[32], w1[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-        acc[j].lo = 0ull;
-        acc[j].hi = 0;
+        w0[j] = 0;
+        w1[j] = 0;
     }
     uint32_t phase[2] = {0u, 0u};
     int issued = 0;  // groups issued over the whole block life (buffer = issued & 1)
@@ -335,10 +370,8 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
             const unsigned long long q0 = fixed63(x0, e), q1 = fixed63(x1, e);
             const bool n0 = x0 < 0.0, n1 = x1 < 0.0;
             const uint32_t off = sw128_off(a, lp * 2);
-            for (int t = 1; t <= s; ++t) {
-                const __half2 h = __halves2half2(digit(q0, n0, t), digit(q1, n1, t));
-                *reinterpret_cast<__half2 *>(sm + (t - 1) * GZ_SLICE_BYTES + off) = h;
-            }
+            for (int t = 1; t <= s; ++t)
+                *reinterpret_cast<__half2 *>(sm + (t - 1) * GZ_SLICE_BYTES + off) = digits2(q0, n0, q1, n1, t);
         }
         fence_async_smem();
         tc_fence_before();
@@ -358,17 +391,21 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
             tc_fence_after();
             if (!s_abort) {
                 const int sh = grp_shift[g];
+                const long long mul = 1ll << (sh & 31);
+                const bool hiw = sh >= 32;
 #pragma unroll
                 for (int j0 = 0; j0 < 32; j0 += 8) {
                     uint32_t v[8];
                     tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 64 + half * 32 + j0), v);
                     tmem_wait_ld();
-                    if (owns) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const long long iv = (long long)__float2ll_rn(__uint_as_float(v[j]));
-                            add128_shifted(acc[j0 + j], iv, sh);
-                        }
+                    for (int j = 0; j < 8; ++j) {
+                        // exact integer |f| < 2^22: f + 1.5*2^23 has f in its low mantissa bits
+                        const int iv = __float_as_int(__uint_as_float(v[j]) + 12582912.0f) - 0x4B400000;
+                        if (hiw)
+                            w1[j0 + j] += (long long)iv * mul;
+                        else
+                            w0[j0 + j] += (long long)iv * mul;
                     }
                 }
             }
@@ -392,10 +429,15 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
         for (int j = 0; j < 32; ++j) {
             const int b = half * 32 + j;
             if (b < K2) {
+                // T = w0 + w1 * 2^32 as (lo, hi)
+                const unsigned long long l1 = (unsigned long long)w1[j] << 32;
+                const long long h1 = w1[j] >> 32;
+                const unsigned long long lo = (unsigned long long)w0[j] + l1;
+                const long long hi = (w0[j] >> 63) + h1 + (lo < l1 ? 1 : 0);
                 unsigned long long *w = dst + ((size_t)b * k2max + orow) * 2;
-                const unsigned long long old = atomicAdd(w, acc[j].lo);
-                const unsigned long long carry = (old + acc[j].lo < old) ? 1ull : 0ull;
-                atomicAdd(w + 1, (unsigned long long)acc[j].hi + carry);
+                const unsigned long long old = atomicAdd(w, lo);
+                const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+                atomicAdd(w + 1, (unsigned long long)hi + carry);
             }
         }
     }
@@ -417,9 +459,16 @@ __global__ void __launch_bounds__(256) gram_fixed_to_double_kernel(
     if (idx >= k * k) return;
     const int a = idx % k, b = idx / k;
     const unsigned long long *P = acc + (size_t)blockIdx.y * k2max * k2max * 2;
+    // C_rc = (acc_rc + acc_cr) / 2 (exact: the sum is even, see the Gram kernel)
     auto ld128 = [&](int r, int c, unsigned long long &lo, long long &hi) {
-        lo = P[((size_t)c * k2max + r) * 2];
-        hi = (long long)P[((size_t)c * k2max + r) * 2 + 1];
+        const unsigned long long l1 = P[((size_t)c * k2max + r) * 2];
+        const long long h1 = (long long)P[((size_t)c * k2max + r) * 2 + 1];
+        const unsigned long long l2 = P[((size_t)r * k2max + c) * 2];
+        const long long h2 = (long long)P[((size_t)r * k2max + c) * 2 + 1];
+        const unsigned long long l = l1 + l2;
+        const long long h = h1 + h2 + (l < l1 ? 1 : 0);
+        lo = (l >> 1) | ((unsigned long long)h << 63);
+        hi = h >> 1;
     };
     auto add = [](unsigned long long &lo, long long &hi, unsigned long long lo2, long long hi2, bool sub) {
         if (sub) {  // negate (lo2, hi2)
@@ -461,11 +510,16 @@ __global__ void __launch_bounds__(256) gram_fixed_to_double_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Update: one block per (128-row tile, pair). A operand: digits of the rows of
-// X = [Xr Xi] (per-row exponent, computed here); B operand: digits of the
-// columns of W2 = [[Wr, Wi], [-Wi, Wr]] (per-column exponent). All diagonal
-// groups (s of them, N columns each) live in TMEM at once; one commit, one
-// drain into int64 fixed-point accumulators, then Y = acc * 2^(r_l + w_j - F).
+// Update: one block per (128-row tile, pair). Two-sided power-of-two scaling
+// keeps every entry's digits relative to a scale close to its own size:
+// X = [Xr Xi] = Xh D with D = diag(2^e_c) the column exponents of the pivot
+// columns, so Y = X W2 = Xh (D W2), W2 = [[Wr, Wi], [-Wi, Wr]].
+// A operand: digits of the rows of Xh (per-row exponent r_l of the
+// column-normalized rows); B operand: digits of the columns of D W2 (per-column
+// exponent w_j). Both scalings are exact (exponent shifts of the digit
+// extraction). All diagonal groups (s of them, N columns each) live in TMEM
+// at once; one commit, one drain into int64 fixed-point accumulators, then
+// Y = acc * 2^(r_l + w_j - F).
 // ---------------------------------------------------------------------------
 constexpr int UZ_THREADS = 256;
 constexpr int UZ_M = 128;
@@ -476,8 +530,8 @@ constexpr int UZ_F = 56;                    // fixed-point fraction bits of the 
 template <bool CPLX>
 __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
     const double *__restrict__ Gs, double *__restrict__ Gd, int64_t ld, int64_t m,
-    const int32_t *__restrict__ pairs, const double *__restrict__ Wb, int kmax, int slices,
-    unsigned long long *__restrict__ counters) {
+    const int32_t *__restrict__ pairs, const double *__restrict__ Wb, int kmax,
+    const int32_t *__restrict__ cexp, int slices, unsigned long long *__restrict__ counters) {
     extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = sm;                               // slices x 128 x 128 B
@@ -486,7 +540,8 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
     __shared__ uint32_t tmem_base_sh;
     __shared__ int rexp[UZ_M];
     __shared__ int wexp[kOzMaxK2];
-    __shared__ unsigned long long rmax_sh[UZ_M];
+    __shared__ int xexp[kOzMaxK2];  // column exponents e_a of the K2 real columns of X
+    __shared__ int rmax_sh[UZ_M];
     __shared__ int s_abort;
 
     const int32_t *pd = pairs + 4 * blockIdx.y;
@@ -529,43 +584,51 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
     // zero operand tiles (padding rows/columns must be zero)
     for (int i = tid; i < s * (UZ_ASLICE + UZ_BSLICE) / 16; i += UZ_THREADS)
         reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
-    // column exponents of W2 (the same for j and j + k in the complex form)
+    for (int a = tid; a < K2; a += UZ_THREADS) {
+        const int c = CPLX ? (a < k ? a : a - k) : a;
+        xexp[a] = cexp[gcol(c)];
+    }
+    __syncthreads();
+    // column exponents of D W2: max over a of (exponent of W2_aj) + e_a, from the
+    // exponent fields (a power-of-two product changes only the exponent)
     for (int j = warp; j < K2; j += UZ_THREADS / 32) {
-        unsigned long long mx = 0;
+        int mx = -100000;
         for (int a = lane; a < K2; a += 32) {
-            const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(w2val(a, j)));
-            mx = v > mx ? v : mx;
+            const double w = w2val(a, j);
+            if (w != 0.0) {
+                const int ew = exp_of_bits((unsigned long long)__double_as_longlong(fabs(w)));
+                mx = max(mx, ew + xexp[a]);
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
-            mx = t > mx ? t : mx;
-        }
-        if (lane == 0) wexp[j] = exp_of_bits(mx);
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) wexp[j] = mx == -100000 ? -1021 : mx;
     }
-    // row exponents of X: two threads per row (halves of the columns)
+    // row exponents of Xh = X D^-1: two threads per row (halves of the columns)
     {
         const int r = tid & (UZ_M - 1), hf = tid >> 7;
         const int64_t l = l0 + r;
-        unsigned long long mx = 0;
+        int mx = -100000;
         if (l < m)
             for (int a = hf; a < K2; a += 2) {
-                const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(xval(l, a)));
-                mx = v > mx ? v : mx;
+                const double x = xval(l, a);
+                if (x != 0.0)
+                    mx = max(mx, exp_of_bits((unsigned long long)__double_as_longlong(fabs(x))) - xexp[a]);
             }
         if (hf == 1) rmax_sh[r] = mx;
         __syncthreads();
         if (hf == 0) {
-            const unsigned long long o = rmax_sh[r];
-            rexp[r] = exp_of_bits(o > mx ? o : mx);
+            const int o = max(rmax_sh[r], mx);
+            rexp[r] = o == -100000 ? -1021 : o;
         }
     }
     __syncthreads();
-    // digits of W2 columns: B operand row j, K position a
+    // digits of the columns of D W2: B operand row j, K position a;
+    // (D W2)_aj < 2^w_j  <=>  W2_aj < 2^(w_j - e_a)
     for (int idx = tid; idx < K2 * K2; idx += UZ_THREADS) {
         const int a = idx % K2, j = idx / K2;
         const double x = w2val(a, j);
-        const unsigned long long q = fixed63(x, wexp[j]);
+        const unsigned long long q = fixed63(x, wexp[j] - xexp[a]);
         const uint32_t off = sw128_off(j, a * 2);
         for (int t = 1; t <= s; ++t)
             *reinterpret_cast<__half *>(sB + (t - 1) * UZ_BSLICE + off) = digit(q, x < 0.0, t);
@@ -576,7 +639,7 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
         const int r = idx % UZ_M, a = idx / UZ_M;
         const int64_t l = l0 + r;
         const double x = l < m ? xval(l, a) : 0.0;
-        const unsigned long long q = fixed63(x, rexp[r]);
+        const unsigned long long q = fixed63(x, rexp[r] + xexp[a]);  // Xh_la < 2^r_l
         const uint32_t off = sw128_off(r, a * 2);
         for (int t = 1; t <= s; ++t)
             *reinterpret_cast<__half *>(sA + (t - 1) * UZ_ASLICE + off) = digit(q, x < 0.0, t);
@@ -629,7 +692,7 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const long long iv = __float2ll_rn(__uint_as_float(v[j]));
+                    const long long iv = (long long)__float2int_rn(__uint_as_float(v[j]));
                     if (sh >= 0)
                         acc[j0 + j] += iv << sh;
                     else
@@ -642,7 +705,7 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
             for (int j = 0; j < 32; ++j) {
                 const int jj = jbase + j;
                 if (jj < K2) {
-                    const double y = ldexp((double)acc[j], rexp[r] + wexp[jj] - UZ_F);
+                    const double y = int_scaled_to_double(acc[j], rexp[r] + wexp[jj] - UZ_F);
                     if (CPLX) {
                         const int c = jj < k ? jj : jj - k;
                         Gd[(gcol(c) * ld + l) * 2 + (jj < k ? 0 : 1)] = y;
@@ -723,7 +786,8 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
 
 cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
                                 const int32_t *pairs, int npairs, const double *W, int kmax,
-                                int slices, unsigned long long *counters, cudaStream_t st) {
+                                const int32_t *cexp, int slices, unsigned long long *counters,
+                                cudaStream_t st) {
     if (npairs <= 0) return cudaSuccess;
     const int k2max = cplx ? 2 * kmax : kmax;
     // all s diagonal groups of N <= 64 columns must fit the 512 TMEM columns
@@ -734,11 +798,11 @@ cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t
     if (cplx) {
         if ((e = set_smem(update_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
         update_ozaki_kernel<true><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
-                                                                   slices, counters);
+                                                                   cexp, slices, counters);
     } else {
         if ((e = set_smem(update_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
         update_ozaki_kernel<false><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
-                                                                    slices, counters);
+                                                                    cexp, slices, counters);
     }
     return cudaGetLastError();
 }

@@ -27,6 +27,7 @@ EXPORTS = [
     "jjacobi_solve_host", "jjacobi_solve_batched", "jjacobi_destroy",
     "jjacobi_status_string", "jjacobi_version", "jjacobi_schedule",
     "jjk_column_norms", "jjk_plain_step", "jjk_gram", "jjk_inner", "jjk_update", "jjk_extract",
+    "jjk_gram_noalloc",
 ]
 
 
@@ -88,6 +89,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "jjk_inner": (ctypes.c_int, [i32, vp, vp, i32, vp, i32, vp, dbl, i32, i32, vp, vp]),
         "jjk_update": (ctypes.c_int, [i32, i32, vp, vp, i64, i64, vp, i32, vp, i32, vp]),
         "jjk_extract": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, vp, vp, i64, vp]),
+        "jjk_gram_noalloc": (ctypes.c_int, [i32, vp, i64, i64, vp, i32, vp, i32, i64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,3 +257,9 @@ def jjk_update(dtype, gemm, Gs, Gd, ld, m, pairs, npairs, W, kmax, stream=None):
 def jjk_extract(dtype, G, ld, m, n, J, lam, U=None, ldu=0, stream=None):
     _check(load().jjk_extract(dtype, _ptr(G), ld, m, n, _ptr(J), _ptr(lam), _ptr(U), ldu,
                               _stream_ptr(stream)), "jjk_extract")
+
+
+def jjk_gram_noalloc(dtype, G, ld, m, pairs, npairs, A, kmax, ncols, stream=None):
+    """Digit-product Gram without allocation (scratch in a fixed device array)."""
+    _check(load().jjk_gram_noalloc(dtype, _ptr(G), ld, m, _ptr(pairs), npairs, _ptr(A), kmax,
+                                   ncols, _stream_ptr(stream)), "jjk_gram_noalloc")
