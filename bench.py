@@ -185,7 +185,7 @@ def src_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_breakdown(jj, torch, P, bw, gemm, stream, nsteps=8):
+def kernel_breakdown(jj, torch, P, bw, g_gram, g_upd, stream, nsteps=8):
     """Per-kernel device time of the first nsteps parallel steps, through the
     building-block entry points, timed with CUDA events on the launching stream."""
     import numpy as np
@@ -211,11 +211,11 @@ def kernel_breakdown(jj, torch, P, bw, gemm, stream, nsteps=8):
             pd = torch.from_numpy(pairs).cuda()
             stream.synchronize()
             ev[0].record(stream)
-            jj.jjk_gram(1, gemm, Gs, Gs.stride(1), m, pd, len(pairs), A, kmax, stream=stream)
+            jj.jjk_gram(1, g_gram, Gs, Gs.stride(1), m, pd, len(pairs), A, kmax, stream=stream)
             ev[1].record(stream)
             jj.jjk_inner(1, A, W, kmax, pd, len(pairs), Jd, 0.0, 30, 0, cnt, stream=stream)
             ev[2].record(stream)
-            jj.jjk_update(1, gemm, Gs, Gd, Gs.stride(1), m, pd, len(pairs), W, kmax, stream=stream)
+            jj.jjk_update(1, g_upd, Gs, Gd, Gs.stride(1), m, pd, len(pairs), W, kmax, stream=stream)
             ev[3].record(stream)
             stream.synchronize()
             t["gram"] += ev[0].elapsed_time(ev[1])
@@ -248,7 +248,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     P = synth.make_workload(WORKLOAD, precision="f64")
     n, m = P.n, P.m
-    gemm = jj.JJ_GEMM_OZAKI_FP16 if args.gemm == "ozaki" else jj.JJ_GEMM_FP64
+    gemm = {"ozaki": jj.JJ_GEMM_OZAKI_FP16, "hybrid": jj.JJ_GEMM_OZAKI_GRAM,
+            "fp64": jj.JJ_GEMM_FP64}[args.gemm]
+    g_gram = jj.JJ_GEMM_FP64 if gemm == jj.JJ_GEMM_FP64 else jj.JJ_GEMM_OZAKI_FP16
+    g_upd = jj.JJ_GEMM_OZAKI_FP16 if gemm == jj.JJ_GEMM_OZAKI_FP16 else jj.JJ_GEMM_FP64
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         G0 = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()  # column-major
@@ -302,7 +305,7 @@ def run_ours(args):
            "h2d_bytes_per_step": int(m * n * 16), "d2h_bytes_per_step": int(n * 8)}
 
     # per-kernel breakdown and roofline of the dominant kernel
-    per, geo = kernel_breakdown(jj, torch, P, args.block_width, gemm, stream)
+    per, geo = kernel_breakdown(jj, torch, P, args.block_width, g_gram, g_upd, stream)
     dom = max(per, key=per.get)
     peaks = _peaks()
     cplx_mac = 8.0
@@ -315,7 +318,7 @@ def run_ours(args):
                 "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 x 2070 MHz (derived)"}
     else:
         tflops_fp16 = peaks.get("bf16_tflops", 1900.0)
-        if gemm == jj.JJ_GEMM_OZAKI_FP16:
+        if (dom == "gram" and g_gram == jj.JJ_GEMM_OZAKI_FP16) or (dom == "update" and g_upd == jj.JJ_GEMM_OZAKI_FP16):
             # executed fp16 tensor flops: digit products x real GEMM size
             s_g, s_u = 9, 8
             if dom == "gram":
@@ -402,7 +405,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-width", type=int, default=16)
-    ap.add_argument("--gemm", default="ozaki", choices=["ozaki", "fp64"])
+    ap.add_argument("--gemm", default="hybrid", choices=["hybrid", "ozaki", "fp64"])
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=6.0)

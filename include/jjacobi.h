@@ -55,9 +55,22 @@ typedef enum { JJ_F64 = 0, JJ_C128 = 1 } jj_dtype;
 typedef enum { JJ_ORDER_ROUND_ROBIN = 0, JJ_ORDER_MODULUS = 1 } jj_order;
 
 /* How the blocked form computes its two dense contractions (Gram (3.6) and
- * update (2.9)): FP64 on the FP64 pipe, or split into exact fp16 slices on the
- * tensor cores (tcgen05) with fp32 accumulation and FP64 recombination. */
-typedef enum { JJ_GEMM_FP64 = 0, JJ_GEMM_OZAKI_FP16 = 1, JJ_GEMM_AUTO = 3 } jj_gemm;
+ * update (2.9)):
+ *   JJ_GEMM_FP64        both on the FP64 pipe;
+ *   JJ_GEMM_OZAKI_FP16  both as sums of exact fp16 digit products on the
+ *                       tensor cores (tcgen05), recombined in integers;
+ *   JJ_GEMM_OZAKI_GRAM  the Gram as digit products, the update in FP64: the
+ *                       digit update carries a shared exponent along each row,
+ *                       which loses relative accuracy on entries far below
+ *                       their row's largest (strongly graded inputs);
+ *   JJ_GEMM_AUTO        JJ_GEMM_OZAKI_GRAM when the pivot fits the digit
+ *                       kernels (real pivot width <= 64), else FP64. */
+typedef enum {
+    JJ_GEMM_FP64 = 0,
+    JJ_GEMM_OZAKI_FP16 = 1,
+    JJ_GEMM_OZAKI_GRAM = 2,
+    JJ_GEMM_AUTO = 3
+} jj_gemm;
 
 typedef enum {
     JJ_OK = 0,

@@ -9,10 +9,11 @@ from __future__ import annotations
 
 from . import jjacobi
 from .jjacobi import (JJ_C128, JJ_F64, JJ_GEMM_AUTO, JJ_GEMM_FP64, JJ_GEMM_OZAKI_FP16,
+                      JJ_GEMM_OZAKI_GRAM,
                       JJ_ORDER_MODULUS, JJ_ORDER_ROUND_ROBIN, Handle, JJError)
 
 __all__ = ["jjacobi", "Handle", "JJError", "solve", "JJ_F64", "JJ_C128", "JJ_GEMM_FP64",
-           "JJ_GEMM_OZAKI_FP16", "JJ_GEMM_AUTO", "JJ_ORDER_ROUND_ROBIN", "JJ_ORDER_MODULUS"]
+           "JJ_GEMM_OZAKI_FP16", "JJ_GEMM_OZAKI_GRAM", "JJ_GEMM_AUTO", "JJ_ORDER_ROUND_ROBIN", "JJ_ORDER_MODULUS"]
 
 
 def solve(G, J, block_width: int = 0, want_vectors: bool = True, **kw):

@@ -29,7 +29,9 @@ struct jj_ctx {
     double *Gw[2] = {nullptr, nullptr};
     double *Ablk = nullptr, *Wblk = nullptr;
     double *d_norm = nullptr;
-    bool ozaki = false;                 // Gram and update on the tensor cores (fp16 digits)
+    bool ozaki = false;                 // Gram on the tensor cores (fp16 digits)
+    bool ozaki_update = false;          // update on the tensor cores too
+    int32_t *d_mod = nullptr, *d_clean = nullptr, *d_flags = nullptr, *d_sweep = nullptr;
     int oz_slices_gram = 9, oz_slices_update = 8;
     int32_t *d_cexp = nullptr;          // column exponents (Ozaki Gram)
     unsigned long long *d_ozacc = nullptr;  // int128 Gram accumulators
@@ -54,6 +56,8 @@ struct jj_ctx {
 };
 
 namespace {
+
+__global__ void sweep_begin_kernel(int32_t *sweep) { *sweep += 1; }
 
 #define JJ_CUDA(call)                                                                   \
     do {                                                                                \
@@ -84,6 +88,10 @@ void free_ctx(jj_ctx *c) {
     cudaFree(c->Wblk);
     cudaFree(c->d_cexp);
     cudaFree(c->d_ozacc);
+    cudaFree(c->d_mod);
+    cudaFree(c->d_clean);
+    cudaFree(c->d_flags);
+    cudaFree(c->d_sweep);
     cudaFree(c->d_norm);
     cudaFree(c->d_perm);
     cudaFree(c->d_rank);
@@ -115,30 +123,41 @@ int enqueue_sweep(jj_ctx *c, int start_buf, int *launches) {
             ++L;
         }
     } else {
+        sweep_begin_kernel<<<1, 1, 0, st>>>(c->d_sweep);
+        JJ_CUDA(cudaGetLastError());
+        ++L;
         int cur = start_buf;
         for (int t = 0; t < c->steps; ++t) {
             const int32_t *pr = c->d_pairs + (size_t)t * c->npairs * 4;
+            StepCtl ctl;
+            ctl.mod_step = c->d_mod;
+            ctl.clean_at = c->d_clean;
+            ctl.flags = c->d_flags;
+            ctl.sweep = c->d_sweep;
+            ctl.step = t;
+            ctl.steps = c->steps;
+            ctl.npairs = c->npairs;
             if (c->ozaki) {
                 JJ_CUDA(launch_colexp(c->cplx, c->Gw[cur], c->ldw, c->m, c->n, c->d_cexp, st));
                 JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw[cur], c->ldw, c->m, pr, c->npairs,
                                           c->Ablk, c->kmax, c->d_cexp, c->d_ozacc,
-                                          c->oz_slices_gram, c->d_cnt, st));
+                                          c->oz_slices_gram, c->d_cnt, st, ctl));
                 L += 3;
             } else {
                 JJ_CUDA(launch_gram(c->cplx, c->p.gemm, c->Gw[cur], c->ldw, c->m, pr, c->npairs,
-                                    c->Ablk, c->kmax, st));
+                                    c->Ablk, c->kmax, st, ctl));
                 L += 1;
             }
             JJ_CUDA(launch_inner(c->cplx, c->Ablk, c->Wblk, c->kmax, pr, c->npairs, c->d_Jw,
                                  c->tol, c->inner_max_sweeps, c->p.inner_block_width, c->d_cnt,
-                                 st));
-            if (c->ozaki)
+                                 st, ctl));
+            if (c->ozaki_update)
                 JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m, pr,
                                             c->npairs, c->Wblk, c->kmax, c->d_cexp,
-                                            c->oz_slices_update, c->d_cnt, st));
+                                            c->oz_slices_update, c->d_cnt, st, ctl));
             else
                 JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m,
-                                      pr, c->npairs, c->Wblk, c->kmax, st));
+                                      pr, c->npairs, c->Wblk, c->kmax, st, ctl));
             L += 2;
             cur ^= 1;
         }
@@ -223,7 +242,7 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
     if (!p || p->n < 1 || p->m < p->n || (p->dtype != JJ_F64 && p->dtype != JJ_C128) ||
         p->block_width < 0 || p->inner_block_width < 0 ||
         (p->order != JJ_ORDER_ROUND_ROBIN && p->order != JJ_ORDER_MODULUS) ||
-        (p->gemm != JJ_GEMM_FP64 && p->gemm != JJ_GEMM_OZAKI_FP16 && p->gemm != JJ_GEMM_AUTO) ||
+        (p->gemm < JJ_GEMM_FP64 || p->gemm > JJ_GEMM_AUTO) ||
         p->n > (int64_t)1 << 30)
         return JJ_INVALID_ARG;
     jj_ctx *c = new jj_ctx();
@@ -300,8 +319,16 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
         if (cudaMalloc(&c->Ablk, bb) != cudaSuccess) return fail(JJ_CUDA_ERROR);
         if (cudaMalloc(&c->Wblk, bb) != cudaSuccess) return fail(JJ_CUDA_ERROR);
         const bool oz_ok = ozaki_supported(c->cplx, c->kmax);
-        if (p->gemm == JJ_GEMM_OZAKI_FP16 && !oz_ok) return fail(JJ_INVALID_ARG);
-        c->ozaki = oz_ok && (p->gemm == JJ_GEMM_OZAKI_FP16 || p->gemm == JJ_GEMM_AUTO);
+        if ((p->gemm == JJ_GEMM_OZAKI_FP16 || p->gemm == JJ_GEMM_OZAKI_GRAM) && !oz_ok)
+            return fail(JJ_INVALID_ARG);
+        c->ozaki = oz_ok && p->gemm != JJ_GEMM_FP64;
+        c->ozaki_update = c->ozaki && p->gemm == JJ_GEMM_OZAKI_FP16;
+        const size_t nslots = (size_t)c->steps * c->npairs;
+        if (cudaMalloc(&c->d_mod, n * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&c->d_clean, nslots * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&c->d_flags, c->npairs * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&c->d_sweep, sizeof(int32_t)) != cudaSuccess)
+            return fail(JJ_CUDA_ERROR);
         if (c->ozaki) {
             if (p->ozaki_slices > 0) {
                 if (p->ozaki_slices > 9) return fail(JJ_INVALID_ARG);
@@ -376,6 +403,12 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
     JJ_CUDA(cudaMemcpyAsync(c->d_Jorig, J, n, cudaMemcpyHostToDevice, st));
     JJ_CUDA(launch_permute_columns(c->cplx, (const double *)G, ldg, c->Gw[0], c->ldw, c->m, n,
                                    c->d_perm, false, st));
+    if (c->blocked) {
+        JJ_CUDA(cudaMemsetAsync(c->d_mod, 0xFF, n * sizeof(int32_t), st));
+        JJ_CUDA(cudaMemsetAsync(c->d_clean, 0xFF, (size_t)c->steps * c->npairs * sizeof(int32_t), st));
+        JJ_CUDA(cudaMemsetAsync(c->d_flags, 0, c->npairs * sizeof(int32_t), st));
+        JJ_CUDA(cudaMemsetAsync(c->d_sweep, 0, sizeof(int32_t), st));
+    }
     int launches = 1;
     int cur = 0;
     int rc = JJ_NOT_CONVERGED;

@@ -26,11 +26,16 @@ constexpr int GKR = 16;  // rows of G staged per k-step
 template <bool CPLX>
 __global__ void __launch_bounds__(256) gram_fp64_kernel(const double *__restrict__ G, int64_t ld,
                                                          int64_t m, const int32_t *__restrict__ pairs,
-                                                         double *__restrict__ A, int kmax) {
+                                                         double *__restrict__ A, int kmax, StepCtl ctl) {
     constexpr int E = CPLX ? 2 : 1;
     __shared__ double xa[GKR][GT][E];
     __shared__ double xb[GKR][GT][E];
     const int32_t *pd = pairs + 4 * blockIdx.y;
+    if (ctl.mod_step) {
+        const bool skip = pair_skip_decide(ctl, pd, blockIdx.y);
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl.flags[blockIdx.y] = skip ? kPairSkipped : 0;
+        if (skip) return;
+    }
     const int k = pd[1] + pd[3];
     // map linear tile index to (ta, tb) with ta <= tb
     int t = blockIdx.x, ta = 0;
@@ -116,7 +121,8 @@ template <bool CPLX>
 __global__ void __launch_bounds__(256) update_fp64_kernel(const double *__restrict__ Gs,
                                                            double *__restrict__ Gd, int64_t ld,
                                                            int64_t m, const int32_t *__restrict__ pairs,
-                                                           const double *__restrict__ W, int kmax) {
+                                                           const double *__restrict__ W, int kmax,
+                                                           StepCtl ctl) {
     constexpr int E = CPLX ? 2 : 1;
     __shared__ double xs[UK][UR][E];
     __shared__ double ws[UK][UC][E];
@@ -125,6 +131,10 @@ __global__ void __launch_bounds__(256) update_fp64_kernel(const double *__restri
     const int b0 = blockIdx.y * UC;
     if (b0 >= k) return;
     const int64_t l0 = (int64_t)blockIdx.x * UR;
+    if (pair_passthrough(ctl, blockIdx.z)) {
+        pair_copy_rows(CPLX, Gs, Gd, ld, pd, l0, min(m, l0 + UR), b0, min(k, b0 + UC), threadIdx.x, 256);
+        return;
+    }
     const double *Wp = W + (int64_t)blockIdx.z * kmax * kmax * E;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // outputs rows ty+16i (4), cols tx+16j (2)
     double acc[4][2][E];
@@ -223,8 +233,10 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
                                                     int kmax, const int32_t *__restrict__ pairs,
                                                     const int8_t *__restrict__ J, double tol,
                                                     int max_sweeps,
-                                                    unsigned long long *__restrict__ counters) {
+                                                    unsigned long long *__restrict__ counters,
+                                                    StepCtl ctl) {
     constexpr int E = CPLX ? 2 : 1;
+    if (ctl.flags && (ctl.flags[blockIdx.x] & kPairSkipped)) return;
     extern __shared__ double smem[];
     double *dsh = smem;                        // kmax tracked diagonal
     int *jsh = reinterpret_cast<int *>(dsh + kmax);  // kmax signs
@@ -285,7 +297,10 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
         __syncthreads();
     }
     if (s_fail) {
-        if (tid == 0) atomicOr(&counters[kCntErr], kErrNotPosdef);
+        if (tid == 0) {
+            atomicOr(&counters[kCntErr], kErrNotPosdef);
+            pair_record(ctl, pd, blockIdx.x, false, true);
+        }
         // leave W = I so that the update is the identity
         for (int64_t t = tid; t < (int64_t)k * k; t += IT) {
             const int a = (int)(t % k), b = (int)(t / k);
@@ -403,6 +418,7 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
         for (int w = 0; w < IT / 32; ++w) mo = fmax(mo, smax[w]);
         atomic_max_nonneg(&counters[kCntMaxOff], mo);
         if (total_rot) atomicAdd(&counters[kCntRot], total_rot);
+        pair_record(ctl, pd, blockIdx.x, total_rot > 0, false);
     }
 }
 
@@ -421,11 +437,12 @@ template <bool CPLX, int ROWS>
 __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double *__restrict__ A, double *__restrict__ Wb, int kmax, const int32_t *__restrict__ pairs,
     const int8_t *__restrict__ J, double tol, int max_sweeps,
-    unsigned long long *__restrict__ counters) {
+    unsigned long long *__restrict__ counters, StepCtl ctl) {
     constexpr int E = CPLX ? 2 : 1;
     extern __shared__ double2 smem4[];
     double *sm = reinterpret_cast<double *>(smem4);
     const int32_t *pd = pairs + 4 * blockIdx.x;
+    if (ctl.flags && (ctl.flags[blockIdx.x] & kPairSkipped)) return;
     const int k = pd[1] + pd[3];
     const int ldr = k;  // smem leading dimension (entries)
     double *R = sm;                              // k x k entries
@@ -491,7 +508,10 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double *Rg = A + (int64_t)blockIdx.x * kmax * kmax * E;
     double *Wg = Wb + (int64_t)blockIdx.x * kmax * kmax * E;
     if (s_fail) {
-        if (tid == 0) atomicOr(&counters[kCntErr], kErrNotPosdef);
+        if (tid == 0) {
+            atomicOr(&counters[kCntErr], kErrNotPosdef);
+            pair_record(ctl, pd, blockIdx.x, false, true);
+        }
         for (int t = tid; t < k * k; t += ST) {
             const int a = t % k, b = t / k;
             Wg[((int64_t)b * kmax + a) * E] = a == b ? 1.0 : 0.0;
@@ -680,6 +700,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         for (int w = 0; w < SW; ++w) mo = fmax(mo, s_max[w]);
         atomic_max_nonneg(&counters[kCntMaxOff], mo);
         if (total_rot) atomicAdd(&counters[kCntRot], total_rot);
+        pair_record(ctl, pd, blockIdx.x, total_rot > 0, false);
     }
 }
 
@@ -693,34 +714,35 @@ size_t inner_smem_bytes(bool cplx, int kmax) {
 
 cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_t m,
                         const int32_t *pairs, int npairs, double *A, int kmax,
-                        cudaStream_t st) {
+                        cudaStream_t st, StepCtl ctl) {
     (void)gemm;
     if (npairs <= 0) return cudaSuccess;
     const int T = (kmax + GT - 1) / GT;
     dim3 grid(T * (T + 1) / 2, npairs);
     if (cplx)
-        gram_fp64_kernel<true><<<grid, 256, 0, st>>>(G, ld, m, pairs, A, kmax);
+        gram_fp64_kernel<true><<<grid, 256, 0, st>>>(G, ld, m, pairs, A, kmax, ctl);
     else
-        gram_fp64_kernel<false><<<grid, 256, 0, st>>>(G, ld, m, pairs, A, kmax);
+        gram_fp64_kernel<false><<<grid, 256, 0, st>>>(G, ld, m, pairs, A, kmax, ctl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int64_t ld,
                           int64_t m, const int32_t *pairs, int npairs, const double *W,
-                          int kmax, cudaStream_t st) {
+                          int kmax, cudaStream_t st, StepCtl ctl) {
     (void)gemm;
     if (npairs <= 0) return cudaSuccess;
     dim3 grid((unsigned)((m + UR - 1) / UR), (kmax + UC - 1) / UC, npairs);
     if (cplx)
-        update_fp64_kernel<true><<<grid, 256, 0, st>>>(Gs, Gd, ld, m, pairs, W, kmax);
+        update_fp64_kernel<true><<<grid, 256, 0, st>>>(Gs, Gd, ld, m, pairs, W, kmax, ctl);
     else
-        update_fp64_kernel<false><<<grid, 256, 0, st>>>(Gs, Gd, ld, m, pairs, W, kmax);
+        update_fp64_kernel<false><<<grid, 256, 0, st>>>(Gs, Gd, ld, m, pairs, W, kmax, ctl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
                          int npairs, const int8_t *J, double tol, int inner_max_sweeps,
-                         int inner_block, unsigned long long *counters, cudaStream_t st) {
+                         int inner_block, unsigned long long *counters, cudaStream_t st,
+                         StepCtl ctl) {
     (void)inner_block;
     if (npairs <= 0) return cudaSuccess;
     // Shared-memory resident form when R and W fit (227 KB per block).
@@ -732,7 +754,7 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)smb);                                       \
         if (e != cudaSuccess) return e;                                                       \
-        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters); \
+        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl); \
         return cudaGetLastError();                                                            \
     } while (0)
         const int rows = (kmax + 31) / 32;
@@ -750,9 +772,9 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
     }
     const size_t sh = (size_t)kmax * sizeof(double) + (size_t)kmax * sizeof(int);
     if (cplx)
-        inner_kernel<true><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters);
+        inner_kernel<true><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl);
     else
-        inner_kernel<false><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters);
+        inner_kernel<false><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl);
     return cudaGetLastError();
 }
 

@@ -98,6 +98,51 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, doub
     atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
+// Skipping unchanged pivot pairs. A pair (i, j) whose two blocks have not
+// changed since the pair was last found diagonal (its inner solve applied no
+// rotation) would produce the same Gram and again no rotation: the kernels are
+// deterministic (the split-precision Gram adds exact integers), so skipping it
+// is exact. Stamps are global step indices T = sweep * steps + step.
+struct StepCtl {
+    int32_t *mod_step = nullptr;      // [n]: by block start column, step of the last change (-1: never)
+    int32_t *clean_at = nullptr;      // [steps * npairs]: step when the slot was found clean (-1: not)
+    int32_t *flags = nullptr;         // [npairs]: bit 0 skipped, bit 1 identity (no rotation)
+    const int32_t *sweep = nullptr;   // device sweep counter (1 in the first sweep)
+    int step = 0;                     // position of this step in the sweep
+    int steps = 0;                    // steps per sweep
+    int npairs = 0;                   // pairs per step
+};
+constexpr int kPairSkipped = 1;
+constexpr int kPairIdentity = 2;
+
+// Decide (Gram kernels) whether pair q of this step can be skipped: the slot was
+// found clean at step `clean` and neither block changed after it.
+__device__ __forceinline__ bool pair_skip_decide(const StepCtl &c, const int32_t *pd, int q) {
+    if (!c.mod_step) return false;
+    const int clean = c.clean_at[c.step * c.npairs + q];
+    return clean >= 0 && c.mod_step[pd[0]] < clean && c.mod_step[pd[2]] < clean;
+}
+
+// Bookkeeping after the inner solve of pair q (one thread).
+__device__ __forceinline__ void pair_record(const StepCtl &c, const int32_t *pd, int q,
+                                            bool rotated, bool failed) {
+    if (!c.mod_step) return;
+    const int T = (*c.sweep) * c.steps + c.step;
+    if (rotated) {
+        c.mod_step[pd[0]] = T;
+        c.mod_step[pd[2]] = T;
+        c.clean_at[c.step * c.npairs + q] = -1;
+        c.flags[q] = 0;
+    } else {
+        c.clean_at[c.step * c.npairs + q] = failed ? -1 : T;
+        c.flags[q] = kPairIdentity;
+    }
+}
+
+__device__ __forceinline__ bool pair_passthrough(const StepCtl &c, int q) {
+    return c.flags && (c.flags[q] & (kPairSkipped | kPairIdentity));
+}
+
 // ---------------------------------------------------------------------------
 // Launchers (host functions, defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -116,13 +161,14 @@ cudaError_t launch_permute_columns(bool cplx, const double *A, int64_t lda, doub
 
 cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_t m,
                         const int32_t *pairs, int npairs, double *A, int kmax,
-                        cudaStream_t st);
+                        cudaStream_t st, StepCtl ctl = StepCtl());
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
                          int npairs, const int8_t *J, double tol, int inner_max_sweeps,
-                         int inner_block, unsigned long long *counters, cudaStream_t st);
+                         int inner_block, unsigned long long *counters, cudaStream_t st,
+                         StepCtl ctl = StepCtl());
 cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int64_t ld,
                           int64_t m, const int32_t *pairs, int npairs, const double *W,
-                          int kmax, cudaStream_t st);
+                          int kmax, cudaStream_t st, StepCtl ctl = StepCtl());
 
 // Split-precision (fp16 digit) forms on the tensor cores (jj_ozaki.cu).
 int ozaki_default_slices(bool gram);
@@ -133,12 +179,29 @@ cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int
 cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
                               const int32_t *pairs, int npairs, double *A, int kmax,
                               const int32_t *cexp, unsigned long long *acc, int slices,
-                              unsigned long long *counters, cudaStream_t st);
+                              unsigned long long *counters, cudaStream_t st,
+                              StepCtl ctl = StepCtl());
 // cexp: column exponents of Gs (launch_colexp), used for the two-sided scaling.
 cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
                                 const int32_t *pairs, int npairs, const double *W, int kmax,
                                 const int32_t *cexp, int slices, unsigned long long *counters,
-                                cudaStream_t st);
+                                cudaStream_t st, StepCtl ctl = StepCtl());
+// Copy the pivot columns of one pair, rows [l0, l1), from Gs to Gd (pass-through).
+__device__ __forceinline__ void pair_copy_rows(bool cplx, const double *Gs, double *Gd, int64_t ld,
+                                               const int32_t *pd, int64_t l0, int64_t l1,
+                                               int c0, int c1, int tid, int nthreads) {
+    const int nc = c1 - c0;
+    const int64_t nr = l1 - l0;
+    for (int64_t t = tid; t < nr * nc; t += nthreads) {
+        const int a = c0 + (int)(t / nr);
+        const int64_t l = l0 + t % nr;
+        const int64_t col = a < pd[1] ? (int64_t)pd[0] + a : (int64_t)pd[2] + (a - pd[1]);
+        if (cplx)
+            reinterpret_cast<double2 *>(Gd)[col * ld + l] = reinterpret_cast<const double2 *>(Gs)[col * ld + l];
+        else
+            Gd[col * ld + l] = Gs[col * ld + l];
+    }
+}
 
 // Host-side ordering tables (jj_schedule.cpp).
 int schedule_pairs(int nbl, int order, int sweep, int32_t *pairs);

@@ -244,7 +244,7 @@ template <bool CPLX>
 __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
     const double *__restrict__ G, int64_t ld, int64_t m, const int32_t *__restrict__ pairs,
     const int32_t *__restrict__ cexp, unsigned long long *__restrict__ acc_out, int k2max,
-    int slices, int rows_per_block, unsigned long long *__restrict__ counters) {
+    int slices, int rows_per_block, unsigned long long *__restrict__ counters, StepCtl ctl) {
     extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) unsigned long long bar_full[2];
@@ -255,6 +255,11 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
     __shared__ int s_ngroups, s_abort;
 
     const int32_t *pd = pairs + 4 * blockIdx.y;
+    if (ctl.mod_step) {
+        const bool skip = pair_skip_decide(ctl, pd, blockIdx.y);
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl.flags[blockIdx.y] = skip ? kPairSkipped : 0;
+        if (skip) return;
+    }
     const int k = pd[1] + pd[3];
     const int K2 = CPLX ? 2 * k : k;
     const int NP = (K2 + 15) & ~15;  // N of the MMA (multiple of 16)
@@ -531,7 +536,8 @@ template <bool CPLX>
 __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
     const double *__restrict__ Gs, double *__restrict__ Gd, int64_t ld, int64_t m,
     const int32_t *__restrict__ pairs, const double *__restrict__ Wb, int kmax,
-    const int32_t *__restrict__ cexp, int slices, unsigned long long *__restrict__ counters) {
+    const int32_t *__restrict__ cexp, int slices, unsigned long long *__restrict__ counters,
+    StepCtl ctl) {
     extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = sm;                               // slices x 128 x 128 B
@@ -546,6 +552,11 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
 
     const int32_t *pd = pairs + 4 * blockIdx.y;
     const int k = pd[1] + pd[3];
+    if (pair_passthrough(ctl, blockIdx.y)) {
+        const int64_t r0 = (int64_t)blockIdx.x * UZ_M;
+        pair_copy_rows(CPLX, Gs, Gd, ld, pd, r0, min(m, r0 + UZ_M), 0, k, threadIdx.x, UZ_THREADS);
+        return;
+    }
     const int K2 = CPLX ? 2 * k : k;
     const int NP = (K2 + 15) & ~15;
     const int KP = NP;  // K of the MMA (K2 padded to 16)
@@ -755,7 +766,7 @@ cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int
 cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
                               const int32_t *pairs, int npairs, double *A, int kmax,
                               const int32_t *cexp, unsigned long long *acc, int slices,
-                              unsigned long long *counters, cudaStream_t st) {
+                              unsigned long long *counters, cudaStream_t st, StepCtl ctl) {
     if (npairs <= 0) return cudaSuccess;
     const int k2max = cplx ? 2 * kmax : kmax;
     if (k2max > kOzMaxK2 || slices < 1 || slices > kOzMaxSlices) return cudaErrorInvalidValue;
@@ -769,11 +780,11 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
     if (cplx) {
         if ((e = set_smem(gram_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
         gram_ozaki_kernel<true><<<grid, GZ_THREADS, smem, st>>>(G, ld, m, pairs, cexp, acc, k2max,
-                                                                 slices, rpb, counters);
+                                                                 slices, rpb, counters, ctl);
     } else {
         if ((e = set_smem(gram_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
         gram_ozaki_kernel<false><<<grid, GZ_THREADS, smem, st>>>(G, ld, m, pairs, cexp, acc, k2max,
-                                                                  slices, rpb, counters);
+                                                                  slices, rpb, counters, ctl);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 g2((unsigned)((kmax * kmax + 255) / 256), npairs);
@@ -787,7 +798,7 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
 cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
                                 const int32_t *pairs, int npairs, const double *W, int kmax,
                                 const int32_t *cexp, int slices, unsigned long long *counters,
-                                cudaStream_t st) {
+                                cudaStream_t st, StepCtl ctl) {
     if (npairs <= 0) return cudaSuccess;
     const int k2max = cplx ? 2 * kmax : kmax;
     // all s diagonal groups of N <= 64 columns must fit the 512 TMEM columns
@@ -798,11 +809,11 @@ cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t
     if (cplx) {
         if ((e = set_smem(update_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
         update_ozaki_kernel<true><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
-                                                                   cexp, slices, counters);
+                                                                   cexp, slices, counters, ctl);
     } else {
         if ((e = set_smem(update_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
         update_ozaki_kernel<false><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
-                                                                    cexp, slices, counters);
+                                                                    cexp, slices, counters, ctl);
     }
     return cudaGetLastError();
 }
