@@ -141,7 +141,7 @@ def cpu_baseline(P, budget_s: float = 15.0):
         t0 = time.perf_counter()
         oracle.solve_plain(Gs, P.J[:ncol], max_sweeps=1)
         dt = time.perf_counter() - t0
-        fl = plain_flops(ncol, P.m, True, 1) * 1.0
+        fl = plain_flops(ncol, P.m, P.is_complex, 1) * 1.0
         best = (fl / dt / 1e9, ncol, dt)
         if dt > budget_s / 3 or ncol >= P.n:
             break
@@ -155,7 +155,7 @@ def run_reference(args):
         return
     import synth
 
-    P = synth.make_workload(WORKLOAD, precision="f64")
+    P = synth.make_workload(args.workload, precision="f64")
     vals = []
     for i in range(args.warmup + args.steps):
         g, ncol, dt = cpu_baseline(P, budget_s=args.ref_budget)
@@ -167,10 +167,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.median(x[2] for x in vals) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": P.n, "m": P.m, "form": "plain oracle sample"},
+        "config": {"workload": args.workload, "n": P.n, "m": P.m, "form": "plain oracle sample"},
         "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                          "sample": f"one row-cyclic plain sweep on the leading {vals[0][1]} "
-                                   f"columns (all {P.m} rows) of the n={P.n} graded input"},
+                                   f"columns (all {P.m} rows) of the n={P.n} input"},
         "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -185,47 +185,59 @@ def src_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_breakdown(jj, torch, P, bw, g_gram, g_upd, stream, nsteps=8):
-    """Per-kernel device time of the first nsteps parallel steps, through the
-    building-block entry points, timed with CUDA events on the launching stream."""
-    import numpy as np
+def gram_products(s: int) -> int:
+    """Digit products of the split-precision Gram (t + u <= s + 1)."""
+    return sum(1 for d in range(2, s + 2) for t in range(1, s + 1) if 1 <= d - t <= s)
 
-    n, m = P.n, P.m
-    nbl = 2 * ((n + 2 * bw - 1) // (2 * bw))
-    sizes = [n // nbl + (1 if l < n % nbl else 0) for l in range(nbl)]
-    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
-    tab = jj.jjacobi_schedule(nbl, 0, 1)
-    kmax = 2 * max(sizes)
-    with torch.cuda.stream(stream):
-        Gs = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()
-        Gd = torch.zeros_like(Gs)
-        A = torch.zeros(nbl // 2 * kmax * kmax * 2, dtype=torch.float64, device="cuda")
-        W = torch.zeros_like(A)
-        Jd = torch.from_numpy(P.J.astype(np.int8)).cuda()
-        cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        t = {"gram": 0.0, "inner": 0.0, "update": 0.0}
-        for s in range(min(nsteps, len(tab))):
-            pairs = np.array([[offs[i], sizes[i], offs[j], sizes[j]] for i, j in tab[s]],
-                             dtype=np.int32)
-            pd = torch.from_numpy(pairs).cuda()
-            stream.synchronize()
-            ev[0].record(stream)
-            jj.jjk_gram(1, g_gram, Gs, Gs.stride(1), m, pd, len(pairs), A, kmax, stream=stream)
-            ev[1].record(stream)
-            jj.jjk_inner(1, A, W, kmax, pd, len(pairs), Jd, 0.0, 30, 0, cnt, stream=stream)
-            ev[2].record(stream)
-            jj.jjk_update(1, g_upd, Gs, Gd, Gs.stride(1), m, pd, len(pairs), W, kmax, stream=stream)
-            ev[3].record(stream)
-            stream.synchronize()
-            t["gram"] += ev[0].elapsed_time(ev[1])
-            t["inner"] += ev[1].elapsed_time(ev[2])
-            t["update"] += ev[2].elapsed_time(ev[3])
-            Gs, Gd = Gd, Gs
-        steps = min(nsteps, len(tab))
-        rot = int(cnt[0])
-    per = {k: v / steps for k, v in t.items()}
-    return per, dict(npairs=nbl // 2, k=kmax, m=m, steps=steps, rotations=rot)
+
+def update_products(s: int) -> int:
+    return sum(1 for d in range(2, s + 2) for t in range(1, s + 1) if 1 <= d - t <= s)
+
+
+def kernel_roofline(jj, P, times, info, gemm_gram_digits, gemm_upd_digits, peaks):
+    """Achieved rate of the dominant kernel family over a profiled solve.
+
+    Work counted (algorithmic, per family, summed over the solve):
+      gram   digit form: products x 2 K2^2 m tensor flops per evaluated pair;
+             FP64 form: Hermitian half k(k+1)/2 m MACs per evaluated pair;
+      inner  5 k MACs per applied rotation plus k^3/3 MACs (Cholesky) per pair;
+      update digit form: products x 2 m K2^2 tensor flops per rotated pair;
+             FP64 form: m k^2 MACs per rotated pair.
+    """
+    cplx = P.is_complex
+    mac = 8.0 if cplx else 2.0
+    m = P.m
+    k = 2.0 * P.n / info["nbl"]
+    K2 = 2 * k if cplx else k
+    fam = {f: times[f] for f in ("gram", "inner", "update")}
+    dom = max(fam, key=lambda f: fam[f][0])
+    ms, launches = fam[dom]
+    if dom == "gram":
+        if gemm_gram_digits:
+            work = info["pairs_evaluated"] * gram_products(8) * 2.0 * K2 * K2 * m
+            bound, peak, unit, name = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", "gram_ozaki_kernel"
+        else:
+            work = info["pairs_evaluated"] * k * (k + 1) / 2 * m * mac
+            bound, peak, unit, name = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "gram_fp64_kernel"
+    elif dom == "inner":
+        work = info["rotations"] * 5.0 * k * mac + info["pairs_evaluated"] * k ** 3 / 3 * mac
+        bound, peak, unit, name = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "inner_smem_kernel"
+    else:
+        if gemm_upd_digits:
+            work = info["pairs_rotated"] * update_products(8) * 2.0 * m * K2 * K2
+            bound, peak, unit, name = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", "update_ozaki_kernel"
+        else:
+            work = info["pairs_rotated"] * m * k * k * mac
+            bound, peak, unit, name = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "update_fp64_kernel"
+    achieved = work / (ms * 1e-3) / 1e12
+    roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak,
+            "peak_source": ("measured bf16 burst of MEASURED_PEAKS.json (fp16 has the same dense rate)"
+                            if bound == "tensor" else
+                            "FP64: 152 SMs x 2 FMA/clk/SM x 2 flops x 2070 MHz (derived; 1.19 measured)"),
+            "ms_per_launch": ms / max(launches, 1), "launches": launches,
+            "family_ms": {f: fam[f][0] for f in fam}}
+    return roof
 
 
 def run_ours(args):
@@ -246,8 +258,10 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    P = synth.make_workload(WORKLOAD, precision="f64")
+    P = synth.make_workload(args.workload, precision="f64")
     n, m = P.n, P.m
+    cplx = P.is_complex
+    dt_code = jj.JJ_C128 if cplx else jj.JJ_F64
     gemm = {"ozaki": jj.JJ_GEMM_OZAKI_FP16, "hybrid": jj.JJ_GEMM_OZAKI_GRAM,
             "fp64": jj.JJ_GEMM_FP64}[args.gemm]
     g_gram = jj.JJ_GEMM_FP64 if gemm == jj.JJ_GEMM_FP64 else jj.JJ_GEMM_OZAKI_FP16
@@ -257,7 +271,7 @@ def run_ours(args):
         G0 = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()  # column-major
         Gw = torch.empty_like(G0)
         lam = torch.empty(n, dtype=torch.float64, device="cuda")
-    h = jj.Handle(m, n, jj.JJ_C128, block_width=args.block_width, gemm=gemm, stream=stream)
+    h = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream)
 
     def step():
         Gw.copy_(G0)
@@ -289,55 +303,34 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     info = infos[-1]
-    flops = blocked_flops(n, m, True, info)
+    flops = blocked_flops(n, m, cplx, info)
     value = flops * world / (ms * 1e-3) / 1e9
     launches = sum(x["kernel_launches"] + 1 for x in infos)  # + extraction kernel
     lam_blocked = lam.cpu().numpy().copy()
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     Gh = torch.from_numpy(np.ascontiguousarray(P.G.T)).pin_memory().numpy().T
+    esz = 16 if cplx else 8
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
         lam_h, _, _ = h.jjacobi_solve_host(Gh, P.J, want_U=False)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = {"value": flops / e2e_s / 1e9, "unit": "GFLOP/s",
-           "h2d_bytes_per_step": int(m * n * 16), "d2h_bytes_per_step": int(n * 8)}
+           "h2d_bytes_per_step": int(m * n * esz), "d2h_bytes_per_step": int(n * 8)}
 
-    # per-kernel breakdown and roofline of the dominant kernel
-    per, geo = kernel_breakdown(jj, torch, P, args.block_width, g_gram, g_upd, stream)
-    dom = max(per, key=per.get)
-    peaks = _peaks()
-    cplx_mac = 8.0
-    npairs, k = geo["npairs"], geo["k"]
-    if dom == "inner":
-        rot_per_step = geo["rotations"] / geo["steps"]
-        achieved = rot_per_step * 5.0 * k * cplx_mac / (per["inner"] * 1e-3) / 1e12
-        roof = {"kernel": "inner_smem_kernel", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 x 2070 MHz (derived)"}
-    else:
-        tflops_fp16 = peaks.get("bf16_tflops", 1900.0)
-        if (dom == "gram" and g_gram == jj.JJ_GEMM_OZAKI_FP16) or (dom == "update" and g_upd == jj.JJ_GEMM_OZAKI_FP16):
-            # executed fp16 tensor flops: digit products x real GEMM size
-            s_g, s_u = 9, 8
-            if dom == "gram":
-                prods = sum(1 for d in range(2, s_g + 2) for t in range(1, s_g + 1)
-                            if 1 <= d - t <= s_g and t <= d - t)
-                fl = npairs * prods * 2.0 * 64 * 64 * m
-            else:
-                prods = sum(1 for d in range(2, s_u + 2) for t in range(1, s_u + 1) if 1 <= d - t <= s_u)
-                fl = npairs * prods * 2.0 * m * 64 * 64
-            achieved = fl / (per[dom] * 1e-3) / 1e12
-            roof = {"kernel": dom + "_ozaki_kernel", "bound": "tensor", "achieved": achieved,
-                    "peak": tflops_fp16, "unit": "TFLOP/s",
-                    "peak_source": "measured bf16 burst (fp16 has the same dense rate)"}
-        else:
-            fl = npairs * (k * (k + 1) / 2 * m if dom == "gram" else m * k * k) * cplx_mac
-            roof = {"kernel": dom + "_fp64_kernel", "bound": "alu",
-                    "achieved": fl / (per[dom] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "peak_source": "FP64 derived"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    # per-kernel device times from a profiled solve (events around every kernel
+    # family of every step, on the solve's stream) and the dominant kernel's roofline
+    hp_ = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
+                    profile=True)
+    with torch.cuda.stream(stream):
+        Gw.copy_(G0)
+        pinfo_ = hp_.jjacobi_solve(Gw, Gw.stride(1), P.J)
+    stream.synchronize()
+    times = hp_.jjacobi_kernel_times()
+    hp_.close()
+    roof = kernel_roofline(jj, P, times, pinfo_.as_dict(), g_gram == jj.JJ_GEMM_OZAKI_FP16,
+                           g_upd == jj.JJ_GEMM_OZAKI_FP16, _peaks())
     roof["traffic"] = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -347,13 +340,11 @@ def run_ours(args):
             roof["traffic"] = ent["bytes_per_launch"]
     except Exception:
         pass
-    roof["ms_per_launch"] = per[dom]
-    roof["kernel_ms_per_step"] = per
 
     # the plain form on the same input, same accuracy target
     plain = None
     if args.plain and rank == 0:
-        hp = jj.Handle(m, n, jj.JJ_C128, block_width=0, stream=stream)
+        hp = jj.Handle(m, n, dt_code, block_width=0, stream=stream)
         with torch.cuda.stream(stream):
             Gw.copy_(G0)
             ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -366,7 +357,7 @@ def run_ours(args):
         pi = pinfo.as_dict()
         rel = float(np.max(np.abs(np.sort(lam_blocked) - np.sort(lam_plain)) / np.abs(np.sort(lam_plain))))
         plain = {"time_to_solution_s": ep0.elapsed_time(ep1) / 1e3, "sweeps": pi["sweeps"],
-                 "gflops": plain_flops(n, m, True, pi["sweeps"]) / (ep0.elapsed_time(ep1) * 1e-3) / 1e9,
+                 "gflops": plain_flops(n, m, cplx, pi["sweeps"]) / (ep0.elapsed_time(ep1) * 1e-3) / 1e9,
                  "speedup_blocked_vs_plain": (ep0.elapsed_time(ep1)) / ms,
                  "max_rel_eig_diff_blocked_vs_plain": rel}
         hp.close()
@@ -377,14 +368,14 @@ def run_ours(args):
         g, ncol, dt = cpu_baseline(P, budget_s=15.0)
         cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"one row-cyclic plain sweep on the leading {ncol} columns (all {m} rows) "
-                         f"of the n={n} graded input, {dt:.1f} s"}
+                         f"of the n={n} input, {dt:.1f} s"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": m, "n": n, "block_width": args.block_width,
+            "config": {"workload": args.workload, "m": m, "n": n, "block_width": args.block_width,
                        "gemm": args.gemm, "order": "round_robin", "sweeps": info["sweeps"],
                        "steps_per_sweep": info["steps_per_sweep"],
                        "time_to_solution_s": ms / 1e3,
@@ -406,6 +397,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-width", type=int, default=16)
     ap.add_argument("--gemm", default="hybrid", choices=["hybrid", "ozaki", "fp64"])
+    ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=6.0)

@@ -93,11 +93,14 @@ typedef struct {
     int32_t inner_block_width; /* 0: two-level; >0: inner block width (three-level) */
     int32_t order;             /* jj_order (blocked form; the plain form is round-robin) */
     int32_t gemm;              /* jj_gemm */
-    int32_t ozaki_slices;      /* 0: automatic */
+    int32_t ozaki_slices;      /* digits of the split-precision update, 0: 8 (at most 512/N) */
     double tol;                /* <= 0: 128 * 2^-53; rotate when |a_rs| > tol sqrt(a_rr a_ss) */
     int32_t max_sweeps;        /* <= 0: 60 */
     int32_t inner_max_sweeps;  /* <= 0: 30 (inner J-Jacobi on R, blocked form) */
     void *cuda_stream;         /* cudaStream_t to run on; NULL: the legacy default stream */
+    int32_t profile;           /* 1: time every kernel family of every step with CUDA events
+                                  (sweeps then run without graph capture); see
+                                  jjacobi_kernel_times */
 } jj_params;
 
 typedef struct {
@@ -110,6 +113,9 @@ typedef struct {
     int32_t nbl;               /* number of blocks (2 x pairs per step), 0 for plain */
     int32_t steps_per_sweep;   /* parallel steps per sweep */
     int32_t kernel_launches;   /* kernels launched by the call */
+    int64_t pairs_evaluated;   /* pivot pairs whose Gram and inner solve ran (blocked form;
+                                  the others were skipped as unchanged) */
+    int64_t pairs_rotated;     /* pivot pairs whose inner solve applied a rotation */
 } jj_info;
 
 /* Fill *p with defaults for an m x n problem of the given dtype (plain form). */
@@ -158,6 +164,14 @@ void jjacobi_destroy(jj_handle h);
 
 /* Human-readable name of a jj_status value. */
 const char *jjacobi_status_string(int status);
+
+/* Device time spent by kernel family in all solves of this handle since its
+ * creation, measured with CUDA events on the handle's stream when the handle
+ * was created with profile = 1 (zeros otherwise). times_ms (host, 8 doubles):
+ * [0] column exponents + Gram (3.6), [1] Cholesky + inner J-Jacobi (3.12),
+ * [2] update (2.9), [3] plain pair steps, [4] column norms, [5..7] reserved.
+ * launches (host, 8 int64, may be NULL): the matching launch counts. */
+int jjacobi_kernel_times(jj_handle h, double *times_ms, int64_t *launches);
 
 /* Library version (JJACOBI_VERSION). */
 int32_t jjacobi_version(void);

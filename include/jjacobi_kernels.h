@@ -16,10 +16,11 @@
  *   blocks  per pair a column-major kmax x kmax block (ld = kmax) at offset
  *           pair * kmax * kmax elements (A_P, R, W_P).
  *   J       device int8 [n], +-1 (signs of the columns of G).
- *   counters device uint64 [4]: [0] rotations applied (atomic add),
+ *   counters device uint64 [8]: [0] rotations applied (atomic add),
  *           [1] bit pattern of the largest scaled |a_rs| seen (atomic max),
  *           [2] error flags (1: not positive definite, 2: non-finite,
- *           4: device wait expired), [3] reserved.
+ *           4: device wait expired), [3] pivot pairs evaluated by jjk_inner,
+ *           [4] pivot pairs that applied a rotation, [5..7] reserved.
  */
 #ifndef JJACOBI_KERNELS_H
 #define JJACOBI_KERNELS_H

@@ -32,7 +32,9 @@ struct jj_ctx {
     bool ozaki = false;                 // Gram on the tensor cores (fp16 digits)
     bool ozaki_update = false;          // update on the tensor cores too
     int32_t *d_mod = nullptr, *d_clean = nullptr, *d_flags = nullptr, *d_sweep = nullptr;
-    int oz_slices_gram = 9, oz_slices_update = 8;
+    uint8_t *d_wdig = nullptr;          // W-side digits of the digit update (per pair)
+    int32_t *d_wdexp = nullptr;
+    int oz_slices_gram = 8, oz_slices_update = 8;
     int32_t *d_cexp = nullptr;          // column exponents (Ozaki Gram)
     unsigned long long *d_ozacc = nullptr;  // int128 Gram accumulators
 
@@ -53,6 +55,10 @@ struct jj_ctx {
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaEvent_t ev_legacy = nullptr;  // orders a private stream after the legacy stream
+    // profiling (params.profile): events around each kernel family of each step
+    std::vector<cudaEvent_t> pev;
+    double prof_ms[8] = {0};
+    int64_t prof_n[8] = {0};
 };
 
 namespace {
@@ -88,6 +94,8 @@ void free_ctx(jj_ctx *c) {
     cudaFree(c->Wblk);
     cudaFree(c->d_cexp);
     cudaFree(c->d_ozacc);
+    cudaFree(c->d_wdig);
+    cudaFree(c->d_wdexp);
     cudaFree(c->d_mod);
     cudaFree(c->d_clean);
     cudaFree(c->d_flags);
@@ -104,24 +112,46 @@ void free_ctx(jj_ctx *c) {
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->h_lam) cudaFreeHost(c->h_lam);
     if (c->ev_legacy) cudaEventDestroy(c->ev_legacy);
+    for (auto e : c->pev) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
+// Profiling: event slot of (step, point) and the kernel family between points.
+struct ProfMark {
+    int ev;
+    int family;  // family timed from this mark to the next one of the step (-1: none)
+};
+
 // Record one sweep into the stream being captured (or run it directly).
-int enqueue_sweep(jj_ctx *c, int start_buf, int *launches) {
+int enqueue_sweep(jj_ctx *c, int start_buf, int *launches, std::vector<ProfMark> *marks) {
     cudaStream_t st = c->stream;
     int L = 0;
-    JJ_CUDA(cudaMemsetAsync(c->d_cnt, 0, 4 * sizeof(unsigned long long), st));
+    auto mark = [&](int family) -> int {
+        if (!marks) return JJ_OK;
+        const int idx = (int)marks->size();
+        if (idx >= (int)c->pev.size()) {
+            cudaEvent_t e;
+            JJ_CUDA(cudaEventCreate(&e));
+            c->pev.push_back(e);
+        }
+        JJ_CUDA(cudaEventRecord(c->pev[idx], st));
+        marks->push_back({idx, family});
+        return JJ_OK;
+    };
+    JJ_CUDA(cudaMemsetAsync(c->d_cnt, 0, kNumCounters * sizeof(unsigned long long), st));
     if (!c->blocked) {
+        if (mark(4)) return JJ_CUDA_ERROR;
         JJ_CUDA(launch_column_norms(c->cplx, c->Gw[0], c->ldw, c->m, c->n, c->d_norm, st));
         ++L;
+        if (mark(3)) return JJ_CUDA_ERROR;
         for (int t = 0; t < c->steps; ++t) {
             JJ_CUDA(launch_plain_step(c->cplx, c->Gw[0], c->ldw, c->m, c->n,
                                       c->d_pairs + (size_t)t * c->npairs * 2, c->npairs, c->d_Jw,
                                       c->d_norm, c->tol, c->d_cnt, st));
             ++L;
         }
+        if (mark(-1)) return JJ_CUDA_ERROR;
     } else {
         sweep_begin_kernel<<<1, 1, 0, st>>>(c->d_sweep);
         JJ_CUDA(cudaGetLastError());
@@ -137,6 +167,7 @@ int enqueue_sweep(jj_ctx *c, int start_buf, int *launches) {
             ctl.step = t;
             ctl.steps = c->steps;
             ctl.npairs = c->npairs;
+            if (mark(0)) return JJ_CUDA_ERROR;
             if (c->ozaki) {
                 JJ_CUDA(launch_colexp(c->cplx, c->Gw[cur], c->ldw, c->m, c->n, c->d_cexp, st));
                 JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw[cur], c->ldw, c->m, pr, c->npairs,
@@ -148,21 +179,31 @@ int enqueue_sweep(jj_ctx *c, int start_buf, int *launches) {
                                     c->Ablk, c->kmax, st, ctl));
                 L += 1;
             }
+            if (mark(1)) return JJ_CUDA_ERROR;
+            UpdDigits ud;
+            if (c->ozaki_update) {
+                ud.img = c->d_wdig;
+                ud.wexp = c->d_wdexp;
+                ud.cexp = c->d_cexp;
+                ud.slices = c->oz_slices_update;
+            }
             JJ_CUDA(launch_inner(c->cplx, c->Ablk, c->Wblk, c->kmax, pr, c->npairs, c->d_Jw,
                                  c->tol, c->inner_max_sweeps, c->p.inner_block_width, c->d_cnt,
-                                 st, ctl));
+                                 st, ctl, ud));
+            if (mark(2)) return JJ_CUDA_ERROR;
             if (c->ozaki_update)
                 JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m, pr,
                                             c->npairs, c->Wblk, c->kmax, c->d_cexp,
-                                            c->oz_slices_update, c->d_cnt, st, ctl));
+                                            c->oz_slices_update, c->d_cnt, st, ctl, ud));
             else
                 JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m,
                                       pr, c->npairs, c->Wblk, c->kmax, st, ctl));
             L += 2;
+            if (mark(-1)) return JJ_CUDA_ERROR;
             cur ^= 1;
         }
     }
-    JJ_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, 4 * sizeof(unsigned long long),
+    JJ_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, kNumCounters * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, st));
     if (launches) *launches = L;
     return JJ_OK;
@@ -173,7 +214,7 @@ int build_graph(jj_ctx *c, int start_buf) {
     cudaGraph_t g = nullptr;
     JJ_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int L = 0;
-    const int rc = enqueue_sweep(c, start_buf, &L);
+    const int rc = enqueue_sweep(c, start_buf, &L, nullptr);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc != JJ_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -235,6 +276,15 @@ const char *jjacobi_status_string(int status) {
 }
 
 int32_t jjacobi_version(void) { return JJACOBI_VERSION; }
+
+int jjacobi_kernel_times(jj_handle c, double *times_ms, int64_t *launches) {
+    if (!c || !times_ms) return JJ_INVALID_ARG;
+    for (int i = 0; i < 8; ++i) {
+        times_ms[i] = c->prof_ms[i];
+        if (launches) launches[i] = c->prof_n[i];
+    }
+    return JJ_OK;
+}
 
 int jjacobi_create(jj_handle *h, const jj_params *p) {
     if (!h) return JJ_INVALID_ARG;
@@ -331,10 +381,14 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
             return fail(JJ_CUDA_ERROR);
         if (c->ozaki) {
             if (p->ozaki_slices > 0) {
-                if (p->ozaki_slices > 9) return fail(JJ_INVALID_ARG);
-                c->oz_slices_gram = p->ozaki_slices;
-                c->oz_slices_update = p->ozaki_slices < 8 ? p->ozaki_slices : 8;
+                if (p->ozaki_slices > ozaki_max_update_slices(c->cplx, c->kmax))
+                    return fail(JJ_INVALID_ARG);
+                c->oz_slices_update = p->ozaki_slices;
             }
+            if (c->ozaki_update &&
+                (cudaMalloc(&c->d_wdig, (size_t)c->npairs * 16 * kUpdSliceBytes) != cudaSuccess ||
+                 cudaMalloc(&c->d_wdexp, (size_t)c->npairs * 64 * sizeof(int32_t)) != cudaSuccess))
+                return fail(JJ_CUDA_ERROR);
             if (cudaMalloc(&c->d_cexp, n * sizeof(int32_t)) != cudaSuccess ||
                 cudaMalloc(&c->d_ozacc, ozaki_gram_workspace_bytes(c->npairs, c->kmax, c->cplx)) !=
                     cudaSuccess)
@@ -353,9 +407,9 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
     if (cudaMalloc(&c->d_perm, n * sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_rank, n * sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_Jw, n) != cudaSuccess || cudaMalloc(&c->d_Jorig, n) != cudaSuccess ||
-        cudaMalloc(&c->d_cnt, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_cnt, kNumCounters * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_lam, n * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&c->h_cnt, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&c->h_cnt, kNumCounters * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&c->h_lam, n * sizeof(double)) != cudaSuccess)
         return fail(JJ_CUDA_ERROR);
     *h = c;
@@ -413,14 +467,32 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
     int cur = 0;
     int rc = JJ_NOT_CONVERGED;
     for (int sweep = 1; sweep <= c->max_sweeps; ++sweep) {
-        int r = build_graph(c, cur);
-        if (r != JJ_OK) return finish(r);
-        JJ_CUDA(cudaGraphLaunch(c->graph[cur], st));
-        JJ_CUDA(cudaStreamSynchronize(st));
-        launches += c->launches_per_sweep;
+        if (c->p.profile) {
+            std::vector<ProfMark> marks;
+            int L = 0;
+            const int r = enqueue_sweep(c, cur, &L, &marks);
+            if (r != JJ_OK) return finish(r);
+            JJ_CUDA(cudaStreamSynchronize(st));
+            for (size_t i = 0; i + 1 < marks.size(); ++i) {
+                if (marks[i].family < 0) continue;
+                float ms = 0.f;
+                JJ_CUDA(cudaEventElapsedTime(&ms, c->pev[marks[i].ev], c->pev[marks[i + 1].ev]));
+                c->prof_ms[marks[i].family] += ms;
+                c->prof_n[marks[i].family] += 1;
+            }
+            launches += L;
+        } else {
+            int r = build_graph(c, cur);
+            if (r != JJ_OK) return finish(r);
+            JJ_CUDA(cudaGraphLaunch(c->graph[cur], st));
+            JJ_CUDA(cudaStreamSynchronize(st));
+            launches += c->launches_per_sweep;
+        }
         inf.sweeps = sweep;
         const unsigned long long rot = c->h_cnt[kCntRot];
         inf.rotations += (int64_t)rot;
+        inf.pairs_evaluated += (int64_t)c->h_cnt[kCntPairs];
+        inf.pairs_rotated += (int64_t)c->h_cnt[kCntPairsRot];
         double mo;
         std::memcpy(&mo, &c->h_cnt[kCntMaxOff], sizeof(double));
         inf.last_max_offdiag = mo;

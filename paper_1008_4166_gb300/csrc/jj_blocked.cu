@@ -418,6 +418,8 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
         for (int w = 0; w < IT / 32; ++w) mo = fmax(mo, smax[w]);
         atomic_max_nonneg(&counters[kCntMaxOff], mo);
         if (total_rot) atomicAdd(&counters[kCntRot], total_rot);
+        atomicAdd(&counters[kCntPairs], 1ull);
+        if (total_rot) atomicAdd(&counters[kCntPairsRot], 1ull);
         pair_record(ctl, pd, blockIdx.x, total_rot > 0, false);
     }
 }
@@ -437,7 +439,7 @@ template <bool CPLX, int ROWS>
 __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double *__restrict__ A, double *__restrict__ Wb, int kmax, const int32_t *__restrict__ pairs,
     const int8_t *__restrict__ J, double tol, int max_sweeps,
-    unsigned long long *__restrict__ counters, StepCtl ctl) {
+    unsigned long long *__restrict__ counters, StepCtl ctl, UpdDigits ud) {
     constexpr int E = CPLX ? 2 : 1;
     extern __shared__ double2 smem4[];
     double *sm = reinterpret_cast<double *>(smem4);
@@ -449,7 +451,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double *W = R + (size_t)k * ldr * E;         // k x k entries
     double *dsh = W + (size_t)k * ldr * E;       // k
     double *qsh = dsh + kmax;                    // per-step dots and rotation parameters
-    int *jsh = reinterpret_cast<int *>(qsh + 2 * 64 + 7 * 64);
+    int *jsh = reinterpret_cast<int *>(qsh + 2 * 64 + 2 * 7 * 64);
     __shared__ int s_rot, s_fail;
     __shared__ double s_piv;
     __shared__ double s_max[SW];
@@ -537,7 +539,38 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double maxoff = 0.0;
     // per-step scratch: dot products and rotation parameters of every pair
     double *sdot = qsh;                       // [nq][2]
-    double *spar = qsh + 2 * 64;              // [nq][7]: ce_re ce_im se_re se_im c hs flag
+    double *spar0 = qsh + 2 * 64;             // [2][nq][7]: ce_re ce_im se_re se_im c hs flag
+    // Rotations of W are needed only at the end, so the W part of step s is
+    // applied by warps 1.. while warp 0 computes the parameters of step s + 1.
+    auto apply_w = [&](int st, const double *par, int w0, int nw) {
+        for (int qi = w0; qi < nq; qi += nw) {
+            const double *pp = par + 7 * qi;
+            if (pp[6] == 0.0) continue;
+            int a = qi == 0 ? P : (st + qi) % P;
+            int b = qi == 0 ? st : (st - qi + P) % P;
+            if (a > b) { const int t = a; a = b; b = t; }
+            Rot Q;
+            Q.ce_re = pp[0]; Q.ce_im = pp[1]; Q.se_re = pp[2]; Q.se_im = pp[3]; Q.c = pp[4]; Q.hs = pp[5];
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                const int l = lane + 32 * i;
+                if (l < k) {
+                    if (CPLX) {
+                        double2 u = *reinterpret_cast<const double2 *>(W + ((size_t)a * ldr + l) * 2);
+                        double2 v = *reinterpret_cast<const double2 *>(W + ((size_t)b * ldr + l) * 2);
+                        rot_apply_c(Q, u.x, u.y, v.x, v.y);
+                        *reinterpret_cast<double2 *>(W + ((size_t)a * ldr + l) * 2) = u;
+                        *reinterpret_cast<double2 *>(W + ((size_t)b * ldr + l) * 2) = v;
+                    } else {
+                        double u = W[(size_t)a * ldr + l], v = W[(size_t)b * ldr + l];
+                        rot_apply_r(Q, u, v);
+                        W[(size_t)a * ldr + l] = u;
+                        W[(size_t)b * ldr + l] = v;
+                    }
+                }
+            }
+        }
+    };
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int c = warp; c < k; c += SW) {
             double acc = 0.0;
@@ -595,7 +628,9 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
             __syncthreads();
             // (2) rotation parameters of all pairs of the step at once: warp 0,
             // one lane per pair (the FP64 sequences run once per step, not once
-            // per pair)
+            // per pair); meanwhile the other warps rotate W for the previous step
+            double *spar = spar0 + 7 * 64 * (step & 1);
+            if (warp != 0 && step > 0) apply_w(step - 1, spar0 + 7 * 64 * ((step - 1) & 1), warp - 1, SW - 1);
             if (warp == 0) {
                 for (int qi = lane; qi < nq; qi += 32) {
                     int a = qi == 0 ? P : (step + qi) % P;
@@ -631,7 +666,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
                 }
             }
             __syncthreads();
-            // (3) apply: one warp per pair, lanes over rows of R and W
+            // (3) apply to R: one warp per pair, lanes over rows
             for (int qi = warp; qi < nq; qi += SW) {
                 const double *pp = spar + 7 * qi;
                 if (pp[6] == 0.0) continue;
@@ -650,27 +685,20 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
                             rot_apply_c(Q, u.x, u.y, v.x, v.y);
                             *reinterpret_cast<double2 *>(R + ((size_t)a * ldr + l) * 2) = u;
                             *reinterpret_cast<double2 *>(R + ((size_t)b * ldr + l) * 2) = v;
-                            u = *reinterpret_cast<const double2 *>(W + ((size_t)a * ldr + l) * 2);
-                            v = *reinterpret_cast<const double2 *>(W + ((size_t)b * ldr + l) * 2);
-                            rot_apply_c(Q, u.x, u.y, v.x, v.y);
-                            *reinterpret_cast<double2 *>(W + ((size_t)a * ldr + l) * 2) = u;
-                            *reinterpret_cast<double2 *>(W + ((size_t)b * ldr + l) * 2) = v;
                         } else {
                             double u = R[(size_t)a * ldr + l], v = R[(size_t)b * ldr + l];
                             rot_apply_r(Q, u, v);
                             R[(size_t)a * ldr + l] = u;
                             R[(size_t)b * ldr + l] = v;
-                            u = W[(size_t)a * ldr + l];
-                            v = W[(size_t)b * ldr + l];
-                            rot_apply_r(Q, u, v);
-                            W[(size_t)a * ldr + l] = u;
-                            W[(size_t)b * ldr + l] = v;
                         }
                     }
                 }
             }
             __syncthreads();
         }
+        // W part of the sweep's last step
+        apply_w(P - 1, spar0 + 7 * 64 * ((P - 1) & 1), warp, SW);
+        __syncthreads();
         if (warp == 0) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) my_rot += __shfl_xor_sync(0xffffffffu, my_rot, o);
@@ -681,6 +709,59 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         total_rot += (unsigned long long)rot;
         __syncthreads();
         if (rot == 0) break;
+    }
+    // Operand of the digit-product update: digits of D (W2 - I), W2 the real form
+    // [[Wr, Wi], [-Wi, Wr]] of W, D the column exponents of the pivot columns.
+    if (ud.img && total_rot > 0) {
+        __shared__ int s_xexp[64], s_wexp[64];
+        const int K2 = CPLX ? 2 * k : k;
+        auto w2m = [&](int a, int j) -> double {  // (W2 - I)_aj from the smem W
+            double v;
+            if (CPLX) {
+                const int ar = a < k ? a : a - k, jr = j < k ? j : j - k;
+                const double re = W[((size_t)jr * ldr + ar) * 2], im = W[((size_t)jr * ldr + ar) * 2 + 1];
+                v = a < k ? (j < k ? re : im) : (j < k ? -im : re);
+            } else {
+                v = W[(size_t)j * ldr + a];
+            }
+            return a == j ? v - 1.0 : v;
+        };
+        for (int a = tid; a < 64; a += ST) {
+            int e = -1021;
+            if (a < K2) {
+                const int c = CPLX ? (a < k ? a : a - k) : a;
+                e = ud.cexp[pivot_col(pd, c)];
+            }
+            s_xexp[a] = e;
+        }
+        __syncthreads();
+        for (int j = warp; j < 64; j += SW) {
+            int mx = -100000;
+            if (j < K2)
+                for (int a = lane; a < K2; a += 32) {
+                    const unsigned long long mb = dg_mag_bits(w2m(a, j));
+                    if (mb) mx = max(mx, dg_exp_of_bits(mb) + s_xexp[a]);
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) s_wexp[j] = mx == -100000 ? -1021 : mx;
+        }
+        __syncthreads();
+        uint8_t *img = ud.img + (size_t)blockIdx.x * ud.slices * kUpdSliceBytes;
+        for (int it = tid; it < 64 * 32; it += ST) {  // (row j, K positions a, a+1)
+            const int j = it / 32, a = (it % 32) * 2;
+            double x0 = 0.0, x1 = 0.0;
+            if (j < K2 && a < K2) x0 = w2m(a, j);
+            if (j < K2 && a + 1 < K2) x1 = w2m(a + 1, j);
+            const unsigned long long q0 = dg_fixed63(x0, s_wexp[j] - s_xexp[a]);
+            const unsigned long long q1 = dg_fixed63(x1, s_wexp[j] - s_xexp[a + 1]);
+            const bool n0 = __double_as_longlong(x0) < 0, n1 = __double_as_longlong(x1) < 0;
+            const uint32_t off = dg_sw128_off(j, a * 2);
+            for (int t = 1; t <= ud.slices; ++t)
+                *reinterpret_cast<uint32_t *>(img + (size_t)(t - 1) * kUpdSliceBytes + off) =
+                    dg_digits2_bits(q0, n0, q1, n1, t);
+        }
+        for (int j = tid; j < 64; j += ST) ud.wexp[(size_t)blockIdx.x * 64 + j] = s_wexp[j];
     }
     // write back R~ and W
     for (int t = tid; t < k * k; t += ST) {
@@ -700,13 +781,15 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         for (int w = 0; w < SW; ++w) mo = fmax(mo, s_max[w]);
         atomic_max_nonneg(&counters[kCntMaxOff], mo);
         if (total_rot) atomicAdd(&counters[kCntRot], total_rot);
+        atomicAdd(&counters[kCntPairs], 1ull);
+        if (total_rot) atomicAdd(&counters[kCntPairsRot], 1ull);
         pair_record(ctl, pd, blockIdx.x, total_rot > 0, false);
     }
 }
 
 size_t inner_smem_bytes(bool cplx, int kmax) {
     const int E = cplx ? 2 : 1;
-    return sizeof(double) * ((size_t)2 * kmax * kmax * E + kmax + 2 * 64 + 7 * 64) +
+    return sizeof(double) * ((size_t)2 * kmax * kmax * E + kmax + 2 * 64 + 2 * 7 * 64) +
            sizeof(int) * kmax + 64;
 }
 
@@ -742,7 +825,7 @@ cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
                          int npairs, const int8_t *J, double tol, int inner_max_sweeps,
                          int inner_block, unsigned long long *counters, cudaStream_t st,
-                         StepCtl ctl) {
+                         StepCtl ctl, UpdDigits ud) {
     (void)inner_block;
     if (npairs <= 0) return cudaSuccess;
     // Shared-memory resident form when R and W fit (227 KB per block).
@@ -754,7 +837,7 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)smb);                                       \
         if (e != cudaSuccess) return e;                                                       \
-        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl); \
+        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl, ud); \
         return cudaGetLastError();                                                            \
     } while (0)
         const int rows = (kmax + 31) / 32;

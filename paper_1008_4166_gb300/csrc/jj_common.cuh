@@ -18,7 +18,7 @@ constexpr unsigned long long kErrTimeout = 4ull;
 constexpr double kDefaultTol = 128.0 * 1.1102230246251565404e-16;
 
 // Counter slots.
-enum { kCntRot = 0, kCntMaxOff = 1, kCntErr = 2 };
+enum { kCntRot = 0, kCntMaxOff = 1, kCntErr = 2, kCntPairs = 3, kCntPairsRot = 4, kNumCounters = 8 };
 
 // Parameters of one J-unitary rotation on a column pair (g_r, g_s), in the form
 //   g_r' = ce * g_r - hs * g_s,   g_s' = se * g_r + c * g_s
@@ -115,6 +115,19 @@ struct StepCtl {
 constexpr int kPairSkipped = 1;
 constexpr int kPairIdentity = 2;
 
+// Operand of the split-precision update produced by the inner solve: the fp16
+// digits of D (W2 - I) as shared-memory images (SWIZZLE_128B, K-major: 64 rows
+// of 128 bytes per digit, row j = output column j, K position a = row of W2),
+// and their column exponents. D holds the column exponents of the pivot
+// columns (cexp). Used only when the update runs as digit products.
+struct UpdDigits {
+    uint8_t *img = nullptr;        // [npairs][slices][64 * 128]
+    int32_t *wexp = nullptr;       // [npairs][64]
+    const int32_t *cexp = nullptr; // column exponents of G (by work column)
+    int slices = 0;
+};
+constexpr int kUpdSliceBytes = 64 * 128;
+
 // Decide (Gram kernels) whether pair q of this step can be skipped: the slot was
 // found clean at step `clean` and neither block changed after it.
 __device__ __forceinline__ bool pair_skip_decide(const StepCtl &c, const int32_t *pd, int q) {
@@ -165,13 +178,14 @@ cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
                          int npairs, const int8_t *J, double tol, int inner_max_sweeps,
                          int inner_block, unsigned long long *counters, cudaStream_t st,
-                         StepCtl ctl = StepCtl());
+                         StepCtl ctl = StepCtl(), UpdDigits ud = UpdDigits());
 cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int64_t ld,
                           int64_t m, const int32_t *pairs, int npairs, const double *W,
                           int kmax, cudaStream_t st, StepCtl ctl = StepCtl());
 
 // Split-precision (fp16 digit) forms on the tensor cores (jj_ozaki.cu).
 int ozaki_default_slices(bool gram);
+int ozaki_max_update_slices(bool cplx, int kmax);
 bool ozaki_supported(bool cplx, int kmax);
 size_t ozaki_gram_workspace_bytes(int npairs, int kmax, bool cplx);
 cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int64_t n,
@@ -185,7 +199,44 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
 cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
                                 const int32_t *pairs, int npairs, const double *W, int kmax,
                                 const int32_t *cexp, int slices, unsigned long long *counters,
-                                cudaStream_t st, StepCtl ctl = StepCtl());
+                                cudaStream_t st, StepCtl ctl = StepCtl(), UpdDigits ud = UpdDigits());
+// Digit helpers shared by the inner solve (W-side digits) and the digit kernels.
+__device__ __forceinline__ unsigned long long dg_mag_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ int dg_exp_of_bits(unsigned long long mag) {
+    const int E = (int)((mag >> 52) & 0x7FF);
+    return E == 0 ? -1021 : E - 1022;
+}
+// floor(|x| 2^(63-e)) for |x| < 2^e (integer shifts of the significand)
+__device__ __forceinline__ unsigned long long dg_fixed63(double x, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return 0ull;
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E - 1012 - e;
+    if (sh >= 0) return mant << sh;
+    if (sh <= -64) return 0ull;
+    return mant >> (-sh);
+}
+// 7-bit digit t (1-based) of two fixed-point values as packed fp16 bits, signed
+__device__ __forceinline__ uint32_t dg_digits2_bits(unsigned long long q0, bool n0,
+                                                    unsigned long long q1, bool n1, int t) {
+    const uint32_t d0 = (uint32_t)((q0 >> (63 - 7 * t)) & 127ull);
+    const uint32_t d1 = (uint32_t)((q1 >> (63 - 7 * t)) & 127ull);
+    // fp16 of an integer d < 128: exponent and significand built directly
+    auto h = [](uint32_t d) -> uint32_t {
+        if (d == 0) return 0u;
+        const int lz = __clz(d) - 16;          // leading zeros in 16 bits
+        const int e = 15 - lz;                 // d in [2^e, 2^(e+1))
+        return (uint32_t)((e + 15) << 10) | ((d << (10 - e)) & 0x3FFu);
+    };
+    return (h(d0) | (n0 ? 0x8000u : 0u)) | ((h(d1) | (n1 ? 0x8000u : 0u)) << 16);
+}
+__device__ __forceinline__ uint32_t dg_sw128_off(int row, int kbyte) {
+    return (uint32_t)(row * 128 + ((((kbyte >> 4) ^ (row & 7))) << 4) + (kbyte & 15));
+}
+
 // Copy the pivot columns of one pair, rows [l0, l1), from Gs to Gd (pass-through).
 __device__ __forceinline__ void pair_copy_rows(bool cplx, const double *Gs, double *Gd, int64_t ld,
                                                const int32_t *pd, int64_t l0, int64_t l1,

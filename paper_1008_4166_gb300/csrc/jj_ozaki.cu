@@ -38,6 +38,7 @@ namespace jj {
 constexpr int kBeta = 7;          // bits per digit
 constexpr int kOzMaxSlices = 9;   // 63 bits
 constexpr int kOzMaxK2 = 64;      // real width 2k (complex) or k (real) handled here
+constexpr int kOzUpdMaxSlices = 16;  // update digits (exact group sums need s * K2 * 127^2 < 2^24)
 
 namespace {
 
@@ -134,6 +135,14 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // ---------------------------------------------------------------------------
 // Digits
 // ---------------------------------------------------------------------------
+// Sign and magnitude tests on the bit pattern of a double: on this part an FP64
+// comparison or absolute value runs on the FP64 pipe, 64 times slower than the
+// integer ALU, so the digit kernels never touch FP64 arithmetic.
+__device__ __forceinline__ bool neg_bits(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
 // Exponent e with |x| < 2^e for the magnitude bit pattern `mag` (a non-negative
 // double's bits); zero and subnormals give the smallest normal exponent.
 __device__ __forceinline__ int exp_of_bits(unsigned long long mag) {
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(256) colexp_kernel(const double *__restrict__ 
     const double *g = G + c * ld * (CPLX ? 2 : 1);
     const int64_t cnt = m * (CPLX ? 2 : 1);
     for (int64_t i = threadIdx.x; i < cnt; i += 256) {
-        const unsigned long long v = (unsigned long long)__double_as_longlong(fabs(g[i]));
+        const unsigned long long v = mag_bits(g[i]);
         mx = v > mx ? v : mx;
     }
 #pragma unroll
@@ -225,34 +234,37 @@ __global__ void __launch_bounds__(256) colexp_kernel(const double *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Gram: one block per (chunk group of rows, pair). The pivot's K2 real columns
-// are the 64 rows of the A operand (M = 64) and, the Gram being X^T X, the N
-// rows of the same shared-memory tile serve as the B operand. Rows of G are
-// taken 64 at a time (K = 64 per chunk); every diagonal group of digit
-// products is accumulated in a TMEM buffer (two buffers: the tensor cores fill
-// one while the block drains the other) and added into int128 accumulators.
-// At the end each block adds its int128 partial sums atomically into the
-// global accumulator (lo, hi words with an explicit carry).
+// Gram: one block per (row range, pair). The pivot's K2 real columns are the
+// 64 rows of the A operand (M = 64) and, the Gram being X^T X, the same
+// shared-memory tile serves as the B operand. With s = 8 digits (56 bits;
+// the Gram error stays below sqrt(m) 2^-56 of ||x_a|| ||x_b|| by the
+// Cauchy-Schwarz inequality), the products of one diagonal d = t + u
+// (d - 1 <= 8 of them) form one TMEM group, and the 8 groups occupy the 512
+// TMEM columns at once. Rows of G arrive 64 at a time in two shared-memory
+// buffers (digits of the next 64 rows are built while the tensor cores read
+// the current ones); every group accumulates 128 rows in TMEM, which keeps its
+// fp32 sum an exact integer below 2^24 (8 * 128 * 127^2 < 2^24), and is then
+// drained into two signed 64-bit words per output (no carries until the end).
+// At the end each block adds its partial sums atomically into the global
+// int128 accumulator (lo, hi words with an explicit carry).
 // ---------------------------------------------------------------------------
-constexpr int GZ_THREADS = 256;
-constexpr int GZ_KC = 64;                 // rows of G per chunk (K of one MMA group)
+constexpr int GZ_THREADS = 512;
+constexpr int GZ_KC = 64;                 // rows of G per shared-memory buffer
 constexpr int GZ_SLICE_BYTES = 64 * 128;  // 64 operand rows x 128 bytes
-constexpr int GZ_GMAX = 4;                // digit products per TMEM group
-constexpr int GZ_MAXGROUPS = 32;
+constexpr int GZ_SLICES = 8;              // digits of the Gram operands
+constexpr int GZ_BUF_BYTES = GZ_SLICES * GZ_SLICE_BYTES;
 
 template <bool CPLX>
-__global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
+__global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
     const double *__restrict__ G, int64_t ld, int64_t m, const int32_t *__restrict__ pairs,
     const int32_t *__restrict__ cexp, unsigned long long *__restrict__ acc_out, int k2max,
-    int slices, int rows_per_block, unsigned long long *__restrict__ counters, StepCtl ctl) {
+    int rows_per_block, unsigned long long *__restrict__ counters, StepCtl ctl) {
     extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) unsigned long long bar_full[2];
+    __shared__ __align__(8) unsigned long long bar_mma[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int sexp[kOzMaxK2];
-    __shared__ int8_t grp_t[kOzMaxSlices * kOzMaxSlices], grp_u[kOzMaxSlices * kOzMaxSlices];
-    __shared__ int grp_start[GZ_MAXGROUPS + 1], grp_shift[GZ_MAXGROUPS];
-    __shared__ int s_ngroups, s_abort;
+    __shared__ int s_abort;
 
     const int32_t *pd = pairs + 4 * blockIdx.y;
     if (ctl.mod_step) {
@@ -264,182 +276,186 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
     const int K2 = CPLX ? 2 * k : k;
     const int NP = (K2 + 15) & ~15;  // N of the MMA (multiple of 16)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int s = slices;
     const int64_t row0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t row1 = min((int64_t)m, row0 + rows_per_block);
 
-    // Group table. X^T X is symmetric, so with P_tu = A_t^T A_u = P_ut^T only the
-    // products t <= u are formed: off-diagonal ones (t < u) with twice their
-    // weight, squares (t = t) with their weight; the result acc satisfies
-    // acc + acc^T = 2 C exactly. Products of one weight share a TMEM group of at
-    // most GZ_GMAX products, which keeps every fp32 group sum an exact integer
-    // below 2^22 (GZ_GMAX * 64 * 127^2 < 2^22).
-    if (tid == 0) {
-        int g = 0, p = 0;
-        for (int d = 2; d <= s + 1; ++d) {
-            int cnt = 0;
-            for (int t = 1; 2 * t < d; ++t) {
-                const int u = d - t;
-                if (u > s) continue;
-                if (cnt == 0) {
-                    grp_start[g] = p;
-                    grp_shift[g] = kBeta * (s + 1 - d) + 1;
-                    ++g;
-                }
-                grp_t[p] = (int8_t)t;
-                grp_u[p] = (int8_t)u;
-                ++p;
-                if (++cnt == GZ_GMAX) cnt = 0;
-            }
-            if ((d & 1) == 0 && d / 2 <= s) {
-                grp_start[g] = p;
-                grp_shift[g] = kBeta * (s + 1 - d);
-                ++g;
-                grp_t[p] = (int8_t)(d / 2);
-                grp_u[p] = (int8_t)(d / 2);
-                ++p;
-            }
-        }
-        grp_start[g] = p;
-        s_ngroups = g;
-        s_abort = 0;
-    }
+    if (tid == 0) s_abort = 0;
     for (int a = tid; a < K2; a += GZ_THREADS) {
         const int c = CPLX ? (a < k ? a : a - k) : a;
         sexp[a] = cexp[c < pd[1] ? pd[0] + c : pd[2] + (c - pd[1])];
     }
-    if (warp == 0) tmem_alloc(su32(&tmem_base_sh), 128);
+    if (warp == 0) tmem_alloc(su32(&tmem_base_sh), 512);
     if (tid == 0) {
-        mbar_init(su32(&bar_full[0]), 1);
-        mbar_init(su32(&bar_full[1]), 1);
+        mbar_init(su32(&bar_mma[0]), 1);
+        mbar_init(su32(&bar_mma[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    // zero the padded operand rows once (rows K2..63 stay zero for every chunk)
-    for (int i = tid; i < s * GZ_SLICE_BYTES / 16; i += GZ_THREADS)
-        reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    // operand rows K2..63 stay zero for every chunk
+    if (K2 < 64)
+        for (int i = tid; i < 2 * GZ_BUF_BYTES / 16; i += GZ_THREADS)
+            reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
-    const int ngroups = s_ngroups;
     const uint32_t idesc = idesc_f16(64, NP);
 
-    // accumulators: this thread owns TMEM lane (warp%4)*32 + lane -> output row
-    // r = (lane < 16) ? (warp%4)*16 + lane : none, and columns [half*32, half*32+32)
-    const int quad = warp & 3, half = warp >> 2;
+    // this thread: TMEM lane (warp%4)*32 + lane holds output row (warp%4)*16 + lane
+    // for lane < 16 (M = 64 layout); columns [cq*16, cq*16 + 16)
+    const int quad = warp & 3, cq = warp >> 2;
     const int orow = quad * 16 + lane;
     const bool owns = lane < 16 && orow < K2;
-    // Accumulator of one output: w0 + w1 * 2^32 with signed 64-bit words; a group
-    // sum v (|v| < 2^22) of shift sh adds v * 2^(sh mod 32) to word sh / 32, so no
-    // carry is propagated until the end (each word stays below 2^60).
-    long long w0[32], w1[32];
+    long long w0[16], w1[16];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < 16; ++j) {
         w0[j] = 0;
         w1[j] = 0;
     }
-    uint32_t phase[2] = {0u, 0u};
-    int issued = 0;  // groups issued over the whole block life (buffer = issued & 1)
+    uint32_t ph[2] = {0u, 0u};
+    bool pending[2] = {false, false};
     const uint32_t sbase = su32(sm);
+    const int nsc = (int)((row1 - row0 + GZ_KC - 1) / GZ_KC);
 
-    auto issue_group = [&](int g, int buf) {
-        const uint32_t dt = tmem + (uint32_t)(buf * 64);
-        bool first = true;
-        for (int p = grp_start[g]; p < grp_start[g + 1]; ++p) {
-            const uint32_t a0 = sbase + (uint32_t)((grp_t[p] - 1) * GZ_SLICE_BYTES);
-            const uint32_t b0 = sbase + (uint32_t)((grp_u[p] - 1) * GZ_SLICE_BYTES);
+    // One thread polls the mbarrier; the others wait in the block barrier that
+    // follows (spinning threads would take issue slots from the digit builders).
+    auto wait_buf = [&](int b) {
+        if (!pending[b]) return;
+        if (tid == 0 && !mbar_wait(su32(&bar_mma[b]), ph[b])) s_abort = 1;
+        __syncthreads();
+        ph[b] ^= 1u;
+        pending[b] = false;
+    };
+    // digits of rows [row0 + 64 i, +64) of the K2 real columns into buffer b;
+    // thread -> (column a, row pair): rows l, l+1 packed into one 32-bit store.
+    // All loads of a thread are issued before any digit work (one memory
+    // latency per 64 rows instead of one per item).
+    constexpr int GZ_ITEMS = 64 * (GZ_KC / 2) / GZ_THREADS;
+    constexpr int GZ_BATCH = 2;
+    auto build = [&](int i, int b) {
+        const int64_t c0 = row0 + (int64_t)i * GZ_KC;
+        const int nrow = (int)min((int64_t)GZ_KC, row1 - c0);
+        uint8_t *buf = sm + (size_t)b * GZ_BUF_BYTES;
+        // two batches of loads: the 64 accumulator registers of the flush
+        // leave no room for all of them at once
 #pragma unroll
-            for (int ks = 0; ks < GZ_KC / 16; ++ks) {
-                mma_f16(dt, desc_sw128(a0 + ks * 32), desc_sw128(b0 + ks * 32), idesc,
-                        first ? 0u : 1u);
-                first = false;
+        for (int h = 0; h < GZ_ITEMS; h += GZ_BATCH) {
+            double xv0[GZ_BATCH], xv1[GZ_BATCH];
+#pragma unroll
+            for (int u = 0; u < GZ_BATCH; ++u) {
+                const int idx = tid + (h + u) * GZ_THREADS;
+                const int a = idx / (GZ_KC / 2);
+                const int lp = (idx % (GZ_KC / 2)) * 2;
+                xv0[u] = 0.0;
+                xv1[u] = 0.0;
+                if (a < K2) {
+                    const int c = CPLX ? (a < k ? a : a - k) : a;
+                    const int64_t col = c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
+                    const int ri = (CPLX && a >= k) ? 1 : 0;
+                    if (lp < nrow) xv0[u] = CPLX ? G[(col * ld + c0 + lp) * 2 + ri] : G[col * ld + c0 + lp];
+                    if (lp + 1 < nrow)
+                        xv1[u] = CPLX ? G[(col * ld + c0 + lp + 1) * 2 + ri] : G[col * ld + c0 + lp + 1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < GZ_BATCH; ++u) {
+                const int idx = tid + (h + u) * GZ_THREADS;
+                const int a = idx / (GZ_KC / 2);
+                const int lp = (idx % (GZ_KC / 2)) * 2;
+                if (a >= K2) continue;
+                const int e = sexp[a];
+                const unsigned long long q0 = fixed63(xv0[u], e), q1 = fixed63(xv1[u], e);
+                const bool n0 = neg_bits(xv0[u]), n1 = neg_bits(xv1[u]);
+                const uint32_t off = sw128_off(a, lp * 2);
+#pragma unroll
+                for (int t = 1; t <= GZ_SLICES; ++t)
+                    *reinterpret_cast<uint32_t *>(buf + (t - 1) * GZ_SLICE_BYTES + off) =
+                        dg_digits2_bits(q0, n0, q1, n1, t);
             }
         }
-        mma_commit(su32(&bar_full[buf]));
     };
 
-    for (int64_t c0 = row0; c0 < row1; c0 += GZ_KC) {
-        // --- digits of rows [c0, c0 + 64) of the K2 real columns -> smem -------
-        // thread -> (column a, row pair): rows l, l+1 packed into one 32-bit store
-        const int nrow = (int)min((int64_t)GZ_KC, row1 - c0);
-        for (int idx = tid; idx < K2 * (GZ_KC / 2); idx += GZ_THREADS) {
-            const int a = idx / (GZ_KC / 2);
-            const int lp = (idx % (GZ_KC / 2)) * 2;
-            const int c = CPLX ? (a < k ? a : a - k) : a;
-            const int64_t col = c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
-            const int e = sexp[a];
-            double x0 = 0.0, x1 = 0.0;
-            if (lp < nrow) x0 = CPLX ? G[(col * ld + c0 + lp) * 2 + (a < k ? 0 : 1)] : G[col * ld + c0 + lp];
-            if (lp + 1 < nrow)
-                x1 = CPLX ? G[(col * ld + c0 + lp + 1) * 2 + (a < k ? 0 : 1)] : G[col * ld + c0 + lp + 1];
-            const unsigned long long q0 = fixed63(x0, e), q1 = fixed63(x1, e);
-            const bool n0 = x0 < 0.0, n1 = x1 < 0.0;
-            const uint32_t off = sw128_off(a, lp * 2);
-            for (int t = 1; t <= s; ++t)
-                *reinterpret_cast<__half2 *>(sm + (t - 1) * GZ_SLICE_BYTES + off) = digits2(q0, n0, q1, n1, t);
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // --- products and flushes ----------------------------------------------
+    if (nsc > 0) build(0, 0);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    for (int i = 0; i < nsc && !s_abort; ++i) {
+        const int b = i & 1;
+        const bool first = (i & 1) == 0;  // first 64 rows of a 128-row accumulation
         if (tid == 0) {
-            issue_group(0, issued & 1);
-            if (ngroups > 1) issue_group(1, (issued + 1) & 1);
-        }
-        for (int g = 0; g < ngroups; ++g) {
-            const int buf = (issued + g) & 1;
-            if (!mbar_wait(su32(&bar_full[buf]), phase[buf])) {
-                if (lane == 0) s_abort = 1;
+            const uint32_t base = sbase + (uint32_t)(b * GZ_BUF_BYTES);
+            for (int d = 2; d <= GZ_SLICES + 1; ++d) {
+                const uint32_t dt = tmem + (uint32_t)((d - 2) * 64);
+                bool acc = !first;
+                for (int t = 1; t <= GZ_SLICES; ++t) {
+                    const int u = d - t;
+                    if (u < 1 || u > GZ_SLICES) continue;
+                    const uint32_t a0 = base + (uint32_t)((t - 1) * GZ_SLICE_BYTES);
+                    const uint32_t b0 = base + (uint32_t)((u - 1) * GZ_SLICE_BYTES);
+#pragma unroll
+                    for (int ks = 0; ks < GZ_KC / 16; ++ks) {
+                        mma_f16(dt, desc_sw128(a0 + ks * 32), desc_sw128(b0 + ks * 32), idesc,
+                                acc ? 1u : 0u);
+                        acc = true;
+                    }
+                }
             }
-            phase[buf] ^= 1u;
+            mma_commit(su32(&bar_mma[b]));
+        }
+        pending[b] = true;
+        if (i + 1 < nsc) {
+            wait_buf(b ^ 1);  // the products that read the other buffer are done
+            build(i + 1, b ^ 1);
+            fence_async_smem();
+        }
+        if ((i & 1) == 1 || i == nsc - 1) {
+            wait_buf(b ^ 1);
+            wait_buf(b);
             tc_fence_after();
             if (!s_abort) {
-                const int sh = grp_shift[g];
-                const long long mul = 1ll << (sh & 31);
-                const bool hiw = sh >= 32;
 #pragma unroll
-                for (int j0 = 0; j0 < 32; j0 += 8) {
-                    uint32_t v[8];
-                    tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 64 + half * 32 + j0), v);
-                    tmem_wait_ld();
+                for (int d = 2; d <= GZ_SLICES + 1; ++d) {
+                    const int sh = kBeta * (GZ_SLICES + 1 - d);
+                    const long long mul = 1ll << (sh & 31);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        // exact integer |f| < 2^22: f + 1.5*2^23 has f in its low mantissa bits
-                        const int iv = __float_as_int(__uint_as_float(v[j]) + 12582912.0f) - 0x4B400000;
-                        if (hiw)
-                            w1[j0 + j] += (long long)iv * mul;
-                        else
-                            w0[j0 + j] += (long long)iv * mul;
+                    for (int j0 = 0; j0 < 16; j0 += 8) {
+                        uint32_t v[8];
+                        tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((d - 2) * 64 + cq * 16 + j0), v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact, |v| < 2^24
+                            if (sh >= 32)
+                                w1[j0 + j] += (long long)iv * mul;
+                            else
+                                w0[j0 + j] += (long long)iv * mul;
+                        }
                     }
                 }
             }
             tc_fence_before();
-            __syncthreads();
-            if (tid == 0 && g + 2 < ngroups && !s_abort) {
-                tc_fence_after();
-                issue_group(g + 2, buf);
-            }
         }
-        issued += ngroups;
-        if (s_abort) break;
         __syncthreads();
+        tc_fence_after();
     }
     if (s_abort) {
+        // give in-flight products a bounded chance to finish before freeing TMEM
+        wait_buf(0);
+        wait_buf(1);
         if (tid == 0 && counters) atomicOr(&counters[kCntErr], kErrTimeout);
     } else if (owns) {
         // add the partial sums: acc_out[pair][col b][row a] = {lo, hi}
         unsigned long long *dst = acc_out + (size_t)blockIdx.y * k2max * k2max * 2;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int b = half * 32 + j;
-            if (b < K2) {
+        for (int j = 0; j < 16; ++j) {
+            const int bcol = cq * 16 + j;
+            if (bcol < K2) {
                 // T = w0 + w1 * 2^32 as (lo, hi)
                 const unsigned long long l1 = (unsigned long long)w1[j] << 32;
                 const long long h1 = w1[j] >> 32;
                 const unsigned long long lo = (unsigned long long)w0[j] + l1;
                 const long long hi = (w0[j] >> 63) + h1 + (lo < l1 ? 1 : 0);
-                unsigned long long *w = dst + ((size_t)b * k2max + orow) * 2;
+                unsigned long long *w = dst + ((size_t)bcol * k2max + orow) * 2;
                 const unsigned long long old = atomicAdd(w, lo);
                 const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
                 atomicAdd(w + 1, (unsigned long long)hi + carry);
@@ -449,7 +465,7 @@ __global__ void __launch_bounds__(GZ_THREADS) gram_ozaki_kernel(
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 128);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // int128 fixed-point Gram -> FP64 A_P (complex: Re = C11 + C22, Im = C12 - C21),
@@ -464,16 +480,9 @@ __global__ void __launch_bounds__(256) gram_fixed_to_double_kernel(
     if (idx >= k * k) return;
     const int a = idx % k, b = idx / k;
     const unsigned long long *P = acc + (size_t)blockIdx.y * k2max * k2max * 2;
-    // C_rc = (acc_rc + acc_cr) / 2 (exact: the sum is even, see the Gram kernel)
     auto ld128 = [&](int r, int c, unsigned long long &lo, long long &hi) {
-        const unsigned long long l1 = P[((size_t)c * k2max + r) * 2];
-        const long long h1 = (long long)P[((size_t)c * k2max + r) * 2 + 1];
-        const unsigned long long l2 = P[((size_t)r * k2max + c) * 2];
-        const long long h2 = (long long)P[((size_t)r * k2max + c) * 2 + 1];
-        const unsigned long long l = l1 + l2;
-        const long long h = h1 + h2 + (l < l1 ? 1 : 0);
-        lo = (l >> 1) | ((unsigned long long)h << 63);
-        hi = h >> 1;
+        lo = P[((size_t)c * k2max + r) * 2];
+        hi = (long long)P[((size_t)c * k2max + r) * 2 + 1];
     };
     auto add = [](unsigned long long &lo, long long &hi, unsigned long long lo2, long long hi2, bool sub) {
         if (sub) {  // negate (lo2, hi2)
@@ -515,29 +524,34 @@ __global__ void __launch_bounds__(256) gram_fixed_to_double_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Update: one block per (128-row tile, pair). Two-sided power-of-two scaling
-// keeps every entry's digits relative to a scale close to its own size:
+// Update: one block per (128-row tile, pair), in correction form
+//     Y = X W2 = X + X (W2 - I),
+// so that only the correction goes through digits: its error scales with
+// ||W2 - I|| and not with the largest entry of each row of X, and the identity
+// part is the exact FP64 entry of X. (W2 - I is exact for the diagonal entries
+// near 1 by Sterbenz's lemma.) Two-sided power-of-two scaling keeps every
+// digit relative to a scale close to its own size:
 // X = [Xr Xi] = Xh D with D = diag(2^e_c) the column exponents of the pivot
-// columns, so Y = X W2 = Xh (D W2), W2 = [[Wr, Wi], [-Wi, Wr]].
+// columns, so X (W2 - I) = Xh (D (W2 - I)), W2 = [[Wr, Wi], [-Wi, Wr]].
 // A operand: digits of the rows of Xh (per-row exponent r_l of the
-// column-normalized rows); B operand: digits of the columns of D W2 (per-column
-// exponent w_j). Both scalings are exact (exponent shifts of the digit
-// extraction). All diagonal groups (s of them, N columns each) live in TMEM
-// at once; one commit, one drain into int64 fixed-point accumulators, then
-// Y = acc * 2^(r_l + w_j - F).
+// column-normalized rows); B operand: digits of the columns of D (W2 - I)
+// (per-column exponent w_j). Both scalings are exact (exponent shifts of the
+// digit extraction). All diagonal groups (s of them, N columns each) live in
+// TMEM at once; one commit, one drain into int64 fixed-point accumulators,
+// then Y = X + acc * 2^(r_l + w_j - F).
 // ---------------------------------------------------------------------------
-constexpr int UZ_THREADS = 256;
+constexpr int UZ_THREADS = 512;
 constexpr int UZ_M = 128;
-constexpr int UZ_ASLICE = UZ_M * 128;       // 128 rows x 128 B
+constexpr int UZ_ASLICE = UZ_M * 128;       // 128 rows x 128 B (per digit)
 constexpr int UZ_BSLICE = kOzMaxK2 * 128;   // 64 rows x 128 B
 constexpr int UZ_F = 56;                    // fixed-point fraction bits of the update
 
 template <bool CPLX>
-__global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
+__global__ void __launch_bounds__(UZ_THREADS, 1) update_ozaki_kernel(
     const double *__restrict__ Gs, double *__restrict__ Gd, int64_t ld, int64_t m,
     const int32_t *__restrict__ pairs, const double *__restrict__ Wb, int kmax,
     const int32_t *__restrict__ cexp, int slices, unsigned long long *__restrict__ counters,
-    StepCtl ctl) {
+    StepCtl ctl, UpdDigits ud) {
     extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = sm;                               // slices x 128 x 128 B
@@ -576,7 +590,7 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
         return Gs[gcol(a) * ld + l];
     };
     // W2[a][j]
-    auto w2val = [&](int a, int j) -> double {
+    auto w2raw = [&](int a, int j) -> double {
         if (CPLX) {
             const int ar = a < k ? a : a - k, jr = j < k ? j : j - k;
             const double re = Wp[((size_t)jr * kmax + ar) * 2], im = Wp[((size_t)jr * kmax + ar) * 2 + 1];
@@ -585,6 +599,7 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
         }
         return Wp[(size_t)j * kmax + a];
     };
+    auto w2val = [&](int a, int j) -> double { return a == j ? w2raw(a, j) - 1.0 : w2raw(a, j); };
 
     if (warp == 0) tmem_alloc(su32(&tmem_base_sh), 512);
     if (tid == 0) {
@@ -592,68 +607,106 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         s_abort = 0;
     }
-    // zero operand tiles (padding rows/columns must be zero)
-    for (int i = tid; i < s * (UZ_ASLICE + UZ_BSLICE) / 16; i += UZ_THREADS)
-        reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    // zero operand tiles when they have padding (K2 below the 64-wide tile)
+    if (K2 < 64)
+        for (int i = tid; i < s * (UZ_ASLICE + UZ_BSLICE) / 16; i += UZ_THREADS)
+            reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
     for (int a = tid; a < K2; a += UZ_THREADS) {
         const int c = CPLX ? (a < k ? a : a - k) : a;
         xexp[a] = cexp[gcol(c)];
     }
     __syncthreads();
+    const bool wpre = ud.img != nullptr;  // W-side digits produced by the inner solve
+    if (wpre) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(ud.img + (size_t)blockIdx.y * s * kUpdSliceBytes);
+        for (int i = tid; i < s * kUpdSliceBytes / 16; i += UZ_THREADS)
+            reinterpret_cast<uint4 *>(sB)[i] = src[i];
+        for (int j = tid; j < 64; j += UZ_THREADS) wexp[j] = ud.wexp[(size_t)blockIdx.y * 64 + j];
+    } else {
     // column exponents of D W2: max over a of (exponent of W2_aj) + e_a, from the
-    // exponent fields (a power-of-two product changes only the exponent)
-    for (int j = warp; j < K2; j += UZ_THREADS / 32) {
-        int mx = -100000;
-        for (int a = lane; a < K2; a += 32) {
-            const double w = w2val(a, j);
-            if (w != 0.0) {
-                const int ew = exp_of_bits((unsigned long long)__double_as_longlong(fabs(w)));
-                mx = max(mx, ew + xexp[a]);
+        // exponent fields (a power-of-two product changes only the exponent)
+        for (int j = warp; j < K2; j += UZ_THREADS / 32) {
+            int mx = -100000;
+            for (int a = lane; a < K2; a += 32) {
+                const unsigned long long mb = mag_bits(w2val(a, j));
+                if (mb) mx = max(mx, exp_of_bits(mb) + xexp[a]);
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) wexp[j] = mx == -100000 ? -1021 : mx;
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) wexp[j] = mx == -100000 ? -1021 : mx;
+        }
     }
-    // row exponents of Xh = X D^-1: two threads per row (halves of the columns)
+    // row exponents of Xh = X D^-1: four threads per row (quarters of the columns)
     {
         const int r = tid & (UZ_M - 1), hf = tid >> 7;
         const int64_t l = l0 + r;
         int mx = -100000;
-        if (l < m)
-            for (int a = hf; a < K2; a += 2) {
-                const double x = xval(l, a);
-                if (x != 0.0)
-                    mx = max(mx, exp_of_bits((unsigned long long)__double_as_longlong(fabs(x))) - xexp[a]);
+        if (l < m) {
+            double xs[kOzMaxK2 / 4];
+#pragma unroll
+            for (int q = 0; q < kOzMaxK2 / 4; ++q) {
+                const int a = hf + 4 * q;
+                xs[q] = a < K2 ? xval(l, a) : 0.0;
             }
-        if (hf == 1) rmax_sh[r] = mx;
+#pragma unroll
+            for (int q = 0; q < kOzMaxK2 / 4; ++q) {
+                const int a = hf + 4 * q;
+                const unsigned long long mb = mag_bits(xs[q]);
+                if (a < K2 && mb) mx = max(mx, exp_of_bits(mb) - xexp[a]);
+            }
+        }
+        if (hf == 0) rmax_sh[r] = mx;
         __syncthreads();
+        for (int h = 1; h < 4; ++h) {
+            if (hf == h) rmax_sh[r] = max(rmax_sh[r], mx);
+            __syncthreads();
+        }
         if (hf == 0) {
-            const int o = max(rmax_sh[r], mx);
+            const int o = rmax_sh[r];
             rexp[r] = o == -100000 ? -1021 : o;
         }
     }
     __syncthreads();
-    // digits of the columns of D W2: B operand row j, K position a;
-    // (D W2)_aj < 2^w_j  <=>  W2_aj < 2^(w_j - e_a)
-    for (int idx = tid; idx < K2 * K2; idx += UZ_THREADS) {
-        const int a = idx % K2, j = idx / K2;
-        const double x = w2val(a, j);
-        const unsigned long long q = fixed63(x, wexp[j] - xexp[a]);
-        const uint32_t off = sw128_off(j, a * 2);
-        for (int t = 1; t <= s; ++t)
-            *reinterpret_cast<__half *>(sB + (t - 1) * UZ_BSLICE + off) = digit(q, x < 0.0, t);
+    if (!wpre) {
+        // digits of the columns of D W2: B operand row j, K position a;
+        // (D W2)_aj < 2^w_j  <=>  W2_aj < 2^(w_j - e_a)
+        for (int idx = tid; idx < K2 * K2; idx += UZ_THREADS) {
+            const int a = idx % K2, j = idx / K2;
+            const double x = w2val(a, j);
+            const unsigned long long q = fixed63(x, wexp[j] - xexp[a]);
+            const uint32_t off = sw128_off(j, a * 2);
+            const bool ng = neg_bits(x);
+            for (int t = 1; t <= s; ++t)
+                *reinterpret_cast<__half *>(sB + (t - 1) * UZ_BSLICE + off) = digit(q, ng, t);
+        }
     }
-    // digits of X rows: A operand row r, K position a (consecutive threads take
-    // consecutive rows of one column: coalesced loads)
-    for (int idx = tid; idx < UZ_M * K2; idx += UZ_THREADS) {
-        const int r = idx % UZ_M, a = idx / UZ_M;
-        const int64_t l = l0 + r;
-        const double x = l < m ? xval(l, a) : 0.0;
-        const unsigned long long q = fixed63(x, rexp[r] + xexp[a]);  // Xh_la < 2^r_l
-        const uint32_t off = sw128_off(r, a * 2);
-        for (int t = 1; t <= s; ++t)
-            *reinterpret_cast<__half *>(sA + (t - 1) * UZ_ASLICE + off) = digit(q, x < 0.0, t);
+    // digits of X rows: A operand row r, K positions a, a+1 (consecutive threads
+    // take consecutive rows of one column pair: coalesced loads, one 32-bit
+    // shared store per digit)
+    const int K2h = (K2 + 1) / 2;
+    constexpr int UZ_ITEMS = UZ_M * (kOzMaxK2 / 2) / UZ_THREADS;
+    {
+        double xv0[UZ_ITEMS], xv1[UZ_ITEMS];
+#pragma unroll
+        for (int it = 0; it < UZ_ITEMS; ++it) {
+            const int idx = tid + it * UZ_THREADS;
+            const int r = idx % UZ_M, a = (idx / UZ_M) * 2;
+            const int64_t l = l0 + r;
+            xv0[it] = (l < m && a < K2) ? xval(l, a) : 0.0;
+            xv1[it] = (l < m && a + 1 < K2) ? xval(l, a + 1) : 0.0;
+        }
+#pragma unroll
+        for (int it = 0; it < UZ_ITEMS; ++it) {
+            const int idx = tid + it * UZ_THREADS;
+            const int r = idx % UZ_M, a = (idx / UZ_M) * 2;
+            if (a >= 2 * K2h) continue;
+            const unsigned long long q0 = fixed63(xv0[it], rexp[r] + xexp[a]);  // Xh_la < 2^r_l
+            const unsigned long long q1 = fixed63(xv1[it], rexp[r] + xexp[a + 1]);
+            const bool n0 = neg_bits(xv0[it]), n1 = neg_bits(xv1[it]);
+            const uint32_t off = sw128_off(r, a * 2);
+            for (int t = 1; t <= s; ++t)
+                *reinterpret_cast<uint32_t *>(sA + (t - 1) * UZ_ASLICE + off) = dg_digits2_bits(q0, n0, q1, n1, t);
+        }
     }
     fence_async_smem();
     tc_fence_before();
@@ -678,25 +731,22 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
         }
         mma_commit(su32(&bar_done));
     }
-    __syncwarp();
-    if (!mbar_wait(su32(&bar_done), 0)) {
-        if (lane == 0) s_abort = 1;
-    }
-    tc_fence_after();
+    if (tid == 0 && !mbar_wait(su32(&bar_done), 0)) s_abort = 1;
     __syncthreads();
+    tc_fence_after();
     if (!s_abort) {
-        // thread: TMEM lane quadrant warp%4 (rows), column half warp/4
+        // thread: TMEM lane quadrant warp%4 (rows), column quarter warp/4
         const int quad = warp & 3, hfc = warp >> 2;
         const int r = quad * 32 + lane;
         const int64_t l = l0 + r;
-        const int jbase = hfc * 32;
-        long long acc[32];
+        const int jbase = hfc * 16;
+        long long acc[16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = 0;
+        for (int j = 0; j < 16; ++j) acc[j] = 0;
         for (int d = 2; d <= s + 1; ++d) {
             const int sh = UZ_F - kBeta * d;  // may be negative for the lowest digits
 #pragma unroll
-            for (int j0 = 0; j0 < 32; j0 += 8) {
+            for (int j0 = 0; j0 < 16; j0 += 8) {
                 if (jbase + j0 >= NP) break;
                 uint32_t v[8];
                 tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((d - 2) * NP + jbase + j0), v);
@@ -706,24 +756,33 @@ __global__ void __launch_bounds__(UZ_THREADS) update_ozaki_kernel(
                     const long long iv = (long long)__float2int_rn(__uint_as_float(v[j]));
                     if (sh >= 0)
                         acc[j0 + j] += iv << sh;
-                    else
+                    else if (sh > -62)
                         acc[j0 + j] += (iv + (1ll << (-sh - 1))) >> (-sh);
                 }
             }
         }
         if (l < m) {
+            double xo[16];
+            int64_t oo[16];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
+            for (int j = 0; j < 16; ++j) {
                 const int jj = jbase + j;
+                oo[j] = -1;
+                xo[j] = 0.0;
                 if (jj < K2) {
-                    const double y = int_scaled_to_double(acc[j], rexp[r] + wexp[jj] - UZ_F);
                     if (CPLX) {
                         const int c = jj < k ? jj : jj - k;
-                        Gd[(gcol(c) * ld + l) * 2 + (jj < k ? 0 : 1)] = y;
+                        oo[j] = (gcol(c) * ld + l) * 2 + (jj < k ? 0 : 1);
                     } else {
-                        Gd[gcol(jj) * ld + l] = y;
+                        oo[j] = gcol(jj) * ld + l;
                     }
+                    xo[j] = Gs[oo[j]];
                 }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int jj = jbase + j;
+                if (jj < K2) Gd[oo[j]] = xo[j] + int_scaled_to_double(acc[j], rexp[r] + wexp[jj] - UZ_F);
             }
         }
     } else if (tid == 0 && counters) {
@@ -742,7 +801,15 @@ cudaError_t set_smem(K kern, size_t bytes) {
 
 }  // namespace
 
-int ozaki_default_slices(bool gram) { return gram ? 9 : 8; }
+int ozaki_default_slices(bool gram) { return gram ? GZ_SLICES : 8; }
+
+int ozaki_max_update_slices(bool cplx, int kmax) {
+    const int np = ((cplx ? 2 * kmax : kmax) + 15) & ~15;
+    const int by_tmem = 512 / np;
+    const int by_smem = (227 * 1024 - 1024) / (UZ_ASLICE + UZ_BSLICE);
+    int s = by_tmem < by_smem ? by_tmem : by_smem;
+    return s < kOzUpdMaxSlices ? s : kOzUpdMaxSlices;
+}
 
 bool ozaki_supported(bool cplx, int kmax) { return (cplx ? 2 * kmax : kmax) <= kOzMaxK2; }
 
@@ -769,22 +836,22 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
                               unsigned long long *counters, cudaStream_t st, StepCtl ctl) {
     if (npairs <= 0) return cudaSuccess;
     const int k2max = cplx ? 2 * kmax : kmax;
-    if (k2max > kOzMaxK2 || slices < 1 || slices > kOzMaxSlices) return cudaErrorInvalidValue;
+    if (k2max > kOzMaxK2 || slices != GZ_SLICES) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(acc, 0, ozaki_gram_workspace_bytes(npairs, kmax, cplx), st);
     if (e != cudaSuccess) return e;
-    // rows per block: enough blocks to fill the GPU, a multiple of the chunk
-    int rpb = GZ_KC * 8;
-    while (rpb > GZ_KC && (int64_t)npairs * ((m + rpb - 1) / rpb) < 2 * 152) rpb /= 2;
+    // rows per block: enough blocks to fill the GPU, a multiple of 128 rows
+    int rpb = 2 * GZ_KC * 8;
+    while (rpb > 2 * GZ_KC && (int64_t)npairs * ((m + rpb - 1) / rpb) < 2 * 152) rpb /= 2;
     dim3 grid((unsigned)((m + rpb - 1) / rpb), npairs);
-    const size_t smem = (size_t)slices * GZ_SLICE_BYTES + 1024;
+    const size_t smem = (size_t)2 * GZ_BUF_BYTES + 1024;
     if (cplx) {
         if ((e = set_smem(gram_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
         gram_ozaki_kernel<true><<<grid, GZ_THREADS, smem, st>>>(G, ld, m, pairs, cexp, acc, k2max,
-                                                                 slices, rpb, counters, ctl);
+                                                                 rpb, counters, ctl);
     } else {
         if ((e = set_smem(gram_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
         gram_ozaki_kernel<false><<<grid, GZ_THREADS, smem, st>>>(G, ld, m, pairs, cexp, acc, k2max,
-                                                                  slices, rpb, counters, ctl);
+                                                                  rpb, counters, ctl);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 g2((unsigned)((kmax * kmax + 255) / 256), npairs);
@@ -798,22 +865,24 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
 cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
                                 const int32_t *pairs, int npairs, const double *W, int kmax,
                                 const int32_t *cexp, int slices, unsigned long long *counters,
-                                cudaStream_t st, StepCtl ctl) {
+                                cudaStream_t st, StepCtl ctl, UpdDigits ud) {
     if (npairs <= 0) return cudaSuccess;
     const int k2max = cplx ? 2 * kmax : kmax;
-    // all s diagonal groups of N <= 64 columns must fit the 512 TMEM columns
-    if (k2max > kOzMaxK2 || slices < 1 || slices > 8) return cudaErrorInvalidValue;
+    // all s diagonal groups of N columns must fit the 512 TMEM columns
+    const int np = (k2max + 15) & ~15;
+    if (k2max > kOzMaxK2 || slices < 1 || slices > kOzUpdMaxSlices || slices * np > 512)
+        return cudaErrorInvalidValue;
     const size_t smem = (size_t)slices * (UZ_ASLICE + UZ_BSLICE) + 1024;
     dim3 grid((unsigned)((m + UZ_M - 1) / UZ_M), npairs);
     cudaError_t e;
     if (cplx) {
         if ((e = set_smem(update_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
         update_ozaki_kernel<true><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
-                                                                   cexp, slices, counters, ctl);
+                                                                   cexp, slices, counters, ctl, ud);
     } else {
         if ((e = set_smem(update_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
         update_ozaki_kernel<false><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
-                                                                    cexp, slices, counters, ctl);
+                                                                    cexp, slices, counters, ctl, ud);
     }
     return cudaGetLastError();
 }

@@ -25,7 +25,7 @@ JJ_GEMM_FP64, JJ_GEMM_OZAKI_FP16, JJ_GEMM_OZAKI_GRAM, JJ_GEMM_AUTO = 0, 1, 2, 3
 EXPORTS = [
     "jjacobi_default_params", "jjacobi_create", "jjacobi_solve", "jjacobi_extract",
     "jjacobi_solve_host", "jjacobi_solve_batched", "jjacobi_destroy",
-    "jjacobi_status_string", "jjacobi_version", "jjacobi_schedule",
+    "jjacobi_status_string", "jjacobi_version", "jjacobi_schedule", "jjacobi_kernel_times",
     "jjk_column_norms", "jjk_plain_step", "jjk_gram", "jjk_inner", "jjk_update", "jjk_extract",
     "jjk_gram_noalloc",
 ]
@@ -37,7 +37,7 @@ class jj_params(ctypes.Structure):
                 ("order", ctypes.c_int32), ("gemm", ctypes.c_int32),
                 ("ozaki_slices", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("inner_max_sweeps", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32)]
 
 
 class jj_info(ctypes.Structure):
@@ -45,7 +45,8 @@ class jj_info(ctypes.Structure):
                 ("rotations", ctypes.c_int64), ("last_max_offdiag", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("block_width", ctypes.c_int32),
                 ("nbl", ctypes.c_int32), ("steps_per_sweep", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int32), ("pairs_evaluated", ctypes.c_int64),
+                ("pairs_rotated", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,6 +84,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "jjacobi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "jjacobi_version": (i32, []),
         "jjacobi_schedule": (i32, [i32, i32, i32, vp]),
+        "jjacobi_kernel_times": (ctypes.c_int, [vp, vp, vp]),
         "jjk_column_norms": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, vp]),
         "jjk_plain_step": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, i32, vp, vp, dbl, vp, vp]),
         "jjk_gram": (ctypes.c_int, [i32, i32, vp, i64, i64, vp, i32, vp, i32, vp]),
@@ -158,7 +160,8 @@ class Handle:
     def __init__(self, m: int, n: int, dtype: int, block_width: int = 0,
                  inner_block_width: int = 0, order: int = JJ_ORDER_ROUND_ROBIN,
                  gemm: int = JJ_GEMM_FP64, tol: float = 0.0, max_sweeps: int = 0,
-                 inner_max_sweeps: int = 0, ozaki_slices: int = 0, stream=None):
+                 inner_max_sweeps: int = 0, ozaki_slices: int = 0, stream=None,
+                 profile: bool = False):
         lib = load()
         p = jjacobi_default_params(m, n, dtype)
         p.block_width = block_width
@@ -174,6 +177,7 @@ class Handle:
             p.inner_max_sweeps = inner_max_sweeps
         sp = _stream_ptr(stream)
         p.cuda_stream = sp
+        p.profile = 1 if profile else 0
         self.params = p
         self.h = ctypes.c_void_p()
         _check(lib.jjacobi_create(ctypes.byref(self.h), ctypes.byref(p)), "jjacobi_create")
@@ -202,6 +206,15 @@ class Handle:
         rc = load().jjacobi_solve(self.h, _ptr(G), int(ldg), Jc.ctypes.data, ctypes.byref(info))
         _check(rc, "jjacobi_solve", allow)
         return info
+
+    def jjacobi_kernel_times(self):
+        """(ms, launches) per kernel family: gram, inner, update, plain step, norms."""
+        t = np.zeros(8, dtype=np.float64)
+        n = np.zeros(8, dtype=np.int64)
+        _check(load().jjacobi_kernel_times(self.h, t.ctypes.data, n.ctypes.data),
+               "jjacobi_kernel_times")
+        names = ["gram", "inner", "update", "plain_step", "norms"]
+        return {k: (float(t[i]), int(n[i])) for i, k in enumerate(names)}
 
     def jjacobi_extract(self, lam, U=None, ldu: int = 0, sort: int = 0) -> None:
         _check(load().jjacobi_extract(self.h, _ptr(lam), _ptr(U), int(ldu), int(sort)),

@@ -129,7 +129,7 @@ def test_inner_matches_oracle(cplx):
     Ad = (torch.view_as_real(Ad) if cplx else Ad).reshape(-1).contiguous()
     Wd = torch.zeros_like(Ad)
     Jd = torch.from_numpy(P.J.astype(np.int8)).cuda()
-    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
     pd = torch.from_numpy(pairs).cuda()
     jj.jjk_inner(dtype_of(P.G), Ad, Wd, kmax, pd, len(pairs), Jd, 0.0, 30, 0, cnt)
     torch.cuda.synchronize()
@@ -223,7 +223,7 @@ def test_one_parallel_step_through_building_blocks(gemm):
     A = torch.zeros(len(pairs) * kmax * kmax * 2, dtype=torch.float64, device="cuda")
     W = torch.zeros_like(A)
     Jd = torch.from_numpy(P.J.astype(np.int8)).cuda()
-    cnt = torch.zeros(4, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
     jj.jjk_gram(jj.JJ_C128, gemm, Gs, Gs.stride(1), P.m, pd, len(pairs), A, kmax)
     jj.jjk_inner(jj.JJ_C128, A, W, kmax, pd, len(pairs), Jd, 0.0, 30, 0, cnt)
     jj.jjk_update(jj.JJ_C128, gemm, Gs, Gd, Gs.stride(1), P.m, pd, len(pairs), W, kmax)
