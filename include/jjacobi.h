@@ -122,10 +122,10 @@ typedef struct {
 void jjacobi_default_params(jj_params *p, int64_t m, int64_t n, int32_t dtype);
 
 /* Create a solver handle for problems of size p->m x p->n: validates the
- * parameters, allocates every device workspace (the ping-pong copies of G that
- * hold the block columns of the update (Sec. 3.3), the pivot Gram/R/W blocks,
- * the ordering tables and counters). Returns JJ_INVALID_ARG or JJ_CUDA_ERROR on
- * failure, with *h set to NULL. */
+ * parameters, allocates every device workspace (the work copy of G, whose
+ * block columns the update transforms in place (Sec. 3.3), the pivot Gram/R/W
+ * blocks, the ordering tables and counters). Returns JJ_INVALID_ARG or
+ * JJ_CUDA_ERROR on failure, with *h set to NULL. */
 int jjacobi_create(jj_handle *h, const jj_params *p);
 
 /* Solve H = G J G^* in place: G (device, m x n, leading dimension ldg >= m,
@@ -148,13 +148,23 @@ int jjacobi_extract(jj_handle h, double *lambda, void *U, int64_t ldu, int32_t s
 int jjacobi_solve_host(jj_handle h, const void *G_host, int64_t ldg, const int8_t *J,
                        double *lambda_host, void *U_host, int64_t ldu, jj_info *info);
 
-/* Batched solve of `count` independent problems of uneven order in one stream
- * of launches (every parallel step of every problem in one launch per kernel).
- * G[k] (device, m[k] x n[k], ldg[k]) is overwritten by G~_k; J[k] host.
- * The handle's m and n are the maxima allowed (p->m >= max m[k], p->n >= max n[k]);
- * infos (may be NULL) receives one jj_info per problem. lambda_out (device,
- * sum of n[k] doubles, problem k at offset sum_{l<k} n[l]) receives the
- * eigenvalues if not NULL. */
+/* Batched solve of `count` independent problems of uneven order: the problems
+ * sit side by side in one work matrix, each with its own block partition (3.3)
+ * and parallel ordering (Sec. 4), and parallel step t of the batch runs step t
+ * of every problem in one launch per kernel (one CUDA graph per sweep). Each
+ * problem stops being transformed after its first sweep without rotations.
+ * G[k] (device, m[k] x n[k], ldg[k] >= m[k], 1 <= n[k] <= m[k]) is overwritten
+ * by G~_k in its own column order; J[k] (host, n[k] entries of +-1).
+ * The handle's m and n bound the sizes (m[k] <= p->m, n[k] <= p->n); its
+ * block_width is used for every problem (capped at ceil(n[k]/2)), or, when 0,
+ * the widest block the contraction form takes (16 complex / 32 real columns for
+ * the digit forms, 32 for FP64). Workspaces are (re)allocated on the first call
+ * and kept while the shapes repeat. lambda_out (host or device, detected; sum of
+ * n[k] doubles, problem k at offset sum_{l<k} n[l], each in its own column
+ * order) receives lambda_i = J_ii ||g~_i||^2 if not NULL. infos (may be NULL)
+ * receives one jj_info per problem (pairs_evaluated, pairs_rotated,
+ * kernel_launches, seconds and last_max_offdiag are batch totals). Returns the
+ * first non-OK problem status, else JJ_OK. jjacobi_extract does not apply. */
 int jjacobi_solve_batched(jj_handle h, int32_t count, void *const *G, const int64_t *m,
                           const int64_t *n, const int64_t *ldg, const int8_t *const *J,
                           double *lambda_out, jj_info *infos);

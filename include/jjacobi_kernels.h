@@ -61,7 +61,9 @@ int jjk_inner(int32_t dtype, double *A, double *W, int32_t kmax, const int32_t *
               int32_t inner_block_width, unsigned long long *counters, void *stream);
 
 /* Block update (K-c, (2.9)): [Gd_i Gd_j] = [Gs_i Gs_j] W_p for every pair
- * (Gs and Gd may not overlap; both use ld and the pair's column offsets). */
+ * (both use ld and the pair's column offsets). Gd may equal Gs (in place: each
+ * block reads every row it writes before writing it); otherwise the two must
+ * not overlap. */
 int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld,
                int64_t m, const int32_t *pairs, int32_t npairs, const double *W,
                int32_t kmax, void *stream);

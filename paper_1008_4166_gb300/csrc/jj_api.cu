@@ -11,24 +11,53 @@
 
 using namespace jj;
 
+// Blocked sweep plan: one or more independent problems side by side in one
+// work matrix (a single solve is a plan of one problem). Problem p owns the
+// work columns [coff_p, coff_p + n_p), rows [0, m_p), with its own uniform
+// block partition (3.3) and parallel ordering (Sec. 4); step t of the sweep
+// runs the pairs of step t of every problem that has one.
+struct Plan {
+    int count = 0;
+    std::vector<int64_t> pm, pn;        // shapes the plan was built for (caller order)
+    std::vector<int> order;             // packing position -> caller index
+    std::vector<int64_t> coff;          // by caller index: first work column
+    std::vector<int> bw, nbl, psteps;   // by caller index
+    int64_t ncols = 0, ldw = 0;
+    int steps = 0, maxnp = 0, kmax = 0, slots = 0;
+    std::vector<int> step_np, step_slot0;
+    int block_param = 0;                // block_width the plan was built with
+};
+
 struct jj_ctx {
     jj_params p{};
     bool cplx = false;
     int E = 1;  // doubles per element
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int64_t m = 0, n = 0, ldw = 0;
+    int64_t m = 0, n = 0;
     double tol = kDefaultTol;
     int max_sweeps = 60, inner_max_sweeps = 30;
 
-    // ordering / blocks
+    // plain (non-blocked) form
     bool blocked = false;
-    int bw = 0, nbl = 0, steps = 0, npairs = 0, kmax = 0;
-    std::vector<int32_t> offs, sizes;
-    int32_t *d_pairs = nullptr;   // blocked: [steps][npairs][4]; plain: [steps][npairs][2]
-    double *Gw[2] = {nullptr, nullptr};
-    double *Ablk = nullptr, *Wblk = nullptr;
+    int steps = 0, npairs = 0;
+    int32_t *d_ppairs = nullptr;  // [steps][npairs][2]
     double *d_norm = nullptr;
+    double *Gp = nullptr;         // work copy of G for the plain form
+    int64_t ldp = 0;              // its leading dimension
+    int32_t *d_pperm = nullptr;   // work column -> caller column
+    int8_t *d_pJw = nullptr;      // J in work order
+    cudaGraphExec_t graph_plain = nullptr;
+    int launches_plain = 0;
+
+    // blocked form
+    Plan P;
+    bool plan_batched = false;
+    int32_t *d_pairs = nullptr;   // [slots][4]: (offset_i, size_i, offset_j, size_j)
+    int32_t *d_rows = nullptr;    // [slots] rows of the pair's problem (batched plans)
+    int32_t *d_prob = nullptr;    // [slots] problem of the pair (batched plans)
+    double *Gw = nullptr;         // work matrix (updated in place)
+    double *Ablk = nullptr, *Wblk = nullptr;
     bool ozaki = false;                 // Gram on the tensor cores (fp16 digits)
     bool ozaki_update = false;          // update on the tensor cores too
     int32_t *d_mod = nullptr, *d_clean = nullptr, *d_flags = nullptr, *d_sweep = nullptr;
@@ -37,14 +66,20 @@ struct jj_ctx {
     int oz_slices_gram = 8, oz_slices_update = 8;
     int32_t *d_cexp = nullptr;          // column exponents (Ozaki Gram)
     unsigned long long *d_ozacc = nullptr;  // int128 Gram accumulators
+    unsigned long long *d_prob_rot = nullptr, *h_prob_rot = nullptr;  // [2 count]
+    // batched gather/scatter tables
+    double **d_bptr = nullptr;
+    int64_t *d_bld = nullptr, *d_brows = nullptr, *d_blamoff = nullptr;
+    int32_t *d_bcolprob = nullptr;
 
-    int32_t *d_perm = nullptr;    // work column -> caller column
+    int32_t *d_perm = nullptr;    // work column -> caller column (within its problem)
     int32_t *d_rank = nullptr;    // extraction with sorting: column -> rank of its lambda
     int8_t *d_Jw = nullptr;       // J in work order
-    int8_t *d_Jorig = nullptr;    // J in caller order
+    int8_t *d_Jorig = nullptr;    // J in caller order (single solve)
     unsigned long long *d_cnt = nullptr, *h_cnt = nullptr;
-    double *d_lam = nullptr;      // extraction temp (n)
-    double *h_lam = nullptr;      // pinned (n)
+    double *d_lam = nullptr;      // extraction temp
+    double *h_lam = nullptr;      // pinned
+    int64_t lam_cap = 0;
     double *d_Ghost = nullptr;    // device copy for jjacobi_solve_host (lazy)
     double *d_Uhost = nullptr;
 
@@ -53,7 +88,7 @@ struct jj_ctx {
     bool solved = false;
     int launches_per_sweep = 0;
 
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph = nullptr;  // one sweep of the current plan
     cudaEvent_t ev_legacy = nullptr;  // orders a private stream after the legacy stream
     // profiling (params.profile): events around each kernel family of each step
     std::vector<cudaEvent_t> pev;
@@ -76,6 +111,11 @@ __global__ void sweep_begin_kernel(int32_t *sweep) { *sweep += 1; }
         }                                                                               \
     } while (0)
 
+template <typename T>
+cudaError_t dmalloc(T **p, size_t count) {
+    return cudaMalloc((void **)p, count ? count * sizeof(T) : 1);
+}
+
 int status_from_flags(unsigned long long err) {
     if (err & kErrNonfinite) return JJ_NONFINITE;
     if (err & kErrNotPosdef) return JJ_NOT_POSDEF;
@@ -83,38 +123,227 @@ int status_from_flags(unsigned long long err) {
     return JJ_OK;
 }
 
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+void free_plan(jj_ctx *c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    dfree(c->d_pairs);
+    dfree(c->d_rows);
+    dfree(c->d_prob);
+    dfree(c->Gw);
+    dfree(c->Ablk);
+    dfree(c->Wblk);
+    dfree(c->d_cexp);
+    dfree(c->d_ozacc);
+    dfree(c->d_wdig);
+    dfree(c->d_wdexp);
+    dfree(c->d_mod);
+    dfree(c->d_clean);
+    dfree(c->d_flags);
+    dfree(c->d_sweep);
+    dfree(c->d_prob_rot);
+    dfree(c->d_bptr);
+    dfree(c->d_bld);
+    dfree(c->d_brows);
+    dfree(c->d_blamoff);
+    dfree(c->d_bcolprob);
+    dfree(c->d_perm);
+    dfree(c->d_Jw);
+    if (c->h_prob_rot) cudaFreeHost(c->h_prob_rot);
+    c->h_prob_rot = nullptr;
+    c->P = Plan();
+}
+
 void free_ctx(jj_ctx *c) {
     if (!c) return;
-    for (auto &g : c->graph)
-        if (g) cudaGraphExecDestroy(g);
-    cudaFree(c->d_pairs);
-    cudaFree(c->Gw[0]);
-    cudaFree(c->Gw[1]);
-    cudaFree(c->Ablk);
-    cudaFree(c->Wblk);
-    cudaFree(c->d_cexp);
-    cudaFree(c->d_ozacc);
-    cudaFree(c->d_wdig);
-    cudaFree(c->d_wdexp);
-    cudaFree(c->d_mod);
-    cudaFree(c->d_clean);
-    cudaFree(c->d_flags);
-    cudaFree(c->d_sweep);
-    cudaFree(c->d_norm);
-    cudaFree(c->d_perm);
-    cudaFree(c->d_rank);
-    cudaFree(c->d_Jw);
-    cudaFree(c->d_Jorig);
-    cudaFree(c->d_cnt);
-    cudaFree(c->d_lam);
-    cudaFree(c->d_Ghost);
-    cudaFree(c->d_Uhost);
+    free_plan(c);
+    if (c->graph_plain) cudaGraphExecDestroy(c->graph_plain);
+    dfree(c->d_ppairs);
+    dfree(c->Gp);
+    dfree(c->d_pperm);
+    dfree(c->d_pJw);
+    dfree(c->d_norm);
+    dfree(c->d_rank);
+    dfree(c->d_Jorig);
+    dfree(c->d_cnt);
+    dfree(c->d_lam);
+    dfree(c->d_Ghost);
+    dfree(c->d_Uhost);
     if (c->h_cnt) cudaFreeHost(c->h_cnt);
     if (c->h_lam) cudaFreeHost(c->h_lam);
     if (c->ev_legacy) cudaEventDestroy(c->ev_legacy);
     for (auto e : c->pev) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+// Capacity of the extraction buffers (device and pinned host) in doubles.
+int ensure_lam(jj_ctx *c, int64_t count) {
+    if (count <= c->lam_cap) return JJ_OK;
+    dfree(c->d_lam);
+    if (c->h_lam) cudaFreeHost(c->h_lam);
+    c->h_lam = nullptr;
+    c->lam_cap = 0;
+    JJ_CUDA(dmalloc(&c->d_lam, (size_t)count));
+    JJ_CUDA(cudaMallocHost((void **)&c->h_lam, (size_t)count * sizeof(double)));
+    c->lam_cap = count;
+    return JJ_OK;
+}
+
+// Block width of one problem of a batched plan when the caller fixes none:
+// the widest block the digit kernels take (complex 16, real 32 columns), or
+// 32 for the FP64 form, never wider than half the problem.
+int batch_block_width(const jj_ctx *c, int64_t n) {
+    int b = c->p.block_width > 0 ? c->p.block_width
+                                 : (c->p.gemm == JJ_GEMM_FP64 ? 32 : (c->cplx ? 16 : 32));
+    if (b > (n + 1) / 2) b = (int)((n + 1) / 2);
+    return b < 1 ? 1 : b;
+}
+
+// Build the blocked plan for `count` problems (ms, ns in caller order; bws the
+// block widths) and allocate every buffer that depends on it.
+int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const int *bws,
+               bool batched) {
+    free_plan(c);
+    Plan &P = c->P;
+    P.count = count;
+    P.pm.assign(ms, ms + count);
+    P.pn.assign(ns, ns + count);
+    P.block_param = c->p.block_width;
+    P.order.resize(count);
+    std::iota(P.order.begin(), P.order.end(), 0);
+    // larger problems first: their pairs lead every step
+    std::stable_sort(P.order.begin(), P.order.end(),
+                     [&](int a, int b) { return ns[a] > ns[b]; });
+    P.coff.assign(count, 0);
+    P.bw.assign(count, 0);
+    P.nbl.assign(count, 0);
+    P.psteps.assign(count, 0);
+    int64_t mmax = 1;
+    for (int k = 0; k < count; ++k) {
+        const int p = P.order[k];
+        P.coff[p] = P.ncols;
+        P.ncols += ns[p];
+        mmax = std::max(mmax, ms[p]);
+    }
+    P.ldw = (mmax + 3) & ~int64_t(3);
+    // per-problem partitions and orderings
+    std::vector<std::vector<int32_t>> offs(count), sizes(count), sched(count);
+    for (int p = 0; p < count; ++p) {
+        const int64_t n = ns[p];
+        if (n < 2) continue;  // one column: nothing to orthogonalise
+        const int b = bws[p];
+        int nbl = (int)(2 * ((n + 2 * (int64_t)b - 1) / (2 * (int64_t)b)));
+        if (nbl > n - (n & 1)) nbl = (int)(n - (n & 1));
+        if (nbl < 2) nbl = 2;
+        P.bw[p] = b;
+        P.nbl[p] = nbl;
+        const int br = (int)(n % nbl), nmin = (int)(n / nbl);
+        sizes[p].resize(nbl);
+        offs[p].resize(nbl + 1);
+        offs[p][0] = 0;
+        for (int l = 0; l < nbl; ++l) {
+            sizes[p][l] = l < br ? nmin + 1 : nmin;  // uniform partition (3.3)
+            offs[p][l + 1] = offs[p][l] + sizes[p][l];
+        }
+        P.kmax = std::max(P.kmax, 2 * (nmin + (br ? 1 : 0)));
+        sched[p].resize((size_t)2 * nbl * nbl);
+        P.psteps[p] = schedule_pairs(nbl, c->p.order, 1, sched[p].data());
+        if (P.psteps[p] < 0) return JJ_INVALID_ARG;
+        P.steps = std::max(P.steps, P.psteps[p]);
+    }
+    if (P.kmax < 2) P.kmax = 2;
+    std::vector<int32_t> tab, rows, prob;
+    for (int t = 0; t < P.steps; ++t) {
+        P.step_slot0.push_back(P.slots);
+        int np = 0;
+        for (int k = 0; k < count; ++k) {
+            const int p = P.order[k];
+            if (t >= P.psteps[p]) continue;
+            const int npp = P.nbl[p] / 2;
+            for (int q = 0; q < npp; ++q) {
+                const int i = sched[p][2 * ((size_t)t * npp + q)];
+                const int j = sched[p][2 * ((size_t)t * npp + q) + 1];
+                tab.push_back((int32_t)(P.coff[p] + offs[p][i]));
+                tab.push_back(sizes[p][i]);
+                tab.push_back((int32_t)(P.coff[p] + offs[p][j]));
+                tab.push_back(sizes[p][j]);
+                rows.push_back((int32_t)ms[p]);
+                prob.push_back(p);
+                ++np;
+            }
+        }
+        P.step_np.push_back(np);
+        P.slots += np;
+        P.maxnp = std::max(P.maxnp, np);
+    }
+    c->plan_batched = batched;
+    // digit forms
+    const bool oz_ok = ozaki_supported(c->cplx, P.kmax);
+    if ((c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM) && !oz_ok)
+        return JJ_INVALID_ARG;
+    c->ozaki = oz_ok && c->p.gemm != JJ_GEMM_FP64;
+    c->ozaki_update = c->ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
+    c->oz_slices_update = ozaki_default_slices(false);
+    if (c->ozaki && c->p.ozaki_slices > 0) {
+        if (c->p.ozaki_slices > ozaki_max_update_slices(c->cplx, P.kmax)) return JJ_INVALID_ARG;
+        c->oz_slices_update = c->p.ozaki_slices;
+    }
+    // device buffers
+    const size_t np = (size_t)std::max(P.maxnp, 1);
+    JJ_CUDA(dmalloc(&c->Gw, (size_t)P.ldw * P.ncols * c->E));
+    JJ_CUDA(dmalloc(&c->Ablk, np * P.kmax * P.kmax * c->E));
+    JJ_CUDA(dmalloc(&c->Wblk, np * P.kmax * P.kmax * c->E));
+    JJ_CUDA(dmalloc(&c->d_mod, (size_t)P.ncols));
+    JJ_CUDA(dmalloc(&c->d_clean, (size_t)P.slots));
+    JJ_CUDA(dmalloc(&c->d_flags, np));
+    JJ_CUDA(dmalloc(&c->d_sweep, 1));
+    JJ_CUDA(dmalloc(&c->d_perm, (size_t)P.ncols));
+    JJ_CUDA(dmalloc(&c->d_Jw, (size_t)P.ncols));
+    if (c->ozaki) {
+        if (c->ozaki_update) {
+            JJ_CUDA(dmalloc(&c->d_wdig, np * 16 * kUpdSliceBytes));
+            JJ_CUDA(dmalloc(&c->d_wdexp, np * 64));
+        }
+        JJ_CUDA(dmalloc(&c->d_cexp, (size_t)P.ncols));
+        JJ_CUDA(cudaMalloc((void **)&c->d_ozacc, ozaki_gram_workspace_bytes((int)np, P.kmax, c->cplx)));
+    }
+    if (!tab.empty()) {
+        JJ_CUDA(dmalloc(&c->d_pairs, tab.size()));
+        JJ_CUDA(cudaMemcpy(c->d_pairs, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    if (batched) {
+        JJ_CUDA(dmalloc(&c->d_prob_rot, 2 * (size_t)count));
+        JJ_CUDA(cudaMallocHost((void **)&c->h_prob_rot, 2 * (size_t)count * sizeof(unsigned long long)));
+        if (!rows.empty()) {
+            JJ_CUDA(dmalloc(&c->d_rows, rows.size()));
+            JJ_CUDA(dmalloc(&c->d_prob, prob.size()));
+            JJ_CUDA(cudaMemcpy(c->d_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            JJ_CUDA(cudaMemcpy(c->d_prob, prob.data(), prob.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
+        JJ_CUDA(dmalloc(&c->d_bptr, (size_t)count));
+        JJ_CUDA(dmalloc(&c->d_bld, (size_t)count));
+        JJ_CUDA(dmalloc(&c->d_brows, (size_t)count));
+        JJ_CUDA(dmalloc(&c->d_blamoff, (size_t)count));
+        JJ_CUDA(dmalloc(&c->d_bcolprob, (size_t)P.ncols));
+        std::vector<int32_t> colprob(P.ncols);
+        std::vector<int64_t> lamoff(count);
+        int64_t off = 0;
+        for (int p = 0; p < count; ++p) {
+            lamoff[p] = off;
+            off += ns[p];
+            for (int64_t i = 0; i < ns[p]; ++i) colprob[P.coff[p] + i] = p;
+        }
+        JJ_CUDA(cudaMemcpy(c->d_bcolprob, colprob.data(), colprob.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        JJ_CUDA(cudaMemcpy(c->d_brows, ms, count * sizeof(int64_t), cudaMemcpyHostToDevice));
+        JJ_CUDA(cudaMemcpy(c->d_blamoff, lamoff.data(), count * sizeof(int64_t), cudaMemcpyHostToDevice));
+    }
+    return JJ_OK;
 }
 
 // Profiling: event slot of (step, point) and the kernel family between points.
@@ -124,7 +353,7 @@ struct ProfMark {
 };
 
 // Record one sweep into the stream being captured (or run it directly).
-int enqueue_sweep(jj_ctx *c, int start_buf, int *launches, std::vector<ProfMark> *marks) {
+int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *marks) {
     cudaStream_t st = c->stream;
     int L = 0;
     auto mark = [&](int family) -> int {
@@ -140,43 +369,55 @@ int enqueue_sweep(jj_ctx *c, int start_buf, int *launches, std::vector<ProfMark>
         return JJ_OK;
     };
     JJ_CUDA(cudaMemsetAsync(c->d_cnt, 0, kNumCounters * sizeof(unsigned long long), st));
-    if (!c->blocked) {
+    if (plain) {
         if (mark(4)) return JJ_CUDA_ERROR;
-        JJ_CUDA(launch_column_norms(c->cplx, c->Gw[0], c->ldw, c->m, c->n, c->d_norm, st));
+        JJ_CUDA(launch_column_norms(c->cplx, c->Gp, c->ldp, c->m, c->n, c->d_norm, st));
         ++L;
         if (mark(3)) return JJ_CUDA_ERROR;
         for (int t = 0; t < c->steps; ++t) {
-            JJ_CUDA(launch_plain_step(c->cplx, c->Gw[0], c->ldw, c->m, c->n,
-                                      c->d_pairs + (size_t)t * c->npairs * 2, c->npairs, c->d_Jw,
+            JJ_CUDA(launch_plain_step(c->cplx, c->Gp, c->ldp, c->m, c->n,
+                                      c->d_ppairs + (size_t)t * c->npairs * 2, c->npairs, c->d_pJw,
                                       c->d_norm, c->tol, c->d_cnt, st));
             ++L;
         }
         if (mark(-1)) return JJ_CUDA_ERROR;
     } else {
+        const Plan &P = c->P;
+        if (c->d_prob_rot)
+            JJ_CUDA(cudaMemsetAsync(c->d_prob_rot, 0, 2 * (size_t)P.count * sizeof(unsigned long long), st));
         sweep_begin_kernel<<<1, 1, 0, st>>>(c->d_sweep);
         JJ_CUDA(cudaGetLastError());
         ++L;
-        int cur = start_buf;
-        for (int t = 0; t < c->steps; ++t) {
-            const int32_t *pr = c->d_pairs + (size_t)t * c->npairs * 4;
+        const int64_t mrows = c->plan_batched ? P.ldw : c->m;
+        for (int t = 0; t < P.steps; ++t) {
+            const int np = P.step_np[t], s0 = P.step_slot0[t];
+            if (np == 0) continue;
+            const int32_t *pr = c->d_pairs + (size_t)s0 * 4;
             StepCtl ctl;
             ctl.mod_step = c->d_mod;
             ctl.clean_at = c->d_clean;
             ctl.flags = c->d_flags;
             ctl.sweep = c->d_sweep;
             ctl.step = t;
-            ctl.steps = c->steps;
-            ctl.npairs = c->npairs;
+            ctl.steps = P.steps;
+            ctl.npairs = np;
+            ctl.slot_base = s0;
+            if (c->d_rows) ctl.rows = c->d_rows + s0;
+            if (c->d_prob) {
+                ctl.prob = c->d_prob + s0;
+                ctl.prob_rot = c->d_prob_rot;
+            }
             if (mark(0)) return JJ_CUDA_ERROR;
             if (c->ozaki) {
-                JJ_CUDA(launch_colexp(c->cplx, c->Gw[cur], c->ldw, c->m, c->n, c->d_cexp, st));
-                JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw[cur], c->ldw, c->m, pr, c->npairs,
-                                          c->Ablk, c->kmax, c->d_cexp, c->d_ozacc,
-                                          c->oz_slices_gram, c->d_cnt, st, ctl));
+                JJ_CUDA(launch_colexp_pairs(c->cplx, c->Gw, P.ldw, mrows, pr, np, P.kmax, c->d_cexp,
+                                            st, ctl));
+                JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw, P.ldw, mrows, pr, np, c->Ablk, P.kmax,
+                                          c->d_cexp, c->d_ozacc, c->oz_slices_gram, c->d_cnt, st,
+                                          ctl));
                 L += 3;
             } else {
-                JJ_CUDA(launch_gram(c->cplx, c->p.gemm, c->Gw[cur], c->ldw, c->m, pr, c->npairs,
-                                    c->Ablk, c->kmax, st, ctl));
+                JJ_CUDA(launch_gram(c->cplx, c->p.gemm, c->Gw, P.ldw, mrows, pr, np, c->Ablk,
+                                    P.kmax, st, ctl));
                 L += 1;
             }
             if (mark(1)) return JJ_CUDA_ERROR;
@@ -187,21 +428,24 @@ int enqueue_sweep(jj_ctx *c, int start_buf, int *launches, std::vector<ProfMark>
                 ud.cexp = c->d_cexp;
                 ud.slices = c->oz_slices_update;
             }
-            JJ_CUDA(launch_inner(c->cplx, c->Ablk, c->Wblk, c->kmax, pr, c->npairs, c->d_Jw,
-                                 c->tol, c->inner_max_sweeps, c->p.inner_block_width, c->d_cnt,
-                                 st, ctl, ud));
+            JJ_CUDA(launch_inner(c->cplx, c->Ablk, c->Wblk, P.kmax, pr, np, c->d_Jw, c->tol,
+                                 c->inner_max_sweeps, c->p.inner_block_width, c->d_cnt, st, ctl,
+                                 ud));
             if (mark(2)) return JJ_CUDA_ERROR;
             if (c->ozaki_update)
-                JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m, pr,
-                                            c->npairs, c->Wblk, c->kmax, c->d_cexp,
-                                            c->oz_slices_update, c->d_cnt, st, ctl, ud));
+                JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw, c->Gw, P.ldw, mrows, pr, np, c->Wblk,
+                                            P.kmax, c->d_cexp, c->oz_slices_update, c->d_cnt, st,
+                                            ctl, ud));
             else
-                JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw[cur], c->Gw[cur ^ 1], c->ldw, c->m,
-                                      pr, c->npairs, c->Wblk, c->kmax, st, ctl));
+                JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw, c->Gw, P.ldw, mrows, pr, np,
+                                      c->Wblk, P.kmax, st, ctl));
             L += 2;
             if (mark(-1)) return JJ_CUDA_ERROR;
-            cur ^= 1;
         }
+        if (c->d_prob_rot)
+            JJ_CUDA(cudaMemcpyAsync(c->h_prob_rot, c->d_prob_rot,
+                                    2 * (size_t)P.count * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, st));
     }
     JJ_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, kNumCounters * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, st));
@@ -209,21 +453,60 @@ int enqueue_sweep(jj_ctx *c, int start_buf, int *launches, std::vector<ProfMark>
     return JJ_OK;
 }
 
-int build_graph(jj_ctx *c, int start_buf) {
-    if (c->graph[start_buf]) return JJ_OK;
+int build_graph(jj_ctx *c, bool plain) {
+    cudaGraphExec_t &ge = plain ? c->graph_plain : c->graph;
+    if (ge) return JJ_OK;
     cudaGraph_t g = nullptr;
     JJ_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int L = 0;
-    const int rc = enqueue_sweep(c, start_buf, &L, nullptr);
+    const int rc = enqueue_sweep(c, plain, &L, nullptr);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc != JJ_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return JJ_CUDA_ERROR;
     }
-    e = cudaGraphInstantiate(&c->graph[start_buf], g, 0);
+    e = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return JJ_CUDA_ERROR;
-    c->launches_per_sweep = L;
+    (plain ? c->launches_plain : c->launches_per_sweep) = L;
+    return JJ_OK;
+}
+
+// One sweep: graph launch (or direct launches with profiling), then wait for
+// the counters.
+int run_sweep(jj_ctx *c, bool plain, int *launches) {
+    cudaStream_t st = c->stream;
+    if (c->p.profile) {
+        std::vector<ProfMark> marks;
+        int L = 0;
+        const int r = enqueue_sweep(c, plain, &L, &marks);
+        if (r != JJ_OK) return r;
+        JJ_CUDA(cudaStreamSynchronize(st));
+        for (size_t i = 0; i + 1 < marks.size(); ++i) {
+            if (marks[i].family < 0) continue;
+            float ms = 0.f;
+            JJ_CUDA(cudaEventElapsedTime(&ms, c->pev[marks[i].ev], c->pev[marks[i + 1].ev]));
+            c->prof_ms[marks[i].family] += ms;
+            c->prof_n[marks[i].family] += 1;
+        }
+        *launches += L;
+    } else {
+        const int r = build_graph(c, plain);
+        if (r != JJ_OK) return r;
+        JJ_CUDA(cudaGraphLaunch(plain ? c->graph_plain : c->graph, st));
+        JJ_CUDA(cudaStreamSynchronize(st));
+        *launches += plain ? c->launches_plain : c->launches_per_sweep;
+    }
+    return JJ_OK;
+}
+
+// Blocked-state reset before a solve: no block changed, no slot clean.
+int reset_skip_state(jj_ctx *c) {
+    cudaStream_t st = c->stream;
+    JJ_CUDA(cudaMemsetAsync(c->d_mod, 0xFF, std::max<int64_t>(c->P.ncols, 1) * sizeof(int32_t), st));
+    JJ_CUDA(cudaMemsetAsync(c->d_clean, 0xFF, std::max(c->P.slots, 1) * sizeof(int32_t), st));
+    JJ_CUDA(cudaMemsetAsync(c->d_flags, 0, std::max(c->P.maxnp, 1) * sizeof(int32_t), st));
+    JJ_CUDA(cudaMemsetAsync(c->d_sweep, 0, sizeof(int32_t), st));
     return JJ_OK;
 }
 
@@ -236,8 +519,17 @@ int order_after_legacy(jj_ctx *c) {
     return JJ_OK;
 }
 
-int end_buffer_after_sweep(const jj_ctx *c, int start) {
-    return c->blocked ? (start ^ (c->steps & 1)) : 0;
+// J-sorting permutation of one problem: columns with J = +1 first (Sec. 2.3).
+bool j_sort(const int8_t *J, int64_t n, std::vector<int32_t> &perm) {
+    perm.clear();
+    perm.reserve(n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (J[i] != 1 && J[i] != -1) return false;
+        if (J[i] > 0) perm.push_back((int32_t)i);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (J[i] < 0) perm.push_back((int32_t)i);
+    return true;
 }
 
 }  // namespace
@@ -292,7 +584,7 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
     if (!p || p->n < 1 || p->m < p->n || (p->dtype != JJ_F64 && p->dtype != JJ_C128) ||
         p->block_width < 0 || p->inner_block_width < 0 ||
         (p->order != JJ_ORDER_ROUND_ROBIN && p->order != JJ_ORDER_MODULUS) ||
-        (p->gemm < JJ_GEMM_FP64 || p->gemm > JJ_GEMM_AUTO) ||
+        (p->gemm < JJ_GEMM_FP64 || p->gemm > JJ_GEMM_AUTO) || p->ozaki_slices < 0 ||
         p->n > (int64_t)1 << 30)
         return JJ_INVALID_ARG;
     jj_ctx *c = new jj_ctx();
@@ -301,7 +593,6 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
     c->E = c->cplx ? 2 : 1;
     c->m = p->m;
     c->n = p->n;
-    c->ldw = (p->m + 3) & ~int64_t(3);
     c->tol = p->tol > 0 ? p->tol : kDefaultTol;
     c->max_sweeps = p->max_sweeps > 0 ? p->max_sweeps : 60;
     c->inner_max_sweeps = p->inner_max_sweeps > 0 ? p->inner_max_sweeps : 30;
@@ -319,99 +610,42 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
             return fail(JJ_CUDA_ERROR);
     }
     const int64_t n = c->n;
-    std::vector<int32_t> tab;
+    if (cudaMalloc(&c->d_rank, n * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_Jorig, n) != cudaSuccess ||
+        cudaMalloc(&c->d_cnt, kNumCounters * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&c->h_cnt, kNumCounters * sizeof(unsigned long long)) != cudaSuccess ||
+        ensure_lam(c, n) != JJ_OK)
+        return fail(JJ_CUDA_ERROR);
     if (p->block_width == 0 || n < 4) {
         // plain: round-robin over single columns (n padded to even)
         c->blocked = false;
         const int npl = (int)(n + (n & 1));
         c->npairs = npl / 2;
         c->steps = npl - 1;
+        c->ldp = (p->m + 3) & ~int64_t(3);
+        std::vector<int32_t> tab;
         if (npl >= 2) {
             tab.resize((size_t)c->steps * c->npairs * 2);
             schedule_pairs(npl, JJ_ORDER_ROUND_ROBIN, 1, tab.data());
         }
+        if (dmalloc(&c->Gp, (size_t)c->ldp * n * c->E) != cudaSuccess ||
+            dmalloc(&c->d_norm, (size_t)n) != cudaSuccess ||
+            dmalloc(&c->d_pperm, (size_t)n) != cudaSuccess ||
+            dmalloc(&c->d_pJw, (size_t)n) != cudaSuccess)
+            return fail(JJ_CUDA_ERROR);
+        if (!tab.empty()) {
+            if (dmalloc(&c->d_ppairs, tab.size()) != cudaSuccess ||
+                cudaMemcpy(c->d_ppairs, tab.data(), tab.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(JJ_CUDA_ERROR);
+        }
     } else {
         c->blocked = true;
+        const int64_t m = p->m;
         const int b = p->block_width;
-        int nbl = (int)(2 * ((n + 2 * (int64_t)b - 1) / (2 * (int64_t)b)));
-        if (nbl > n - (n & 1)) nbl = (int)(n - (n & 1));
-        if (nbl < 2) nbl = 2;
-        c->nbl = nbl;
-        c->bw = b;
-        const int br = (int)(n % nbl), nmin = (int)(n / nbl);
-        c->sizes.resize(nbl);
-        c->offs.resize(nbl + 1);
-        c->offs[0] = 0;
-        for (int l = 0; l < nbl; ++l) {
-            c->sizes[l] = l < br ? nmin + 1 : nmin;  // uniform partition (3.3)
-            c->offs[l + 1] = c->offs[l] + c->sizes[l];
-        }
-        c->npairs = nbl / 2;
-        c->kmax = 2 * (nmin + (br ? 1 : 0));
-        std::vector<int32_t> bp((size_t)2 * nbl * nbl);
-        c->steps = schedule_pairs(nbl, p->order, 1, bp.data());
-        tab.resize((size_t)c->steps * c->npairs * 4);
-        for (int t = 0; t < c->steps; ++t)
-            for (int q = 0; q < c->npairs; ++q) {
-                const int i = bp[2 * (t * c->npairs + q)], j = bp[2 * (t * c->npairs + q) + 1];
-                int32_t *d = &tab[4 * ((size_t)t * c->npairs + q)];
-                d[0] = c->offs[i];
-                d[1] = c->sizes[i];
-                d[2] = c->offs[j];
-                d[3] = c->sizes[j];
-            }
+        const int rc = build_plan(c, 1, &m, &n, &b, false);
+        if (rc != JJ_OK) return fail(rc);
     }
-    const size_t gbytes = (size_t)c->ldw * n * c->E * sizeof(double);
-    if (cudaMalloc(&c->Gw[0], gbytes) != cudaSuccess) return fail(JJ_CUDA_ERROR);
-    if (c->blocked) {
-        if (cudaMalloc(&c->Gw[1], gbytes) != cudaSuccess) return fail(JJ_CUDA_ERROR);
-        const size_t bb = (size_t)c->npairs * c->kmax * c->kmax * c->E * sizeof(double);
-        if (cudaMalloc(&c->Ablk, bb) != cudaSuccess) return fail(JJ_CUDA_ERROR);
-        if (cudaMalloc(&c->Wblk, bb) != cudaSuccess) return fail(JJ_CUDA_ERROR);
-        const bool oz_ok = ozaki_supported(c->cplx, c->kmax);
-        if ((p->gemm == JJ_GEMM_OZAKI_FP16 || p->gemm == JJ_GEMM_OZAKI_GRAM) && !oz_ok)
-            return fail(JJ_INVALID_ARG);
-        c->ozaki = oz_ok && p->gemm != JJ_GEMM_FP64;
-        c->ozaki_update = c->ozaki && p->gemm == JJ_GEMM_OZAKI_FP16;
-        const size_t nslots = (size_t)c->steps * c->npairs;
-        if (cudaMalloc(&c->d_mod, n * sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc(&c->d_clean, nslots * sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc(&c->d_flags, c->npairs * sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc(&c->d_sweep, sizeof(int32_t)) != cudaSuccess)
-            return fail(JJ_CUDA_ERROR);
-        if (c->ozaki) {
-            if (p->ozaki_slices > 0) {
-                if (p->ozaki_slices > ozaki_max_update_slices(c->cplx, c->kmax))
-                    return fail(JJ_INVALID_ARG);
-                c->oz_slices_update = p->ozaki_slices;
-            }
-            if (c->ozaki_update &&
-                (cudaMalloc(&c->d_wdig, (size_t)c->npairs * 16 * kUpdSliceBytes) != cudaSuccess ||
-                 cudaMalloc(&c->d_wdexp, (size_t)c->npairs * 64 * sizeof(int32_t)) != cudaSuccess))
-                return fail(JJ_CUDA_ERROR);
-            if (cudaMalloc(&c->d_cexp, n * sizeof(int32_t)) != cudaSuccess ||
-                cudaMalloc(&c->d_ozacc, ozaki_gram_workspace_bytes(c->npairs, c->kmax, c->cplx)) !=
-                    cudaSuccess)
-                return fail(JJ_CUDA_ERROR);
-        }
-    } else {
-        if (cudaMalloc(&c->d_norm, n * sizeof(double)) != cudaSuccess) return fail(JJ_CUDA_ERROR);
-    }
-    if (!tab.empty()) {
-        if (cudaMalloc(&c->d_pairs, tab.size() * sizeof(int32_t)) != cudaSuccess)
-            return fail(JJ_CUDA_ERROR);
-        if (cudaMemcpy(c->d_pairs, tab.data(), tab.size() * sizeof(int32_t),
-                       cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(JJ_CUDA_ERROR);
-    }
-    if (cudaMalloc(&c->d_perm, n * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&c->d_rank, n * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&c->d_Jw, n) != cudaSuccess || cudaMalloc(&c->d_Jorig, n) != cudaSuccess ||
-        cudaMalloc(&c->d_cnt, kNumCounters * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc(&c->d_lam, n * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&c->h_cnt, kNumCounters * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&c->h_lam, n * sizeof(double)) != cudaSuccess)
-        return fail(JJ_CUDA_ERROR);
     *h = c;
     return JJ_OK;
 }
@@ -435,59 +669,38 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
     if (!c || !G || !J || ldg < c->m) return finish(JJ_INVALID_ARG);
     const int64_t n = c->n;
     std::vector<int32_t> perm;
-    perm.reserve(n);
-    for (int64_t i = 0; i < n; ++i) {
-        if (J[i] != 1 && J[i] != -1) return finish(JJ_INVALID_ARG);
-        if (J[i] > 0) perm.push_back((int32_t)i);
+    if (!j_sort(J, n, perm)) return finish(JJ_INVALID_ARG);
+    if (c->blocked && (c->plan_batched || c->P.count != 1)) {
+        const int64_t m = c->m;
+        const int b = c->p.block_width;
+        const int r = build_plan(c, 1, &m, &n, &b, false);
+        if (r != JJ_OK) return finish(r);
     }
-    for (int64_t i = 0; i < n; ++i)
-        if (J[i] < 0) perm.push_back((int32_t)i);
     std::vector<int8_t> Jw(n);
     for (int64_t i = 0; i < n; ++i) Jw[i] = J[perm[i]];
     c->solved = false;
     c->G_user = G;
     c->ldg_user = ldg;
-    inf.block_width = c->blocked ? c->bw : 0;
-    inf.nbl = c->nbl;
-    inf.steps_per_sweep = c->steps;
+    inf.block_width = c->blocked ? c->P.bw[0] : 0;
+    inf.nbl = c->blocked ? c->P.nbl[0] : 0;
+    inf.steps_per_sweep = c->blocked ? c->P.steps : c->steps;
     cudaStream_t st = c->stream;
+    const bool plain = !c->blocked;
+    double *W = plain ? c->Gp : c->Gw;
+    const int64_t ldw = plain ? c->ldp : c->P.ldw;
+    int32_t *dperm = plain ? c->d_pperm : c->d_perm;
     if (order_after_legacy(c) != JJ_OK) return finish(JJ_CUDA_ERROR);
-    JJ_CUDA(cudaMemcpyAsync(c->d_perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    JJ_CUDA(cudaMemcpyAsync(c->d_Jw, Jw.data(), n, cudaMemcpyHostToDevice, st));
+    JJ_CUDA(cudaMemcpyAsync(dperm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    JJ_CUDA(cudaMemcpyAsync(plain ? c->d_pJw : c->d_Jw, Jw.data(), n, cudaMemcpyHostToDevice, st));
     JJ_CUDA(cudaMemcpyAsync(c->d_Jorig, J, n, cudaMemcpyHostToDevice, st));
-    JJ_CUDA(launch_permute_columns(c->cplx, (const double *)G, ldg, c->Gw[0], c->ldw, c->m, n,
-                                   c->d_perm, false, st));
-    if (c->blocked) {
-        JJ_CUDA(cudaMemsetAsync(c->d_mod, 0xFF, n * sizeof(int32_t), st));
-        JJ_CUDA(cudaMemsetAsync(c->d_clean, 0xFF, (size_t)c->steps * c->npairs * sizeof(int32_t), st));
-        JJ_CUDA(cudaMemsetAsync(c->d_flags, 0, c->npairs * sizeof(int32_t), st));
-        JJ_CUDA(cudaMemsetAsync(c->d_sweep, 0, sizeof(int32_t), st));
-    }
+    JJ_CUDA(launch_permute_columns(c->cplx, (const double *)G, ldg, W, ldw, c->m, n, dperm, false,
+                                   st));
+    if (c->blocked && reset_skip_state(c) != JJ_OK) return finish(JJ_CUDA_ERROR);
     int launches = 1;
-    int cur = 0;
     int rc = JJ_NOT_CONVERGED;
     for (int sweep = 1; sweep <= c->max_sweeps; ++sweep) {
-        if (c->p.profile) {
-            std::vector<ProfMark> marks;
-            int L = 0;
-            const int r = enqueue_sweep(c, cur, &L, &marks);
-            if (r != JJ_OK) return finish(r);
-            JJ_CUDA(cudaStreamSynchronize(st));
-            for (size_t i = 0; i + 1 < marks.size(); ++i) {
-                if (marks[i].family < 0) continue;
-                float ms = 0.f;
-                JJ_CUDA(cudaEventElapsedTime(&ms, c->pev[marks[i].ev], c->pev[marks[i + 1].ev]));
-                c->prof_ms[marks[i].family] += ms;
-                c->prof_n[marks[i].family] += 1;
-            }
-            launches += L;
-        } else {
-            int r = build_graph(c, cur);
-            if (r != JJ_OK) return finish(r);
-            JJ_CUDA(cudaGraphLaunch(c->graph[cur], st));
-            JJ_CUDA(cudaStreamSynchronize(st));
-            launches += c->launches_per_sweep;
-        }
+        const int r = run_sweep(c, plain, &launches);
+        if (r != JJ_OK) return finish(r);
         inf.sweeps = sweep;
         const unsigned long long rot = c->h_cnt[kCntRot];
         inf.rotations += (int64_t)rot;
@@ -496,7 +709,6 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
         double mo;
         std::memcpy(&mo, &c->h_cnt[kCntMaxOff], sizeof(double));
         inf.last_max_offdiag = mo;
-        cur = end_buffer_after_sweep(c, cur);
         const int err = status_from_flags(c->h_cnt[kCntErr]);
         if (err != JJ_OK) {
             rc = err;
@@ -507,8 +719,7 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
             break;
         }
     }
-    JJ_CUDA(launch_permute_columns(c->cplx, c->Gw[cur], c->ldw, (double *)G, ldg, c->m, n,
-                                   c->d_perm, true, st));
+    JJ_CUDA(launch_permute_columns(c->cplx, W, ldw, (double *)G, ldg, c->m, n, dperm, true, st));
     ++launches;
     JJ_CUDA(cudaStreamSynchronize(st));
     inf.kernel_launches = launches;
@@ -559,23 +770,24 @@ int jjacobi_solve_host(jj_handle c, const void *G_host, int64_t ldg, const int8_
         return JJ_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
     const size_t esz = (size_t)c->E * sizeof(double);
-    const size_t bytes = (size_t)c->ldw * c->n * esz;
+    const int64_t ldh = (c->m + 3) & ~int64_t(3);
+    const size_t bytes = (size_t)ldh * c->n * esz;
     if (!c->d_Ghost) JJ_CUDA(cudaMalloc(&c->d_Ghost, bytes));
     if (U_host && !c->d_Uhost) JJ_CUDA(cudaMalloc(&c->d_Uhost, bytes));
     cudaStream_t st = c->stream;
-    JJ_CUDA(cudaMemcpy2DAsync(c->d_Ghost, c->ldw * esz, G_host, ldg * esz, c->m * esz, c->n,
+    JJ_CUDA(cudaMemcpy2DAsync(c->d_Ghost, ldh * esz, G_host, ldg * esz, c->m * esz, c->n,
                               cudaMemcpyHostToDevice, st));
     jj_info inf{};
-    int rc = jjacobi_solve(c, c->d_Ghost, c->ldw, J, &inf);
+    int rc = jjacobi_solve(c, c->d_Ghost, ldh, J, &inf);
     if (rc == JJ_OK || rc == JJ_NOT_CONVERGED) {
-        const int rx = jjacobi_extract(c, c->d_lam, U_host ? c->d_Uhost : nullptr, c->ldw, 0);
+        const int rx = jjacobi_extract(c, c->d_lam, U_host ? c->d_Uhost : nullptr, ldh, 0);
         if (rx != JJ_OK) rc = rx;
     }
     if (rc == JJ_OK || rc == JJ_NOT_CONVERGED) {
         JJ_CUDA(cudaMemcpyAsync(lambda_host, c->d_lam, c->n * sizeof(double),
                                 cudaMemcpyDeviceToHost, st));
         if (U_host)
-            JJ_CUDA(cudaMemcpy2DAsync(U_host, ldu * esz, c->d_Uhost, c->ldw * esz, c->m * esz,
+            JJ_CUDA(cudaMemcpy2DAsync(U_host, ldu * esz, c->d_Uhost, ldh * esz, c->m * esz,
                                       c->n, cudaMemcpyDeviceToHost, st));
         JJ_CUDA(cudaStreamSynchronize(st));
     }
@@ -585,12 +797,119 @@ int jjacobi_solve_host(jj_handle c, const void *G_host, int64_t ldg, const int8_
     return rc;
 }
 
-int jjacobi_solve_batched(jj_handle h, int32_t count, void *const *G, const int64_t *m,
+int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int64_t *m,
                           const int64_t *n, const int64_t *ldg, const int8_t *const *J,
                           double *lambda_out, jj_info *infos) {
-    (void)h; (void)count; (void)G; (void)m; (void)n; (void)ldg; (void)J; (void)lambda_out;
-    (void)infos;
-    return JJ_INVALID_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || count < 1 || !G || !m || !n || !ldg || !J) return JJ_INVALID_ARG;
+    int64_t ntot = 0;
+    for (int p = 0; p < count; ++p) {
+        if (!G[p] || !J[p] || n[p] < 1 || m[p] < n[p] || ldg[p] < m[p] || m[p] > c->m ||
+            n[p] > c->n)
+            return JJ_INVALID_ARG;
+        ntot += n[p];
+    }
+    if (ntot > ((int64_t)1 << 31) - 1) return JJ_INVALID_ARG;
+    c->solved = false;  // jjacobi_extract refers to single solves
+    // plan: reuse when the shapes repeat
+    const Plan &P0 = c->P;
+    const bool same = c->plan_batched && P0.count == count && P0.block_param == c->p.block_width &&
+                      std::equal(m, m + count, P0.pm.begin()) &&
+                      std::equal(n, n + count, P0.pn.begin());
+    if (!same) {
+        std::vector<int> bws(count);
+        for (int p = 0; p < count; ++p) bws[p] = batch_block_width(c, n[p]);
+        const int r = build_plan(c, count, m, n, bws.data(), true);
+        if (r != JJ_OK) {
+            free_plan(c);
+            return r;
+        }
+    }
+    const Plan &P = c->P;
+    cudaStream_t st = c->stream;
+    // J-sorted work order of every problem
+    std::vector<int32_t> srccol(P.ncols), perm;
+    std::vector<int8_t> Jw(P.ncols);
+    for (int p = 0; p < count; ++p) {
+        if (!j_sort(J[p], n[p], perm)) return JJ_INVALID_ARG;
+        for (int64_t i = 0; i < n[p]; ++i) {
+            srccol[P.coff[p] + i] = perm[i];
+            Jw[P.coff[p] + i] = J[p][perm[i]];
+        }
+    }
+    if (order_after_legacy(c) != JJ_OK) return JJ_CUDA_ERROR;
+    JJ_CUDA(cudaMemcpyAsync(c->d_perm, srccol.data(), P.ncols * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    JJ_CUDA(cudaMemcpyAsync(c->d_Jw, Jw.data(), P.ncols, cudaMemcpyHostToDevice, st));
+    JJ_CUDA(cudaMemcpyAsync(c->d_bptr, G, count * sizeof(void *), cudaMemcpyHostToDevice, st));
+    JJ_CUDA(cudaMemcpyAsync(c->d_bld, ldg, count * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    JJ_CUDA(launch_batch_gather(c->cplx, c->d_bptr, c->d_bld, c->d_brows, c->d_bcolprob, c->d_perm,
+                                c->Gw, P.ldw, P.ncols, st));
+    if (reset_skip_state(c) != JJ_OK) return JJ_CUDA_ERROR;
+    std::vector<jj_info> inf(count);
+    std::vector<char> done(count, 0);
+    int ndone = 0;
+    for (int p = 0; p < count; ++p) {
+        inf[p].status = JJ_NOT_CONVERGED;
+        inf[p].block_width = P.bw[p];
+        inf[p].nbl = P.nbl[p];
+        inf[p].steps_per_sweep = P.psteps[p];
+    }
+    int launches = 2;
+    int rc = JJ_OK;
+    int64_t pairs_eval = 0, pairs_rot = 0;
+    for (int sweep = 1; sweep <= c->max_sweeps && ndone < count; ++sweep) {
+        const int r = run_sweep(c, false, &launches);
+        if (r != JJ_OK) return r;
+        pairs_eval += (int64_t)c->h_cnt[kCntPairs];
+        pairs_rot += (int64_t)c->h_cnt[kCntPairsRot];
+        double mo;
+        std::memcpy(&mo, &c->h_cnt[kCntMaxOff], sizeof(double));
+        if (c->h_cnt[kCntErr] & kErrTimeout) {
+            rc = JJ_DEVICE_TIMEOUT;
+            break;
+        }
+        for (int p = 0; p < count; ++p) {
+            if (done[p]) continue;
+            const unsigned long long rot = c->h_prob_rot[2 * p];
+            const int err = status_from_flags(c->h_prob_rot[2 * p + 1]);
+            inf[p].sweeps = sweep;
+            inf[p].rotations += (int64_t)rot;
+            inf[p].last_max_offdiag = mo;
+            if (err != JJ_OK || rot == 0) {
+                inf[p].status = err != JJ_OK ? err : JJ_OK;
+                done[p] = 1;
+                ++ndone;
+            }
+        }
+    }
+    // scatter back, with the eigenvalues (lambda_out host or device)
+    double *lam = nullptr;
+    bool lam_dev = false;
+    if (lambda_out) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, lambda_out) == cudaSuccess)
+            lam_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+        cudaGetLastError();
+        if (!lam_dev && ensure_lam(c, P.ncols) != JJ_OK) return JJ_CUDA_ERROR;
+        lam = lam_dev ? lambda_out : c->d_lam;
+    }
+    JJ_CUDA(launch_batch_scatter(c->cplx, c->Gw, P.ldw, c->d_bptr, c->d_bld, c->d_brows,
+                                 c->d_bcolprob, c->d_perm, c->d_blamoff, c->d_Jw, lam, P.ncols, st));
+    if (lambda_out && !lam_dev)
+        JJ_CUDA(cudaMemcpyAsync(lambda_out, c->d_lam, P.ncols * sizeof(double), cudaMemcpyDeviceToHost, st));
+    JJ_CUDA(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int worst = rc;
+    for (int p = 0; p < count; ++p) {
+        if (rc != JJ_OK) inf[p].status = rc;
+        inf[p].seconds = secs;
+        inf[p].kernel_launches = launches;
+        inf[p].pairs_evaluated = pairs_eval;
+        inf[p].pairs_rotated = pairs_rot;
+        if (worst == JJ_OK && inf[p].status != JJ_OK) worst = inf[p].status;
+        if (infos) infos[p] = inf[p];
+    }
+    return worst;
 }
 
 // ---------------------------------------------------------------------------

@@ -99,10 +99,12 @@ __global__ void __launch_bounds__(256) gram_fp64_kernel(const double *__restrict
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int b = b0 + tx + 16 * j;
-            if (a < k && b < k) {
+            // one writer per entry: on a diagonal tile only a <= b (the (b, a)
+            // sum is rounded in another order and must not race with it)
+            if (a < k && b < k && (ta != tb || a <= b)) {
                 Ap[((int64_t)b * kmax + a) * E] = acc[i][j][0];
-                if (CPLX) Ap[((int64_t)b * kmax + a) * E + 1] = acc[i][j][E - 1];
-                if (ta != tb || a != b) {
+                if (CPLX) Ap[((int64_t)b * kmax + a) * E + 1] = a == b ? 0.0 : acc[i][j][E - 1];
+                if (a != b) {
                     Ap[((int64_t)a * kmax + b) * E] = acc[i][j][0];
                     if (CPLX) Ap[((int64_t)a * kmax + b) * E + 1] = -acc[i][j][E - 1];
                 }
@@ -112,93 +114,107 @@ __global__ void __launch_bounds__(256) gram_fp64_kernel(const double *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// Update, FP64: Gd[:, pivot cols] = Gs[:, pivot cols] * W_P. One block per
-// (64-row x 32-column tile, pair).
+// Update, FP64 (2.9): [G_i G_j] <- [G_i G_j] W_P for the rows of one tile. One
+// block per (tile of VR rows, pair) computes every output column of its rows,
+// so the tile of X is read completely (into shared memory) before any output
+// is written: the update is done in place (Gd may equal Gs). W_P is staged
+// through shared memory VKA rows at a time. Thread (rg, cg) owns rows
+// rg + 8 i and columns cg + 32 j of a chunk of 32 NJ output columns.
 // ---------------------------------------------------------------------------
-constexpr int UR = 64, UC = 32, UK = 16;
+constexpr int VKA = 16;  // rows of W_P per stage
 
-template <bool CPLX>
-__global__ void __launch_bounds__(256) update_fp64_kernel(const double *__restrict__ Gs,
-                                                           double *__restrict__ Gd, int64_t ld,
+template <bool CPLX, int NJ>
+__global__ void __launch_bounds__(256) update_fp64_kernel(const double *Gs, double *Gd, int64_t ld,
                                                            int64_t m, const int32_t *__restrict__ pairs,
                                                            const double *__restrict__ W, int kmax,
-                                                           StepCtl ctl) {
+                                                           int VR, StepCtl ctl) {
     constexpr int E = CPLX ? 2 : 1;
-    __shared__ double xs[UK][UR][E];
-    __shared__ double ws[UK][UC][E];
-    const int32_t *pd = pairs + 4 * blockIdx.z;
+    constexpr int KW = 32 * NJ;  // output columns per chunk
+    extern __shared__ double usm[];
+    double *xs = usm;                              // [a][r][e], k x VR
+    double *ws = usm + (size_t)kmax * VR * E;      // [a'][c][e], VKA x KW
+    const int q = blockIdx.y;
+    const int32_t *pd = pairs + 4 * q;
     const int k = pd[1] + pd[3];
-    const int b0 = blockIdx.y * UC;
-    if (b0 >= k) return;
-    const int64_t l0 = (int64_t)blockIdx.x * UR;
-    if (pair_passthrough(ctl, blockIdx.z)) {
-        pair_copy_rows(CPLX, Gs, Gd, ld, pd, l0, min(m, l0 + UR), b0, min(k, b0 + UC), threadIdx.x, 256);
+    const int64_t mq = pair_rows(ctl, q, m);
+    const int64_t l0 = (int64_t)blockIdx.x * VR;
+    if (l0 >= mq) return;
+    const int64_t l1 = min(mq, l0 + VR);
+    if (pair_passthrough(ctl, q)) {
+        if (Gd != Gs) pair_copy_rows(CPLX, Gs, Gd, ld, pd, l0, l1, 0, k, threadIdx.x, 256);
         return;
     }
-    const double *Wp = W + (int64_t)blockIdx.z * kmax * kmax * E;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // outputs rows ty+16i (4), cols tx+16j (2)
-    double acc[4][2][E];
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < k * VR; idx += 256) {
+        const int a = idx / VR, r = idx % VR;
+        const int64_t l = l0 + r;
+        const int64_t col = pivot_col(pd, a);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+        for (int e = 0; e < E; ++e) xs[((size_t)a * VR + r) * E + e] = l < l1 ? Gs[(col * ld + l) * E + e] : 0.0;
+    }
+    const double *Wp = W + (size_t)q * kmax * kmax * E;
+    const int rg = tid & 7, cg = tid >> 3;
+    const int nri = VR / 8;  // rows per thread (<= 4)
+    for (int c0 = 0; c0 < k; c0 += KW) {
+        double acc[4][NJ][E];
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc[i][j][e] = 0.0;
-    for (int a0 = 0; a0 < k; a0 += UK) {
-        // X tile: UK columns x UR rows (4 entries per thread)
+            for (int j = 0; j < NJ; ++j)
 #pragma unroll
-        for (int v = 0; v < (UK * UR) / 256; ++v) {
-            const int idx = threadIdx.x + 256 * v;
-            const int q = idx / UR, r = idx % UR;
-            const int a = a0 + q;
-            const int64_t l = l0 + r;
-            const bool ok = a < k && l < m;
-            const int64_t col = ok ? pivot_col(pd, a) : 0;
+                for (int e = 0; e < E; ++e) acc[i][j][e] = 0.0;
+        for (int a0 = 0; a0 < k; a0 += VKA) {
+            __syncthreads();  // X tile complete / previous W stage consumed
+            for (int idx = tid; idx < VKA * KW; idx += 256) {
+                const int aa = idx % VKA, c = idx / VKA;
+                const int a = a0 + aa, b = c0 + c;
+                const bool ok = a < k && b < k;
 #pragma unroll
-            for (int e = 0; e < E; ++e) xs[q][r][e] = ok ? Gs[(col * ld + l) * E + e] : 0.0;
-        }
-        // W tile: UK rows x UC columns (2 entries per thread)
+                for (int e = 0; e < E; ++e)
+                    ws[((size_t)aa * KW + c) * E + e] = ok ? Wp[((size_t)b * kmax + a) * E + e] : 0.0;
+            }
+            __syncthreads();
+            const int na = min(VKA, k - a0);
+            for (int aa = 0; aa < na; ++aa) {
+                const double *xa = xs + (size_t)(a0 + aa) * VR * E;
+                const double *wa = ws + (size_t)aa * KW * E;
+                double w[NJ][E];
 #pragma unroll
-        for (int v = 0; v < (UK * UC) / 256; ++v) {
-            const int idx = threadIdx.x + 256 * v;
-            const int q = idx % UK, c = idx / UK;
-            const int a = a0 + q, b = b0 + c;
-            const bool ok = a < k && b < k;
+                for (int j = 0; j < NJ; ++j)
 #pragma unroll
-            for (int e = 0; e < E; ++e) ws[q][c][e] = ok ? Wp[((int64_t)b * kmax + a) * E + e] : 0.0;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int q = 0; q < UK; ++q) {
+                    for (int e = 0; e < E; ++e) w[j][e] = wa[(cg + 32 * j) * E + e];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = ty + 16 * i;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int c = tx + 16 * j;
+                for (int i = 0; i < 4; ++i) {
+                    if (i >= nri) break;
+                    const int r = rg + 8 * i;
                     if (CPLX) {
-                        const double xr = xs[q][r][0], xi = xs[q][r][1];
-                        const double wr = ws[q][c][0], wi = ws[q][c][1];
-                        acc[i][j][0] = fma(xr, wr, fma(-xi, wi, acc[i][j][0]));
-                        acc[i][j][E - 1] = fma(xr, wi, fma(xi, wr, acc[i][j][E - 1]));
+                        const double xr = xa[r * 2], xi = xa[r * 2 + 1];
+#pragma unroll
+                        for (int j = 0; j < NJ; ++j) {
+                            acc[i][j][0] = fma(xr, w[j][0], fma(-xi, w[j][E - 1], acc[i][j][0]));
+                            acc[i][j][E - 1] = fma(xr, w[j][E - 1], fma(xi, w[j][0], acc[i][j][E - 1]));
+                        }
                     } else {
-                        acc[i][j][0] = fma(xs[q][r][0], ws[q][c][0], acc[i][j][0]);
+                        const double x = xa[r];
+#pragma unroll
+                        for (int j = 0; j < NJ; ++j) acc[i][j][0] = fma(x, w[j][0], acc[i][j][0]);
                     }
                 }
             }
         }
-        __syncthreads();
-    }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t l = l0 + ty + 16 * i;
+        for (int i = 0; i < 4; ++i) {
+            if (i >= nri) break;
+            const int64_t l = l0 + rg + 8 * i;
+            if (l >= l1) continue;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int b = b0 + tx + 16 * j;
-            if (l < m && b < k) {
-                const int64_t col = pivot_col(pd, b);
+            for (int j = 0; j < NJ; ++j) {
+                const int b = c0 + cg + 32 * j;
+                if (b < k) {
+                    const int64_t col = pivot_col(pd, b);
 #pragma unroll
-                for (int e = 0; e < E; ++e) Gd[(col * ld + l) * E + e] = acc[i][j][e];
+                    for (int e = 0; e < E; ++e) Gd[(col * ld + l) * E + e] = acc[i][j][e];
+                }
             }
         }
     }
@@ -300,6 +316,7 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
         if (tid == 0) {
             atomicOr(&counters[kCntErr], kErrNotPosdef);
             pair_record(ctl, pd, blockIdx.x, false, true);
+            pair_flag_prob(ctl, blockIdx.x, kErrNotPosdef);
         }
         // leave W = I so that the update is the identity
         for (int64_t t = tid; t < (int64_t)k * k; t += IT) {
@@ -373,7 +390,10 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
                 const double absa = CPLX ? sqrt(sr * sr + si * si) : fabs(sr);
                 const double rel = absa / sqrt(da * db);
                 if (!isfinite(rel)) {
-                    if (lane == 0) atomicOr(&counters[kCntErr], kErrNonfinite);
+                    if (lane == 0) {
+                        atomicOr(&counters[kCntErr], kErrNonfinite);
+                        pair_flag_prob(ctl, blockIdx.x, kErrNonfinite);
+                    }
                     continue;
                 }
                 maxoff = fmax(maxoff, rel);
@@ -381,7 +401,10 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
                 Rot Q;
                 const bool ok = rotation(da, db, sr, si, jsh[a] * jsh[b], CPLX, Q);
                 if (!ok) {
-                    if (lane == 0) atomicOr(&counters[kCntErr], kErrNotPosdef);
+                    if (lane == 0) {
+                        atomicOr(&counters[kCntErr], kErrNotPosdef);
+                        pair_flag_prob(ctl, blockIdx.x, kErrNotPosdef);
+                    }
                     continue;
                 }
                 if (lane == 0) {
@@ -421,6 +444,7 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
         atomicAdd(&counters[kCntPairs], 1ull);
         if (total_rot) atomicAdd(&counters[kCntPairsRot], 1ull);
         pair_record(ctl, pd, blockIdx.x, total_rot > 0, false);
+        pair_count_prob(ctl, blockIdx.x, total_rot);
     }
 }
 
@@ -513,6 +537,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         if (tid == 0) {
             atomicOr(&counters[kCntErr], kErrNotPosdef);
             pair_record(ctl, pd, blockIdx.x, false, true);
+            pair_flag_prob(ctl, blockIdx.x, kErrNotPosdef);
         }
         for (int t = tid; t < k * k; t += ST) {
             const int a = t % k, b = t / k;
@@ -644,6 +669,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
                         const double rel = absa / sqrt(da * db);
                         if (!isfinite(rel)) {
                             atomicOr(&counters[kCntErr], kErrNonfinite);
+                            pair_flag_prob(ctl, blockIdx.x, kErrNonfinite);
                         } else {
                             maxoff = fmax(maxoff, rel);
                             if (rel > tol) {
@@ -658,6 +684,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
                                     ++my_rot;
                                 } else {
                                     atomicOr(&counters[kCntErr], kErrNotPosdef);
+                                    pair_flag_prob(ctl, blockIdx.x, kErrNotPosdef);
                                 }
                             }
                         }
@@ -784,6 +811,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         atomicAdd(&counters[kCntPairs], 1ull);
         if (total_rot) atomicAdd(&counters[kCntPairsRot], 1ull);
         pair_record(ctl, pd, blockIdx.x, total_rot > 0, false);
+        pair_count_prob(ctl, blockIdx.x, total_rot);
     }
 }
 
@@ -814,12 +842,35 @@ cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int
                           int kmax, cudaStream_t st, StepCtl ctl) {
     (void)gemm;
     if (npairs <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((m + UR - 1) / UR), (kmax + UC - 1) / UC, npairs);
-    if (cplx)
-        update_fp64_kernel<true><<<grid, 256, 0, st>>>(Gs, Gd, ld, m, pairs, W, kmax, ctl);
-    else
-        update_fp64_kernel<false><<<grid, 256, 0, st>>>(Gs, Gd, ld, m, pairs, W, kmax, ctl);
-    return cudaGetLastError();
+    const int E = cplx ? 2 : 1;
+    const int nj = kmax <= 32 ? 1 : kmax <= 64 ? 2 : (cplx || kmax <= 128) ? 4 : 8;
+    // rows per tile: 32, fewer when the X tile would not fit shared memory
+    int vr = 32;
+    auto smem = [&](int r) { return sizeof(double) * E * ((size_t)kmax * r + (size_t)VKA * 32 * nj); };
+    while (vr > 8 && smem(vr) > 200 * 1024) vr /= 2;
+    if (smem(vr) > 227 * 1024) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((m + vr - 1) / vr), npairs);
+    const size_t sb = smem(vr);
+#define JJ_UPD(C, N)                                                                          \
+    do {                                                                                      \
+        auto kern = update_fp64_kernel<C, N>;                                                 \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)sb);                                        \
+        if (e != cudaSuccess) return e;                                                       \
+        kern<<<grid, 256, sb, st>>>(Gs, Gd, ld, m, pairs, W, kmax, vr, ctl);                  \
+        return cudaGetLastError();                                                            \
+    } while (0)
+    if (cplx) {
+        if (nj == 1) JJ_UPD(true, 1);
+        if (nj == 2) JJ_UPD(true, 2);
+        JJ_UPD(true, 4);
+    } else {
+        if (nj == 1) JJ_UPD(false, 1);
+        if (nj == 2) JJ_UPD(false, 2);
+        if (nj == 4) JJ_UPD(false, 4);
+        JJ_UPD(false, 8);
+    }
+#undef JJ_UPD
 }
 
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,

@@ -105,12 +105,17 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, doub
 // is exact. Stamps are global step indices T = sweep * steps + step.
 struct StepCtl {
     int32_t *mod_step = nullptr;      // [n]: by block start column, step of the last change (-1: never)
-    int32_t *clean_at = nullptr;      // [steps * npairs]: step when the slot was found clean (-1: not)
+    int32_t *clean_at = nullptr;      // [slots]: step when the slot was found clean (-1: not)
     int32_t *flags = nullptr;         // [npairs]: bit 0 skipped, bit 1 identity (no rotation)
     const int32_t *sweep = nullptr;   // device sweep counter (1 in the first sweep)
     int step = 0;                     // position of this step in the sweep
     int steps = 0;                    // steps per sweep
-    int npairs = 0;                   // pairs per step
+    int npairs = 0;                   // pairs in this step
+    int slot_base = 0;                // clean_at index of pair 0 of this step
+    // Several independent problems in one work matrix (batched solve):
+    const int32_t *rows = nullptr;    // [npairs]: rows of the pair's problem (nullptr: all m)
+    const int32_t *prob = nullptr;    // [npairs]: problem of the pair
+    unsigned long long *prob_rot = nullptr;  // [2 problems]: rotations, error flags (this sweep)
 };
 constexpr int kPairSkipped = 1;
 constexpr int kPairIdentity = 2;
@@ -132,7 +137,7 @@ constexpr int kUpdSliceBytes = 64 * 128;
 // found clean at step `clean` and neither block changed after it.
 __device__ __forceinline__ bool pair_skip_decide(const StepCtl &c, const int32_t *pd, int q) {
     if (!c.mod_step) return false;
-    const int clean = c.clean_at[c.step * c.npairs + q];
+    const int clean = c.clean_at[c.slot_base + q];
     return clean >= 0 && c.mod_step[pd[0]] < clean && c.mod_step[pd[2]] < clean;
 }
 
@@ -144,12 +149,26 @@ __device__ __forceinline__ void pair_record(const StepCtl &c, const int32_t *pd,
     if (rotated) {
         c.mod_step[pd[0]] = T;
         c.mod_step[pd[2]] = T;
-        c.clean_at[c.step * c.npairs + q] = -1;
+        c.clean_at[c.slot_base + q] = -1;
         c.flags[q] = 0;
     } else {
-        c.clean_at[c.step * c.npairs + q] = failed ? -1 : T;
+        c.clean_at[c.slot_base + q] = failed ? -1 : T;
         c.flags[q] = kPairIdentity;
     }
+}
+
+// Rotations and error flags of pair q credited to its problem (batched solve):
+// prob_rot[2 p] rotations, prob_rot[2 p + 1] error flags.
+__device__ __forceinline__ void pair_count_prob(const StepCtl &c, int q, unsigned long long rot) {
+    if (c.prob_rot && rot) atomicAdd(&c.prob_rot[2 * c.prob[q]], rot);
+}
+__device__ __forceinline__ void pair_flag_prob(const StepCtl &c, int q, unsigned long long flag) {
+    if (c.prob_rot) atomicOr(&c.prob_rot[2 * c.prob[q] + 1], flag);
+}
+
+// Rows of the problem that pair q belongs to.
+__device__ __forceinline__ int64_t pair_rows(const StepCtl &c, int q, int64_t m) {
+    return c.rows ? (int64_t)c.rows[q] : m;
 }
 
 __device__ __forceinline__ bool pair_passthrough(const StepCtl &c, int q) {
@@ -190,6 +209,10 @@ bool ozaki_supported(bool cplx, int kmax);
 size_t ozaki_gram_workspace_bytes(int npairs, int kmax, bool cplx);
 cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int64_t n,
                           int32_t *cexp, cudaStream_t st);
+// Column exponents of the pivot columns of one step's pairs (grid kmax x npairs).
+cudaError_t launch_colexp_pairs(bool cplx, const double *G, int64_t ld, int64_t m,
+                                const int32_t *pairs, int npairs, int kmax, int32_t *cexp,
+                                cudaStream_t st, StepCtl ctl);
 cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
                               const int32_t *pairs, int npairs, double *A, int kmax,
                               const int32_t *cexp, unsigned long long *acc, int slices,
@@ -253,6 +276,16 @@ __device__ __forceinline__ void pair_copy_rows(bool cplx, const double *Gs, doub
             Gd[col * ld + l] = Gs[col * ld + l];
     }
 }
+
+// Batched solve: problems <-> one work matrix (jj_batch.cu).
+cudaError_t launch_batch_gather(bool cplx, const double *const *src, const int64_t *ld,
+                                const int64_t *rows, const int32_t *colprob,
+                                const int32_t *srccol, double *Gw, int64_t ldw, int64_t ncols,
+                                cudaStream_t st);
+cudaError_t launch_batch_scatter(bool cplx, const double *Gw, int64_t ldw, double *const *dst,
+                                 const int64_t *ld, const int64_t *rows, const int32_t *colprob,
+                                 const int32_t *srccol, const int64_t *lamoff, const int8_t *Jw,
+                                 double *lambda, int64_t ncols, cudaStream_t st);
 
 // Host-side ordering tables (jj_schedule.cpp).
 int schedule_pairs(int nbl, int order, int sweep, int32_t *pairs);

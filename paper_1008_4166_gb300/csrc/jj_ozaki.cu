@@ -233,6 +233,40 @@ __global__ void __launch_bounds__(256) colexp_kernel(const double *__restrict__ 
     }
 }
 
+// Column exponents of the pivot columns of the pairs of one step, over the
+// rows of each pair's problem: one block per (pivot column, pair). Pairs the
+// Gram will skip (unchanged since found diagonal) are left out.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) colexp_pairs_kernel(const double *__restrict__ G, int64_t ld,
+                                                            int64_t m, const int32_t *__restrict__ pairs,
+                                                            int32_t *__restrict__ cexp, StepCtl ctl) {
+    __shared__ unsigned long long sh[8];
+    const int q = blockIdx.y;
+    const int32_t *pd = pairs + 4 * q;
+    const int a = blockIdx.x;
+    if (a >= pd[1] + pd[3]) return;
+    if (ctl.mod_step && pair_skip_decide(ctl, pd, q)) return;
+    const int64_t c = a < pd[1] ? (int64_t)pd[0] + a : (int64_t)pd[2] + (a - pd[1]);
+    unsigned long long mx = 0;
+    const double *g = G + c * ld * (CPLX ? 2 : 1);
+    const int64_t cnt = pair_rows(ctl, q, m) * (CPLX ? 2 : 1);
+    for (int64_t i = threadIdx.x; i < cnt; i += 256) {
+        const unsigned long long v = mag_bits(g[i]);
+        mx = v > mx ? v : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+    }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) mx = sh[w] > mx ? sh[w] : mx;
+        cexp[c] = exp_of_bits(mx);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Gram: one block per (row range, pair). The pivot's K2 real columns are the
 // 64 rows of the A operand (M = 64) and, the Gram being X^T X, the same
@@ -276,7 +310,9 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
     const int K2 = CPLX ? 2 * k : k;
     const int NP = (K2 + 15) & ~15;  // N of the MMA (multiple of 16)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    m = pair_rows(ctl, blockIdx.y, m);
     const int64_t row0 = (int64_t)blockIdx.x * rows_per_block;
+    if (row0 >= m) return;
     const int64_t row1 = min((int64_t)m, row0 + rows_per_block);
 
     if (tid == 0) s_abort = 0;
@@ -539,6 +575,8 @@ __global__ void __launch_bounds__(256) gram_fixed_to_double_kernel(
 // digit extraction). All diagonal groups (s of them, N columns each) live in
 // TMEM at once; one commit, one drain into int64 fixed-point accumulators,
 // then Y = X + acc * 2^(r_l + w_j - F).
+// Every read of a tile's rows precedes the block barrier before the MMA, so
+// the update may run in place (Gd = Gs).
 // ---------------------------------------------------------------------------
 constexpr int UZ_THREADS = 512;
 constexpr int UZ_M = 128;
@@ -548,7 +586,7 @@ constexpr int UZ_F = 56;                    // fixed-point fraction bits of the 
 
 template <bool CPLX>
 __global__ void __launch_bounds__(UZ_THREADS, 1) update_ozaki_kernel(
-    const double *__restrict__ Gs, double *__restrict__ Gd, int64_t ld, int64_t m,
+    const double *Gs, double *Gd, int64_t ld, int64_t m,
     const int32_t *__restrict__ pairs, const double *__restrict__ Wb, int kmax,
     const int32_t *__restrict__ cexp, int slices, unsigned long long *__restrict__ counters,
     StepCtl ctl, UpdDigits ud) {
@@ -566,9 +604,12 @@ __global__ void __launch_bounds__(UZ_THREADS, 1) update_ozaki_kernel(
 
     const int32_t *pd = pairs + 4 * blockIdx.y;
     const int k = pd[1] + pd[3];
+    m = pair_rows(ctl, blockIdx.y, m);
+    if ((int64_t)blockIdx.x * UZ_M >= m) return;
     if (pair_passthrough(ctl, blockIdx.y)) {
         const int64_t r0 = (int64_t)blockIdx.x * UZ_M;
-        pair_copy_rows(CPLX, Gs, Gd, ld, pd, r0, min(m, r0 + UZ_M), 0, k, threadIdx.x, UZ_THREADS);
+        if (Gd != Gs)
+            pair_copy_rows(CPLX, Gs, Gd, ld, pd, r0, min(m, r0 + UZ_M), 0, k, threadIdx.x, UZ_THREADS);
         return;
     }
     const int K2 = CPLX ? 2 * k : k;
@@ -825,6 +866,18 @@ cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int
         colexp_kernel<true><<<(unsigned)n, 256, 0, st>>>(G, ld, m, cexp);
     else
         colexp_kernel<false><<<(unsigned)n, 256, 0, st>>>(G, ld, m, cexp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colexp_pairs(bool cplx, const double *G, int64_t ld, int64_t m,
+                                const int32_t *pairs, int npairs, int kmax, int32_t *cexp,
+                                cudaStream_t st, StepCtl ctl) {
+    if (npairs <= 0) return cudaSuccess;
+    dim3 grid((unsigned)kmax, npairs);
+    if (cplx)
+        colexp_pairs_kernel<true><<<grid, 256, 0, st>>>(G, ld, m, pairs, cexp, ctl);
+    else
+        colexp_pairs_kernel<false><<<grid, 256, 0, st>>>(G, ld, m, pairs, cexp, ctl);
     return cudaGetLastError();
 }
 

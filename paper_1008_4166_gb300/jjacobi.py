@@ -234,6 +234,25 @@ class Handle:
         _check(rc, "jjacobi_solve_host", allow)
         return lam, U, info
 
+    def jjacobi_solve_batched(self, Gs, Js, lam=None, allow=(JJ_OK,)):
+        """Solve len(Gs) independent problems (device tensors, column-major
+        m_k x n_k, leading dimension = stride(1)) in place. lam (device tensor or
+        numpy array, sum n_k doubles) receives the eigenvalues, problem k at
+        offset sum_{l<k} n_l. Returns the status and the per-problem infos."""
+        count = len(Gs)
+        ptrs = (ctypes.c_void_p * count)(*[_ptr(G) for G in Gs])
+        m = np.array([G.shape[0] for G in Gs], dtype=np.int64)
+        n = np.array([G.shape[1] for G in Gs], dtype=np.int64)
+        ld = np.array([G.stride(1) if hasattr(G, "stride") else G.shape[0] for G in Gs],
+                      dtype=np.int64)
+        Jcs = [np.ascontiguousarray(np.asarray(J, dtype=np.int8)) for J in Js]
+        jptrs = (ctypes.c_void_p * count)(*[J.ctypes.data for J in Jcs])
+        infos = (jj_info * count)()
+        rc = load().jjacobi_solve_batched(self.h, count, ptrs, m.ctypes.data, n.ctypes.data,
+                                          ld.ctypes.data, jptrs, _ptr(lam), infos)
+        _check(rc, "jjacobi_solve_batched", allow)
+        return rc, list(infos)
+
 
 # ---------------------------------------------------------------------------
 # Building blocks (include/jjacobi_kernels.h)
