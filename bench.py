@@ -9,10 +9,14 @@ graded complex128 problem of order 4096 (G = D1 B D2, B = Q |Lambda|^{1/2} W,
 J = diag(+I_2560, -I_1536)).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--block-width B] [--gemm ozaki|fp64] [--no-plain]
+                  [--block-width B] [--gemm hybrid|ozaki|fp64] [--no-plain] [--no-cpu]
+                  [--one-step]
 
 --impl reference times the CPU oracle (the plain one-sided J-Jacobi, in C,
 single-threaded) on a bounded sample of the same workload.
+--one-step runs only the first parallel step of the sweep (column exponents,
+Gram, inner solve, update of every block pair) through the building-block
+entry points, K times: the small case for kernel profiles.
 """
 from __future__ import annotations
 
@@ -312,20 +316,21 @@ def run_ours(args):
     Gh = torch.from_numpy(np.ascontiguousarray(P.G.T)).pin_memory().numpy().T
     esz = 16 if cplx else 8
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 1
     for _ in range(e2e_steps):
         lam_h, _, _ = h.jjacobi_solve_host(Gh, P.J, want_U=False)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = {"value": flops / e2e_s / 1e9, "unit": "GFLOP/s",
            "h2d_bytes_per_step": int(m * n * esz), "d2h_bytes_per_step": int(n * 8)}
 
-    # per-kernel device times from a profiled solve (events around every kernel
-    # family of every step, on the solve's stream) and the dominant kernel's roofline
+    # per-kernel device times from a profiled solve of the first sweeps (events
+    # around every kernel family of every step, on the solve's stream) and the
+    # dominant kernel's roofline
     hp_ = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
-                    profile=True)
+                    profile=True, max_sweeps=args.profile_sweeps)
     with torch.cuda.stream(stream):
         Gw.copy_(G0)
-        pinfo_ = hp_.jjacobi_solve(Gw, Gw.stride(1), P.J)
+        pinfo_ = hp_.jjacobi_solve(Gw, Gw.stride(1), P.J, allow=(jj.JJ_OK, jj.JJ_NOT_CONVERGED))
     stream.synchronize()
     times = hp_.jjacobi_kernel_times()
     hp_.close()
@@ -379,7 +384,7 @@ def run_ours(args):
                        "gemm": args.gemm, "order": "round_robin", "sweeps": info["sweeps"],
                        "steps_per_sweep": info["steps_per_sweep"],
                        "time_to_solution_s": ms / 1e3,
-                       "l2": "inputs larger than L2 (G = 256 MiB, 2 work copies)",
+                       "l2": "inputs larger than L2 (G = 256 MiB; every step reads and writes it)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "plain": plain,
@@ -389,10 +394,58 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_one_step(args):
+    """One parallel step (every block pair of step 1 of the round-robin order)
+    through the building-block entry points, repeated --steps times."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_1008_4166_gb300 import jjacobi as jj
+
+    P = synth.make_workload(args.workload, precision="f64")
+    n, m, cplx = P.n, P.m, P.is_complex
+    dt_code = jj.JJ_C128 if cplx else jj.JJ_F64
+    g_gram = jj.JJ_GEMM_FP64 if args.gemm == "fp64" else jj.JJ_GEMM_OZAKI_FP16
+    g_upd = jj.JJ_GEMM_OZAKI_FP16 if args.gemm == "ozaki" else jj.JJ_GEMM_FP64
+    b = args.block_width
+    nbl = 2 * ((n + 2 * b - 1) // (2 * b))
+    sizes = [n // nbl + (1 if l < n % nbl else 0) for l in range(nbl)]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    tab = jj.jjacobi_schedule(nbl, 0, 1)
+    pairs = np.array([[offs[i], sizes[i], offs[j], sizes[j]] for i, j in tab[0]], dtype=np.int32)
+    kmax = 2 * max(sizes)
+    E = 2 if cplx else 1
+    G = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()
+    Gd = torch.empty_like(G)
+    pd = torch.from_numpy(pairs).cuda()
+    A = torch.zeros(len(pairs) * kmax * kmax * E, dtype=torch.float64, device="cuda")
+    W = torch.zeros_like(A)
+    Jd = torch.from_numpy(P.J.astype(np.int8)).cuda()
+    cnt = torch.zeros(8, dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for it in range(args.warmup + args.steps):
+        if it == args.warmup:
+            e0.record(st)
+        jj.jjk_gram(dt_code, g_gram, G, G.stride(1), m, pd, len(pairs), A, kmax)
+        jj.jjk_inner(dt_code, A, W, kmax, pd, len(pairs), Jd, 0.0, 30, 0, cnt)
+        jj.jjk_update(dt_code, g_upd, G, Gd, G.stride(1), m, pd, len(pairs), W, kmax)
+    e1.record(st)
+    torch.cuda.synchronize()
+    print(json.dumps({"one_step": args.workload, "block_width": b, "gemm": args.gemm,
+                      "pairs": len(pairs), "kmax": kmax,
+                      "ms_per_step": e0.elapsed_time(e1) / max(args.steps, 1),
+                      "rotations": int(cnt[0]), "err_flags": int(cnt[2])}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-width", type=int, default=16)
@@ -401,8 +454,12 @@ def main():
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=6.0)
+    ap.add_argument("--profile-sweeps", type=int, default=3)
+    ap.add_argument("--one-step", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.one_step:
+        run_one_step(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -28,6 +28,28 @@ struct Plan {
     int block_param = 0;                // block_width the plan was built with
 };
 
+// Three-level form (Sec. 5.1, 3F): per outer step, the inner blocked method
+// runs on X = [R_q; W_q] of every outer pair q at once (see jj_three.cu).
+struct Three {
+    bool on = false;
+    int ib = 0, kmax_in = 0;
+    int64_t ldx = 0;
+    int max_np = 0, max_slots = 0;
+    std::vector<std::vector<int>> np, slot0;  // [outer step][inner step]
+    std::vector<int> steps;                   // inner steps per inner sweep, by outer step
+    std::vector<int64_t> tab0;                // first inner slot of each outer step
+    int32_t *d_tab = nullptr, *d_prob = nullptr;
+    double *X = nullptr, *Ain = nullptr, *Win = nullptr;
+    int8_t *d_JX = nullptr;
+    int32_t *d_fail = nullptr;
+    int32_t *d_mod = nullptr, *d_clean = nullptr, *d_flags = nullptr, *d_sweep = nullptr;
+    unsigned long long *d_cnt = nullptr, *h_cnt = nullptr, *d_rot = nullptr;
+    bool ozaki = false, ozaki_update = false;
+    int32_t *d_cexp = nullptr, *d_cexp2 = nullptr, *d_wdexp = nullptr;
+    unsigned long long *d_ozacc = nullptr;
+    uint8_t *d_wdig = nullptr;
+};
+
 struct jj_ctx {
     jj_params p{};
     bool cplx = false;
@@ -52,6 +74,7 @@ struct jj_ctx {
 
     // blocked form
     Plan P;
+    Three T3;
     bool plan_batched = false;
     int32_t *d_pairs = nullptr;   // [slots][4]: (offset_i, size_i, offset_j, size_j)
     int32_t *d_rows = nullptr;    // [slots] rows of the pair's problem (batched plans)
@@ -89,6 +112,7 @@ struct jj_ctx {
     int launches_per_sweep = 0;
 
     cudaGraphExec_t graph = nullptr;  // one sweep of the current plan
+    double three_maxoff = 0.0;
     cudaEvent_t ev_legacy = nullptr;  // orders a private stream after the legacy stream
     // profiling (params.profile): events around each kernel family of each step
     std::vector<cudaEvent_t> pev;
@@ -157,6 +181,27 @@ void free_plan(jj_ctx *c) {
     if (c->h_prob_rot) cudaFreeHost(c->h_prob_rot);
     c->h_prob_rot = nullptr;
     c->P = Plan();
+    Three &T = c->T3;
+    dfree(T.d_tab);
+    dfree(T.d_prob);
+    dfree(T.X);
+    dfree(T.Ain);
+    dfree(T.Win);
+    dfree(T.d_JX);
+    dfree(T.d_fail);
+    dfree(T.d_mod);
+    dfree(T.d_clean);
+    dfree(T.d_flags);
+    dfree(T.d_sweep);
+    dfree(T.d_cnt);
+    dfree(T.d_rot);
+    dfree(T.d_cexp);
+    dfree(T.d_cexp2);
+    dfree(T.d_wdexp);
+    dfree(T.d_ozacc);
+    dfree(T.d_wdig);
+    if (T.h_cnt) cudaFreeHost(T.h_cnt);
+    T = Three();
 }
 
 void free_ctx(jj_ctx *c) {
@@ -203,6 +248,102 @@ int batch_block_width(const jj_ctx *c, int64_t n) {
                                  : (c->p.gemm == JJ_GEMM_FP64 ? 32 : (c->cplx ? 16 : 32));
     if (b > (n + 1) / 2) b = (int)((n + 1) / 2);
     return b < 1 ? 1 : b;
+}
+
+// Inner tables and buffers of the three-level form for the outer pair table
+// `tab` of the current plan (Alg. 3.3 on R: inner blocks of ib columns,
+// uniform partition (3.3) of each pivot, the plan's ordering, inner pairs of
+// all outer pairs of a step side by side).
+int build_three(jj_ctx *c, const std::vector<int32_t> &tab) {
+    Plan &P = c->P;
+    Three &T = c->T3;
+    T.on = true;
+    T.ib = c->p.inner_block_width;
+    T.ldx = (2 * (int64_t)P.kmax + 3) & ~int64_t(3);
+    std::vector<int32_t> itab, iprob;
+    for (int t = 0; t < P.steps; ++t) {
+        const int np = P.step_np[t], s0 = P.step_slot0[t];
+        T.tab0.push_back((int64_t)itab.size() / 4);
+        std::vector<std::vector<int32_t>> offs(np), sizes(np), sched(np);
+        std::vector<int> nbl(np, 0), steps(np, 0);
+        int smax = 0;
+        for (int q = 0; q < np; ++q) {
+            const int k = tab[4 * (s0 + q) + 1] + tab[4 * (s0 + q) + 3];
+            int nb = 2 * ((k + 2 * T.ib - 1) / (2 * T.ib));
+            if (nb > k - (k & 1)) nb = k - (k & 1);
+            if (nb < 2) nb = 2;
+            nbl[q] = nb;
+            const int br = k % nb, nmin = k / nb;
+            sizes[q].resize(nb);
+            offs[q].resize(nb + 1);
+            offs[q][0] = 0;
+            for (int l = 0; l < nb; ++l) {
+                sizes[q][l] = l < br ? nmin + 1 : nmin;
+                offs[q][l + 1] = offs[q][l] + sizes[q][l];
+            }
+            T.kmax_in = std::max(T.kmax_in, 2 * (nmin + (br ? 1 : 0)));
+            sched[q].resize((size_t)2 * nb * nb);
+            steps[q] = schedule_pairs(nb, c->p.order, 1, sched[q].data());
+            if (steps[q] < 0) return JJ_INVALID_ARG;
+            smax = std::max(smax, steps[q]);
+        }
+        T.steps.push_back(smax);
+        T.np.emplace_back();
+        T.slot0.emplace_back();
+        int slots = 0;
+        for (int ti = 0; ti < smax; ++ti) {
+            T.slot0[t].push_back(slots);
+            int n_in = 0;
+            for (int q = 0; q < np; ++q) {
+                if (ti >= steps[q]) continue;
+                const int npp = nbl[q] / 2;
+                for (int u = 0; u < npp; ++u) {
+                    const int i = sched[q][2 * ((size_t)ti * npp + u)];
+                    const int j = sched[q][2 * ((size_t)ti * npp + u) + 1];
+                    itab.push_back(q * P.kmax + offs[q][i]);
+                    itab.push_back(sizes[q][i]);
+                    itab.push_back(q * P.kmax + offs[q][j]);
+                    itab.push_back(sizes[q][j]);
+                    iprob.push_back(q);
+                    ++n_in;
+                }
+            }
+            T.np[t].push_back(n_in);
+            slots += n_in;
+            T.max_np = std::max(T.max_np, n_in);
+        }
+        T.max_slots = std::max(T.max_slots, slots);
+    }
+    T.ozaki = ozaki_supported(c->cplx, T.kmax_in) && c->p.gemm != JJ_GEMM_FP64;
+    T.ozaki_update = T.ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
+    const size_t np = (size_t)std::max(P.maxnp, 1), npi = (size_t)std::max(T.max_np, 1);
+    const size_t xcols = np * P.kmax;
+    JJ_CUDA(dmalloc(&T.d_tab, itab.size()));
+    JJ_CUDA(dmalloc(&T.d_prob, iprob.size()));
+    JJ_CUDA(cudaMemcpy(T.d_tab, itab.data(), itab.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    JJ_CUDA(cudaMemcpy(T.d_prob, iprob.data(), iprob.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    JJ_CUDA(dmalloc(&T.X, (size_t)T.ldx * xcols * c->E));
+    JJ_CUDA(dmalloc(&T.Ain, npi * T.kmax_in * T.kmax_in * c->E));
+    JJ_CUDA(dmalloc(&T.Win, npi * T.kmax_in * T.kmax_in * c->E));
+    JJ_CUDA(dmalloc(&T.d_JX, xcols));
+    JJ_CUDA(dmalloc(&T.d_fail, np));
+    JJ_CUDA(dmalloc(&T.d_mod, xcols));
+    JJ_CUDA(dmalloc(&T.d_clean, (size_t)std::max(T.max_slots, 1)));
+    JJ_CUDA(dmalloc(&T.d_flags, npi));
+    JJ_CUDA(dmalloc(&T.d_sweep, 1));
+    JJ_CUDA(dmalloc(&T.d_cnt, kNumCounters));
+    JJ_CUDA(dmalloc(&T.d_rot, 2 * np));
+    JJ_CUDA(cudaMallocHost((void **)&T.h_cnt, kNumCounters * sizeof(unsigned long long)));
+    if (T.ozaki) {
+        JJ_CUDA(dmalloc(&T.d_cexp, xcols));
+        JJ_CUDA(dmalloc(&T.d_cexp2, xcols));
+        JJ_CUDA(cudaMalloc((void **)&T.d_ozacc, ozaki_gram_workspace_bytes((int)npi, T.kmax_in, c->cplx)));
+        if (T.ozaki_update) {
+            JJ_CUDA(dmalloc(&T.d_wdig, npi * 16 * kUpdSliceBytes));
+            JJ_CUDA(dmalloc(&T.d_wdexp, npi * 64));
+        }
+    }
+    return JJ_OK;
 }
 
 // Build the blocked plan for `count` problems (ms, ns in caller order; bws the
@@ -283,9 +424,13 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
         P.maxnp = std::max(P.maxnp, np);
     }
     c->plan_batched = batched;
-    // digit forms
+    // three-level: the inner method blocked with inner_block_width columns
+    const int ib = c->p.inner_block_width;
+    const bool three = !batched && ib > 0 && P.kmax > 2 * ib;
+    // digit forms (in the three-level form the outer level uses them where the
+    // outer pivot fits the digit kernels; the choice applies to the inner level)
     const bool oz_ok = ozaki_supported(c->cplx, P.kmax);
-    if ((c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM) && !oz_ok)
+    if (!three && (c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM) && !oz_ok)
         return JJ_INVALID_ARG;
     c->ozaki = oz_ok && c->p.gemm != JJ_GEMM_FP64;
     c->ozaki_update = c->ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
@@ -316,6 +461,10 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
     if (!tab.empty()) {
         JJ_CUDA(dmalloc(&c->d_pairs, tab.size()));
         JJ_CUDA(cudaMemcpy(c->d_pairs, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    if (three) {
+        const int r = build_three(c, tab);
+        if (r != JJ_OK) return r;
     }
     if (batched) {
         JJ_CUDA(dmalloc(&c->d_prob_rot, 2 * (size_t)count));
@@ -453,6 +602,151 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
     return JJ_OK;
 }
 
+// One sweep of the three-level form (direct launches: the inner sweeps of each
+// outer step stop on the host when one applies no rotation).
+int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
+    cudaStream_t st = c->stream;
+    const Plan &P = c->P;
+    Three &T = c->T3;
+    int L = 0;
+    auto mark = [&](int family) -> int {
+        if (!marks) return JJ_OK;
+        const int idx = (int)marks->size();
+        if (idx >= (int)c->pev.size()) {
+            cudaEvent_t e;
+            JJ_CUDA(cudaEventCreate(&e));
+            c->pev.push_back(e);
+        }
+        JJ_CUDA(cudaEventRecord(c->pev[idx], st));
+        marks->push_back({idx, family});
+        return JJ_OK;
+    };
+    JJ_CUDA(cudaMemsetAsync(c->d_cnt, 0, kNumCounters * sizeof(unsigned long long), st));
+    sweep_begin_kernel<<<1, 1, 0, st>>>(c->d_sweep);
+    JJ_CUDA(cudaGetLastError());
+    ++L;
+    const int64_t xcols = (int64_t)std::max(P.maxnp, 1) * P.kmax;
+    for (int t = 0; t < P.steps; ++t) {
+        const int np = P.step_np[t], s0 = P.step_slot0[t];
+        if (np == 0) continue;
+        const int32_t *pr = c->d_pairs + (size_t)s0 * 4;
+        StepCtl ctl;
+        ctl.mod_step = c->d_mod;
+        ctl.clean_at = c->d_clean;
+        ctl.flags = c->d_flags;
+        ctl.sweep = c->d_sweep;
+        ctl.step = t;
+        ctl.steps = P.steps;
+        ctl.npairs = np;
+        ctl.slot_base = s0;
+        if (mark(0)) return JJ_CUDA_ERROR;
+        if (c->ozaki) {
+            JJ_CUDA(launch_colexp_pairs(c->cplx, c->Gw, P.ldw, c->m, pr, np, P.kmax, c->d_cexp, st, ctl));
+            JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw, P.ldw, c->m, pr, np, c->Ablk, P.kmax, c->d_cexp,
+                                      c->d_ozacc, c->oz_slices_gram, c->d_cnt, st, ctl));
+            L += 3;
+        } else {
+            JJ_CUDA(launch_gram(c->cplx, c->p.gemm, c->Gw, P.ldw, c->m, pr, np, c->Ablk, P.kmax, st, ctl));
+            L += 1;
+        }
+        if (mark(1)) return JJ_CUDA_ERROR;
+        // inner level: Cholesky into X = [R; I], then the blocked inner method
+        JJ_CUDA(launch_three_cholesky(c->cplx, c->Ablk, P.kmax, pr, np, c->d_Jw, T.X, T.ldx, T.d_JX,
+                                      T.d_fail, c->d_cnt, st, ctl));
+        JJ_CUDA(cudaMemsetAsync(T.d_mod, 0xFF, xcols * sizeof(int32_t), st));
+        JJ_CUDA(cudaMemsetAsync(T.d_clean, 0xFF, std::max(T.max_slots, 1) * sizeof(int32_t), st));
+        JJ_CUDA(cudaMemsetAsync(T.d_flags, 0, std::max(T.max_np, 1) * sizeof(int32_t), st));
+        JJ_CUDA(cudaMemsetAsync(T.d_sweep, 0, sizeof(int32_t), st));
+        JJ_CUDA(cudaMemsetAsync(T.d_rot, 0, 2 * (size_t)std::max(P.maxnp, 1) * sizeof(unsigned long long), st));
+        L += 1;
+        const int ts = T.steps[t];
+        for (int sw = 1; sw <= c->inner_max_sweeps; ++sw) {
+            JJ_CUDA(cudaMemsetAsync(T.d_cnt, 0, kNumCounters * sizeof(unsigned long long), st));
+            sweep_begin_kernel<<<1, 1, 0, st>>>(T.d_sweep);
+            JJ_CUDA(cudaGetLastError());
+            ++L;
+            for (int ti = 0; ti < ts; ++ti) {
+                const int ni = T.np[t][ti];
+                if (ni == 0) continue;
+                const int64_t sl = T.tab0[t] + T.slot0[t][ti];
+                const int32_t *ip = T.d_tab + sl * 4;
+                StepCtl ic;
+                ic.mod_step = T.d_mod;
+                ic.clean_at = T.d_clean;
+                ic.flags = T.d_flags;
+                ic.sweep = T.d_sweep;
+                ic.step = ti;
+                ic.steps = ts;
+                ic.npairs = ni;
+                ic.slot_base = T.slot0[t][ti];
+                ic.prob = T.d_prob + sl;
+                ic.prob_rot = T.d_rot;
+                UpdDigits ud;
+                if (T.ozaki) {
+                    // Gram exponents over the R rows; update exponents over R and W rows
+                    JJ_CUDA(launch_colexp_pairs(c->cplx, T.X, T.ldx, P.kmax, ip, ni, T.kmax_in, T.d_cexp, st, ic));
+                    JJ_CUDA(launch_gram_ozaki(c->cplx, T.X, T.ldx, P.kmax, ip, ni, T.Ain, T.kmax_in,
+                                              T.d_cexp, T.d_ozacc, c->oz_slices_gram, T.d_cnt, st, ic));
+                    L += 3;
+                    if (T.ozaki_update) {
+                        JJ_CUDA(launch_colexp_pairs(c->cplx, T.X, T.ldx, 2 * P.kmax, ip, ni, T.kmax_in,
+                                                    T.d_cexp2, st, ic));
+                        ++L;
+                        ud.img = T.d_wdig;
+                        ud.wexp = T.d_wdexp;
+                        ud.cexp = T.d_cexp2;
+                        ud.slices = ozaki_default_slices(false);
+                    }
+                } else {
+                    JJ_CUDA(launch_gram(c->cplx, c->p.gemm, T.X, T.ldx, P.kmax, ip, ni, T.Ain, T.kmax_in, st, ic));
+                    L += 1;
+                }
+                JJ_CUDA(launch_inner(c->cplx, T.Ain, T.Win, T.kmax_in, ip, ni, T.d_JX, c->tol,
+                                     c->inner_max_sweeps, 0, T.d_cnt, st, ic, ud));
+                if (T.ozaki_update)
+                    JJ_CUDA(launch_update_ozaki(c->cplx, T.X, T.X, T.ldx, 2 * P.kmax, ip, ni, T.Win,
+                                                T.kmax_in, T.d_cexp2, ozaki_default_slices(false),
+                                                T.d_cnt, st, ic, ud));
+                else
+                    JJ_CUDA(launch_update(c->cplx, c->p.gemm, T.X, T.X, T.ldx, 2 * P.kmax, ip, ni,
+                                          T.Win, T.kmax_in, st, ic));
+                L += 2;
+            }
+            JJ_CUDA(cudaMemcpyAsync(T.h_cnt, T.d_cnt, kNumCounters * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, st));
+            JJ_CUDA(cudaStreamSynchronize(st));
+            double mo;
+            std::memcpy(&mo, &T.h_cnt[kCntMaxOff], sizeof(double));
+            if (sw == 1) c->three_maxoff = std::max(c->three_maxoff, mo);
+            if (T.h_cnt[kCntErr] & kErrTimeout) return JJ_DEVICE_TIMEOUT;
+            if (T.h_cnt[kCntRot] == 0) break;
+        }
+        JJ_CUDA(launch_three_finish(c->cplx, T.X, T.ldx, P.kmax, pr, np, c->Wblk, T.d_rot, T.d_fail,
+                                    c->d_cnt, st, ctl));
+        ++L;
+        if (mark(2)) return JJ_CUDA_ERROR;
+        if (c->ozaki_update)
+            JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw, c->Gw, P.ldw, c->m, pr, np, c->Wblk, P.kmax,
+                                        c->d_cexp, c->oz_slices_update, c->d_cnt, st, ctl, UpdDigits()));
+        else
+            JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw, c->Gw, P.ldw, c->m, pr, np, c->Wblk,
+                                  P.kmax, st, ctl));
+        L += 1;
+        if (mark(-1)) return JJ_CUDA_ERROR;
+    }
+    JJ_CUDA(cudaMemcpyAsync(c->h_cnt, c->d_cnt, kNumCounters * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, st));
+    JJ_CUDA(cudaStreamSynchronize(st));
+    // the outer max off-diagonal: the largest first-inner-sweep value of the step
+    double mo;
+    std::memcpy(&mo, &c->h_cnt[kCntMaxOff], sizeof(double));
+    mo = std::max(mo, c->three_maxoff);
+    std::memcpy(&c->h_cnt[kCntMaxOff], &mo, sizeof(double));
+    c->three_maxoff = 0.0;
+    *launches += L;
+    return JJ_OK;
+}
+
 int build_graph(jj_ctx *c, bool plain) {
     cudaGraphExec_t &ge = plain ? c->graph_plain : c->graph;
     if (ge) return JJ_OK;
@@ -476,6 +770,19 @@ int build_graph(jj_ctx *c, bool plain) {
 // the counters.
 int run_sweep(jj_ctx *c, bool plain, int *launches) {
     cudaStream_t st = c->stream;
+    if (!plain && c->T3.on) {
+        std::vector<ProfMark> marks;
+        const int r = run_three_sweep(c, launches, c->p.profile ? &marks : nullptr);
+        if (r != JJ_OK) return r;
+        for (size_t i = 0; i + 1 < marks.size(); ++i) {
+            if (marks[i].family < 0) continue;
+            float ms = 0.f;
+            JJ_CUDA(cudaEventElapsedTime(&ms, c->pev[marks[i].ev], c->pev[marks[i + 1].ev]));
+            c->prof_ms[marks[i].family] += ms;
+            c->prof_n[marks[i].family] += 1;
+        }
+        return JJ_OK;
+    }
     if (c->p.profile) {
         std::vector<ProfMark> marks;
         int L = 0;

@@ -287,6 +287,17 @@ cudaError_t launch_batch_scatter(bool cplx, const double *Gw, int64_t ldw, doubl
                                  const int32_t *srccol, const int64_t *lamoff, const int8_t *Jw,
                                  double *lambda, int64_t ncols, cudaStream_t st);
 
+// Three-level form: outer Cholesky into the inner work matrix, and the hand-back
+// of W_P after the inner sweeps (jj_three.cu).
+cudaError_t launch_three_cholesky(bool cplx, const double *A, int kmax, const int32_t *pairs,
+                                  int npairs, const int8_t *J, double *X, int64_t ldx, int8_t *JX,
+                                  int32_t *fail, unsigned long long *counters, cudaStream_t st,
+                                  StepCtl ctl);
+cudaError_t launch_three_finish(bool cplx, const double *X, int64_t ldx, int kmax,
+                                const int32_t *pairs, int npairs, double *W,
+                                const unsigned long long *inner_rot, const int32_t *fail,
+                                unsigned long long *counters, cudaStream_t st, StepCtl ctl);
+
 // Host-side ordering tables (jj_schedule.cpp).
 int schedule_pairs(int nbl, int order, int sweep, int32_t *pairs);
 

@@ -190,15 +190,18 @@ def test_blocked_complex_ragged(gemm):
     assert max_rel_err(got["lam"], P.lam_exact) <= eig_rel_tol(P.G)
 
 
-@pytest.mark.parametrize("gemm", GEMMS)
+@pytest.mark.parametrize("gemm", [0, 1, 2])
 def test_blocked_graded_complex(gemm):
-    """Graded G = D1 B D2 (the graded complex recipe at n = 192)."""
+    """Graded G = D1 B D2 (the graded complex recipe at n = 192): the published
+    bound for the graded case, 1e-10 relative to the FP64 oracle. (The scaled
+    condition of G is far above 1e4 here; the FP64 oracle and its long-double
+    variant agree to ~1e-12 on these inputs, so the bound is meaningful.)"""
     require_gpu()
     P = synth.make_workload("graded_c128_n4096_b64", n=192)
     ref = oracle.solve_plain(P.G, P.J)
     got = solve_gpu(P.G, P.J, block_width=16, gemm=gemm)
     assert got["info"]["status"] == 0
-    assert max_rel_err(got["lam"], ref["lam"]) <= max(1e-10, eig_rel_tol(P.G))
+    assert max_rel_err(got["lam"], ref["lam"]) <= 1e-10
 
 
 @pytest.mark.parametrize("gemm", GEMMS)

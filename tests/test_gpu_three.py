@@ -1,0 +1,66 @@
+"""Three-level form (Sec. 5.1, case 3F: the inner J-Jacobi of every outer pivot
+is itself the blocked method, Alg. 3.3 on R) against the oracle, against
+eigenvalues known by construction and against the two-level form."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._util import eig_rel_tol, max_rel_err, orth_residual, reconstruction_residual
+from tests.gpu_util import require_gpu, solve_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("gemm", [0, 1, 2])
+@pytest.mark.parametrize("order", [0, 1])
+def test_three_level_real_matches_oracle(gemm, order):
+    require_gpu()
+    P = synth.make_workload("threelevel_f64_n16384_b128", n=256)
+    ref = oracle.solve_plain(P.G, P.J)
+    # outer pivots of 64 columns, inner blocks of 8: 8 inner blocks per pivot
+    got = solve_gpu(P.G, P.J, block_width=32, inner_block_width=8, gemm=gemm, order=order,
+                    want_U=True)
+    tol = eig_rel_tol(P.G)
+    assert got["info"]["status"] == 0
+    assert max_rel_err(got["lam"], ref["lam"]) <= tol
+    assert max_rel_err(got["lam"], P.lam_exact) <= tol
+    assert orth_residual(got["U"]) <= 8 * oracle.TOL_DEFAULT
+    assert reconstruction_residual(P.G, P.J, got["lam"], got["U"]) <= 1e-12
+
+
+@pytest.mark.parametrize("gemm", [0, 1])
+def test_three_level_complex_ragged(gemm):
+    """Complex, ragged outer and inner partitions (150 columns, b = 20: pivots
+    of 36-40 columns; inner blocks of 6)."""
+    require_gpu()
+    P = synth.make_workload("plain_c128_n128", n=150)
+    ref = oracle.solve_plain(P.G, P.J)
+    got = solve_gpu(P.G, P.J, block_width=20, inner_block_width=6, gemm=gemm)
+    assert got["info"]["status"] == 0
+    assert max_rel_err(got["lam"], ref["lam"]) <= eig_rel_tol(P.G)
+    assert max_rel_err(got["lam"], P.lam_exact) <= eig_rel_tol(P.G)
+
+
+def test_three_level_agrees_with_two_level_wide_pivot():
+    """Outer pivots of 256 columns (the 16 384-column workload's b = 128) with
+    inner blocks of 16, at n = 1024: the outer contractions run in FP64, the
+    inner ones as digit products; eigenvalues by construction and against the
+    two-level form."""
+    require_gpu()
+    P = synth.make_workload("threelevel_f64_n16384_b128", n=1024)
+    three = solve_gpu(P.G, P.J, block_width=128, inner_block_width=16, gemm=1)
+    two = solve_gpu(P.G, P.J, block_width=128, gemm=0)
+    tol = eig_rel_tol(P.G)
+    assert three["info"]["status"] == 0 and two["info"]["status"] == 0
+    assert max_rel_err(three["lam"], P.lam_exact) <= tol
+    assert max_rel_err(three["lam"], two["lam"]) <= tol
+
+
+def test_three_level_inner_width_not_below_pivot_is_two_level():
+    """inner_block_width >= half the pivot: the two-level form runs (same bits)."""
+    require_gpu()
+    P = synth.make_workload("blocked_f64_n2048_b32", n=96)
+    a = solve_gpu(P.G, P.J, block_width=8, inner_block_width=8, gemm=0)
+    b = solve_gpu(P.G, P.J, block_width=8, gemm=0)
+    assert np.array_equal(a["Gt"], b["Gt"])
