@@ -243,18 +243,20 @@ __device__ __forceinline__ unsigned long long dg_fixed63(double x, int e) {
     return mant >> (-sh);
 }
 // 7-bit digit t (1-based) of two fixed-point values as packed fp16 bits, signed
+// by n0, n1. A digit d <= 127 comes out exactly as (1024 + d) - 1024 in fp16:
+// the bit pattern of +-(1024 + d) is (0x6400 or 0xE400) | d, and adding -+1024
+// leaves +-d. Per pair of digits: two field extracts, a byte permute, an OR and
+// one f16x2 add (the sign-dependent constants are loop invariants).
 __device__ __forceinline__ uint32_t dg_digits2_bits(unsigned long long q0, bool n0,
                                                     unsigned long long q1, bool n1, int t) {
-    const uint32_t d0 = (uint32_t)((q0 >> (63 - 7 * t)) & 127ull);
-    const uint32_t d1 = (uint32_t)((q1 >> (63 - 7 * t)) & 127ull);
-    // fp16 of an integer d < 128: exponent and significand built directly
-    auto h = [](uint32_t d) -> uint32_t {
-        if (d == 0) return 0u;
-        const int lz = __clz(d) - 16;          // leading zeros in 16 bits
-        const int e = 15 - lz;                 // d in [2^e, 2^(e+1))
-        return (uint32_t)((e + 15) << 10) | ((d << (10 - e)) & 0x3FFu);
-    };
-    return (h(d0) | (n0 ? 0x8000u : 0u)) | ((h(d1) | (n1 ? 0x8000u : 0u)) << 16);
+    const uint32_t bias = (n0 ? 0xE400u : 0x6400u) | ((n1 ? 0xE400u : 0x6400u) << 16);
+    const uint32_t add = bias ^ 0x80008000u;  // -1024 for a positive lane, +1024 for a negative one
+    const uint32_t d0 = (uint32_t)(q0 >> (63 - 7 * t)) & 127u;
+    const uint32_t d1 = (uint32_t)(q1 >> (63 - 7 * t)) & 127u;
+    const uint32_t v = __byte_perm(d0, d1, 0x5410) | bias;
+    uint32_t r;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(add));
+    return r;
 }
 __device__ __forceinline__ uint32_t dg_sw128_off(int row, int kbyte) {
     return (uint32_t)(row * 128 + ((((kbyte >> 4) ^ (row & 7))) << 4) + (kbyte & 15));
