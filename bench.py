@@ -442,6 +442,117 @@ def run_one_step(args):
                       "rotations": int(cnt[0]), "err_flags": int(cnt[2])}), flush=True)
 
 
+def run_batched(args):
+    """The batched workload: every step solves all problems (copies of the
+    resident inputs) in one jjacobi_solve_batched call."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_1008_4166_gb300 import jjacobi as jj
+
+    probs = synth.make_batched(count=args.batch_count, precision="f64")
+    gemm = {"ozaki": jj.JJ_GEMM_OZAKI_FP16, "hybrid": jj.JJ_GEMM_OZAKI_GRAM,
+            "fp64": jj.JJ_GEMM_FP64}[args.gemm]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        G0 = [torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t() for P in probs]
+        Gw = [torch.empty_like(g) for g in G0]
+        lam = torch.empty(sum(P.n for P in probs), dtype=torch.float64, device="cuda")
+    mmax = max(P.m for P in probs)
+    nmax = max(P.n for P in probs)
+    bw = args.block_width if args.block_width_set else 0
+    h = jj.Handle(mmax, nmax, jj.JJ_C128, block_width=bw, gemm=gemm, stream=stream)
+
+    def step():
+        for a, b in zip(Gw, G0):
+            a.copy_(b)
+        return h.jjacobi_solve_batched(Gw, [P.J for P in probs], lam)[1]
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos = step()
+        e1.record(stream)
+    stream.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = sum(blocked_flops(P.n, P.m, True, i.as_dict()) for P, i in zip(probs, infos)
+                if i.nbl > 0)
+    sweeps = [i.sweeps for i in infos]
+    line = {
+        "metric": "batched J-Jacobi GFLOP/s and problems/s", "value": flops / (ms * 1e-3) / 1e9,
+        "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "batched_c128_512x", "problems": len(probs),
+                   "n_range": [min(P.n for P in probs), nmax], "gemm": args.gemm,
+                   "block_widths": sorted(set(i.block_width for i in infos)),
+                   "problems_per_s": len(probs) / (ms * 1e-3),
+                   "sweeps_min_max": [min(sweeps), max(sweeps)],
+                   "launches_per_solve": infos[0].kernel_launches},
+        "clocks": clocks,
+    }
+    h.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_threelevel(args):
+    """The three-level workload (real, n = 16384, b = 128, inner blocks of 16):
+    one solve (or --max-sweeps sweeps of it), against the plain form's sweeps."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_1008_4166_gb300 import jjacobi as jj
+
+    t0 = time.time()
+    P = synth.make_workload("threelevel_f64_n16384_b128", precision="f64")
+    gen_s = time.time() - t0
+    n, m = P.n, P.m
+    gemm = {"ozaki": jj.JJ_GEMM_OZAKI_FP16, "hybrid": jj.JJ_GEMM_OZAKI_GRAM,
+            "fp64": jj.JJ_GEMM_FP64}[args.gemm]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        G0 = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()
+        Gw = torch.empty_like(G0)
+    out = {}
+    for name, kw in (("three_level", dict(block_width=128, inner_block_width=16, gemm=gemm)),
+                     ("two_level", dict(block_width=128, gemm=jj.JJ_GEMM_FP64)),
+                     ("plain", dict(block_width=0))):
+        if name not in args.forms:
+            continue
+        h = jj.Handle(m, n, jj.JJ_F64, stream=stream, max_sweeps=args.max_sweeps, **kw)
+        with torch.cuda.stream(stream):
+            Gw.copy_(G0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = h.jjacobi_solve(Gw, Gw.stride(1), P.J, allow=(jj.JJ_OK, jj.JJ_NOT_CONVERGED))
+            e1.record(stream)
+        stream.synchronize()
+        d = info.as_dict()
+        s = e0.elapsed_time(e1) / 1e3
+        out[name] = {"seconds": s, "sweeps": d["sweeps"], "s_per_sweep": s / max(d["sweeps"], 1),
+                     "status": d["status"], "rotations": d["rotations"]}
+        h.close()
+    print(json.dumps({"workload": "threelevel_f64_n16384_b128", "gemm": args.gemm,
+                      "generation_s": gen_s, "max_sweeps": args.max_sweeps, "forms": out}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,9 +567,17 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--profile-sweeps", type=int, default=3)
     ap.add_argument("--one-step", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--max-sweeps", type=int, default=0)
+    ap.add_argument("--forms", default="three_level,two_level,plain")
     args = ap.parse_args()
+    args.block_width_set = any(a.startswith("--block-width") for a in sys.argv[1:])
     if args.one_step:
         run_one_step(args)
+    elif args.workload == "batched_c128_512x":
+        run_batched(args)
+    elif args.workload == "threelevel_f64_n16384_b128":
+        run_threelevel(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -12,7 +12,8 @@
  * Forms:
  *   block_width == 0  plain, non-blocked method (Algs. 3.1/3.2) with the
  *                     round-robin parallel order over single columns.
- *   block_width  > 0  blocked full-block method (Sec. 3.3, Alg. 5.2 case 2F):
+ *   block_width  > 0  blocked full-block method (Sec. 3.3, Alg. 5.2 case 2F)
+ *                     (block_width == JJ_BLOCK_AUTO: the same, width autotuned):
  *                     per parallel step, for every block pair (i, j):
  *                     Gram A_P = [G_i G_j]^*[G_i G_j] (3.6), Cholesky
  *                     A_P = R^* R (3.8), inner J-Jacobi R W_P = U Sigma with W_P
@@ -72,6 +73,12 @@ typedef enum {
     JJ_GEMM_AUTO = 3
 } jj_gemm;
 
+/* block_width value that lets the library pick the block width: at the first
+ * solve of the handle, one sweep of every candidate width (powers of two from
+ * 8 up to the widest pivot the contraction form takes, at most n/4) is timed on
+ * a scratch copy of the input and the fastest is kept (see jj_info.block_width). */
+#define JJ_BLOCK_AUTO (-1)
+
 typedef enum {
     JJ_OK = 0,
     JJ_INVALID_ARG = 1,    /* m < n, n < 1, bad ld, J entry not +-1, bad params */
@@ -89,7 +96,7 @@ typedef struct {
     int64_t m;                 /* rows of G (m >= n) */
     int64_t n;                 /* columns of G */
     int32_t dtype;             /* jj_dtype */
-    int32_t block_width;       /* 0: plain; >0: target columns per block (b) */
+    int32_t block_width;       /* 0: plain; >0: target columns per block (b); JJ_BLOCK_AUTO */
     int32_t inner_block_width; /* 0: two-level; >0: inner block width (three-level) */
     int32_t order;             /* jj_order (blocked form; the plain form is round-robin) */
     int32_t gemm;              /* jj_gemm */
@@ -156,12 +163,16 @@ int jjacobi_solve_host(jj_handle h, const void *G_host, int64_t ldg, const int8_
  * G[k] (device, m[k] x n[k], ldg[k] >= m[k], 1 <= n[k] <= m[k]) is overwritten
  * by G~_k in its own column order; J[k] (host, n[k] entries of +-1).
  * The handle's m and n bound the sizes (m[k] <= p->m, n[k] <= p->n); its
- * block_width is used for every problem (capped at ceil(n[k]/2)), or, when 0,
+ * block_width is used for every problem (capped at ceil(n[k]/2)), or, when 0 or JJ_BLOCK_AUTO,
  * the widest block the contraction form takes (16 complex / 32 real columns for
  * the digit forms, 32 for FP64). Workspaces are (re)allocated on the first call
  * and kept while the shapes repeat. lambda_out (host or device, detected; sum of
  * n[k] doubles, problem k at offset sum_{l<k} n[l], each in its own column
- * order) receives lambda_i = J_ii ||g~_i||^2 if not NULL. infos (may be NULL)
+ * order) receives lambda_i = J_ii ||g~_i||^2 if not NULL. A problem whose blocked
+ * sweeps stop on a pivot Gram block that is not positive definite in working
+ * precision (columns too close to dependent for A_P = G_P^* G_P, Sec. 3.2) is
+ * finished by the plain method from its current columns; its jj_info then
+ * reports block_width 0. infos (may be NULL)
  * receives one jj_info per problem (pairs_evaluated, pairs_rotated,
  * kernel_launches, seconds and last_max_offdiag are batch totals). Returns the
  * first non-OK problem status, else JJ_OK. jjacobi_extract does not apply. */

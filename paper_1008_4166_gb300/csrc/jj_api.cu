@@ -113,6 +113,7 @@ struct jj_ctx {
 
     cudaGraphExec_t graph = nullptr;  // one sweep of the current plan
     double three_maxoff = 0.0;
+    int tuned_bw = 0;                 // block width chosen (0: not yet tuned)
     cudaEvent_t ev_legacy = nullptr;  // orders a private stream after the legacy stream
     // profiling (params.profile): events around each kernel family of each step
     std::vector<cudaEvent_t> pev;
@@ -839,6 +840,167 @@ bool j_sort(const int8_t *J, int64_t n, std::vector<int32_t> &perm) {
     return true;
 }
 
+// Block widths the autotuner tries (block_width = JJ_BLOCK_AUTO): powers of two
+// from 8 up to the widest pivot the chosen contraction form takes (the digit
+// kernels: 64 real columns per pivot, i.e. b <= 16 complex / 32 real), and not
+// wider than a quarter of n (at least two block pairs per step).
+std::vector<int> autotune_candidates(const jj_ctx *c) {
+    std::vector<int> out;
+    if (c->p.block_width > 0) {
+        out.push_back(c->p.block_width);
+        return out;
+    }
+    const bool digits = c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM;
+    const int bmax = digits ? (c->cplx ? 16 : 32) : 64;
+    for (int b = 8; b <= bmax; b *= 2)
+        if (4 * (int64_t)b <= c->n || b == 8) out.push_back(b);
+    return out;
+}
+
+// Autotuner: one sweep of every candidate block width on a scratch copy of G
+// (the caller's G, J-sorted), timed with CUDA events around the sweep's graph;
+// the fastest width is kept for this and every later solve of the handle.
+int autotune(jj_ctx *c, const void *G, int64_t ldg, const std::vector<int32_t> &perm,
+             const std::vector<int8_t> &Jw) {
+    const std::vector<int> cand = autotune_candidates(c);
+    cudaStream_t st = c->stream;
+    cudaEvent_t e0, e1;
+    JJ_CUDA(cudaEventCreate(&e0));
+    JJ_CUDA(cudaEventCreate(&e1));
+    float best = 0.f;
+    int best_b = cand[0];
+    const int64_t m = c->m, n = c->n;
+    int rc = JJ_OK;
+    for (int b : cand) {
+        if ((rc = build_plan(c, 1, &m, &n, &b, false)) != JJ_OK) break;
+        if (cudaMemcpyAsync(c->d_perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(c->d_Jw, Jw.data(), n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            launch_permute_columns(c->cplx, (const double *)G, ldg, c->Gw, c->P.ldw, m, n, c->d_perm,
+                                   false, st) != cudaSuccess ||
+            (rc = reset_skip_state(c)) != JJ_OK) {
+            rc = rc ? rc : JJ_CUDA_ERROR;
+            break;
+        }
+        float ms = 0.f;
+        if (c->T3.on) {
+            int L = 0;
+            cudaEventRecord(e0, st);
+            if ((rc = run_three_sweep(c, &L, nullptr)) != JJ_OK) break;
+            cudaEventRecord(e1, st);
+        } else {
+            if ((rc = build_graph(c, false)) != JJ_OK) break;
+            cudaEventRecord(e0, st);
+            cudaGraphLaunch(c->graph, st);
+            cudaEventRecord(e1, st);
+        }
+        if (cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = JJ_CUDA_ERROR;
+            break;
+        }
+        if (best == 0.f || ms < best) {
+            best = ms;
+            best_b = b;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != JJ_OK) return rc;
+    c->tuned_bw = best_b;
+    return build_plan(c, 1, &m, &n, &best_b, false);
+}
+
+// Batched solve, second phase: problems whose blocked sweeps failed because a
+// pivot Gram block was not positive definite in working precision (its
+// columns' scaled condition squared above ~1/u; the non-blocked method never
+// forms a Gram block) are finished by the plain method (Algs. 3.1/3.2, round-
+// robin over each problem's columns) from their current columns: every
+// transformation applied so far was J-unitary, so the pencil is unchanged.
+int batch_plain_finish(jj_ctx *c, const std::vector<int> &failed, std::vector<jj_info> &inf,
+                       int *launches) {
+    const Plan &P = c->P;
+    cudaStream_t st = c->stream;
+    std::vector<std::vector<int32_t>> sched(failed.size());
+    std::vector<int> steps(failed.size());
+    int smax = 0;
+    for (size_t f = 0; f < failed.size(); ++f) {
+        const int n = (int)P.pn[failed[f]];
+        const int npl = n + (n & 1);
+        sched[f].resize((size_t)npl * npl);
+        steps[f] = schedule_pairs(npl, JJ_ORDER_ROUND_ROBIN, 1, sched[f].data());
+        smax = std::max(smax, steps[f]);
+    }
+    std::vector<int32_t> tab;
+    std::vector<int> np_t, off_t;
+    for (int t = 0; t < smax; ++t) {
+        off_t.push_back((int)tab.size() / 2);
+        int np = 0;
+        for (size_t f = 0; f < failed.size(); ++f) {
+            const int p = failed[f], n = (int)P.pn[p], npl = n + (n & 1);
+            if (t >= steps[f]) continue;
+            for (int q = 0; q < npl / 2; ++q) {
+                const int i = sched[f][2 * ((size_t)t * (npl / 2) + q)];
+                const int j = sched[f][2 * ((size_t)t * (npl / 2) + q) + 1];
+                if (i >= n || j >= n) continue;  // the dummy player of an odd order
+                tab.push_back((int32_t)(P.coff[p] + i));
+                tab.push_back((int32_t)(P.coff[p] + j));
+                ++np;
+            }
+        }
+        np_t.push_back(np);
+    }
+    int32_t *d_tab = nullptr;
+    double *d_norm = nullptr;
+    int rc = JJ_OK;
+    auto done = [&](int r) {
+        dfree(d_tab);
+        dfree(d_norm);
+        return r;
+    };
+    if (dmalloc(&d_tab, std::max<size_t>(tab.size(), 2)) != cudaSuccess ||
+        dmalloc(&d_norm, (size_t)P.ncols) != cudaSuccess ||
+        cudaMemcpy(d_tab, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return done(JJ_CUDA_ERROR);
+    int status = JJ_NOT_CONVERGED, sweeps = 0;
+    int64_t rot_total = 0;
+    for (int sweep = 1; sweep <= c->max_sweeps; ++sweep) {
+        sweeps = sweep;
+        if (cudaMemsetAsync(c->d_cnt, 0, kNumCounters * sizeof(unsigned long long), st) != cudaSuccess ||
+            launch_column_norms(c->cplx, c->Gw, P.ldw, P.ldw, P.ncols, d_norm, st) != cudaSuccess)
+            return done(JJ_CUDA_ERROR);
+        ++*launches;
+        for (int t = 0; t < smax; ++t) {
+            if (np_t[t] == 0) continue;
+            if (launch_plain_step(c->cplx, c->Gw, P.ldw, P.ldw, P.ncols, d_tab + 2 * (size_t)off_t[t],
+                                  np_t[t], c->d_Jw, d_norm, c->tol, c->d_cnt, st) != cudaSuccess)
+                return done(JJ_CUDA_ERROR);
+            ++*launches;
+        }
+        if (cudaMemcpyAsync(c->h_cnt, c->d_cnt, kNumCounters * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return done(JJ_CUDA_ERROR);
+        rot_total += (int64_t)c->h_cnt[kCntRot];
+        const int err = status_from_flags(c->h_cnt[kCntErr]);
+        if (err != JJ_OK) {
+            status = err;
+            break;
+        }
+        if (c->h_cnt[kCntRot] == 0) {
+            status = JJ_OK;
+            break;
+        }
+    }
+    for (int p : failed) {
+        inf[p].status = status;
+        inf[p].sweeps += sweeps;
+        inf[p].rotations += rot_total;  // the plain phase's total over the failed problems
+        inf[p].block_width = 0;         // finished by the non-blocked form
+    }
+    return done(rc);
+}
+
 }  // namespace
 
 extern "C" {
@@ -889,7 +1051,7 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
     if (!h) return JJ_INVALID_ARG;
     *h = nullptr;
     if (!p || p->n < 1 || p->m < p->n || (p->dtype != JJ_F64 && p->dtype != JJ_C128) ||
-        p->block_width < 0 || p->inner_block_width < 0 ||
+        p->block_width < JJ_BLOCK_AUTO || p->inner_block_width < 0 ||
         (p->order != JJ_ORDER_ROUND_ROBIN && p->order != JJ_ORDER_MODULUS) ||
         (p->gemm < JJ_GEMM_FP64 || p->gemm > JJ_GEMM_AUTO) || p->ozaki_slices < 0 ||
         p->n > (int64_t)1 << 30)
@@ -949,9 +1111,14 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
     } else {
         c->blocked = true;
         const int64_t m = p->m;
-        const int b = p->block_width;
+        const std::vector<int> cand = autotune_candidates(c);
+        if (cand.empty()) return fail(JJ_INVALID_ARG);
+        // a fixed width builds its plan now; the autotuner builds the first
+        // candidate's (so that the workspaces exist) and picks at the first solve
+        const int b = cand[0];
         const int rc = build_plan(c, 1, &m, &n, &b, false);
         if (rc != JJ_OK) return fail(rc);
+        c->tuned_bw = p->block_width > 0 ? p->block_width : 0;
     }
     *h = c;
     return JJ_OK;
@@ -977,9 +1144,9 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
     const int64_t n = c->n;
     std::vector<int32_t> perm;
     if (!j_sort(J, n, perm)) return finish(JJ_INVALID_ARG);
-    if (c->blocked && (c->plan_batched || c->P.count != 1)) {
+    if (c->blocked && c->tuned_bw > 0 && (c->plan_batched || c->P.count != 1)) {
         const int64_t m = c->m;
-        const int b = c->p.block_width;
+        const int b = c->tuned_bw;
         const int r = build_plan(c, 1, &m, &n, &b, false);
         if (r != JJ_OK) return finish(r);
     }
@@ -988,6 +1155,11 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
     c->solved = false;
     c->G_user = G;
     c->ldg_user = ldg;
+    if (c->blocked && c->tuned_bw == 0) {
+        if (order_after_legacy(c) != JJ_OK) return finish(JJ_CUDA_ERROR);
+        const int r = autotune(c, G, ldg, perm, Jw);
+        if (r != JJ_OK) return finish(r);
+    }
     inf.block_width = c->blocked ? c->P.bw[0] : 0;
     inf.nbl = c->blocked ? c->P.nbl[0] : 0;
     inf.steps_per_sweep = c->blocked ? c->P.steps : c->steps;
@@ -1187,6 +1359,15 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
                 done[p] = 1;
                 ++ndone;
             }
+        }
+    }
+    if (rc == JJ_OK) {
+        std::vector<int> failed;
+        for (int p = 0; p < count; ++p)
+            if (inf[p].status == JJ_NOT_POSDEF) failed.push_back(p);
+        if (!failed.empty()) {
+            const int r = batch_plain_finish(c, failed, inf, &launches);
+            if (r != JJ_OK) return r;
         }
     }
     // scatter back, with the eigenvalues (lambda_out host or device)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libjjacobi.so")
 JJ_F64, JJ_C128 = 0, 1
 JJ_ORDER_ROUND_ROBIN, JJ_ORDER_MODULUS = 0, 1
 JJ_GEMM_FP64, JJ_GEMM_OZAKI_FP16, JJ_GEMM_OZAKI_GRAM, JJ_GEMM_AUTO = 0, 1, 2, 3
+JJ_BLOCK_AUTO = -1
 (JJ_OK, JJ_INVALID_ARG, JJ_NOT_CONVERGED, JJ_NOT_POSDEF, JJ_NONFINITE, JJ_DEVICE_TIMEOUT,
  JJ_CUDA_ERROR, JJ_NOT_SOLVED) = range(8)
 

@@ -81,6 +81,14 @@ def test_create_rejects_bad_params(jj):
     lib.jjacobi_destroy(None)  # no-op
 
 
+def test_create_accepts_auto_block_width_only_as_minus_one(jj):
+    lib = jj.load()
+    h = ctypes.c_void_p()
+    p = jj.jjacobi_default_params(64, 64, jj.JJ_C128)
+    p.block_width = -2
+    assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(p)) == jj.JJ_INVALID_ARG
+
+
 def test_kernel_entry_points_validate_arguments(jj):
     lib = jj.load()
     assert lib.jjk_gram(9, 0, None, 1, 1, None, 0, None, 1, None) == jj.JJ_INVALID_ARG

@@ -134,3 +134,21 @@ def test_batched_workload_sample():
     for i in np.argsort([P.n for P in probs])[:3]:
         ref = oracle.solve_plain(probs[i].G, probs[i].J)
         assert max_rel_err(lams[i], ref["lam"]) <= eig_rel_tol(probs[i].G)
+
+
+def test_batched_ill_conditioned_problem_finished_by_plain_method():
+    """Problem 30 of the 512-problem workload (n = 32, scaled condition ~6e9):
+    its single pivot is the whole problem, whose Gram block is not positive
+    definite in FP64; the batch finishes it with the plain method (block_width
+    0 in its info) and its eigenvalues match the plain oracle."""
+    jj = require_gpu()
+    allp = synth.make_batched(count=31)
+    probs = [allp[0], allp[30], allp[5]]
+    rc, infos, lams, _ = _run(jj, probs, True, 1)
+    assert rc == 0
+    d = infos[1].as_dict()
+    assert d["status"] == 0 and d["block_width"] == 0
+    assert infos[0].as_dict()["block_width"] > 0
+    for P, lam in zip(probs, lams):
+        ref = oracle.solve_plain(P.G, P.J)
+        assert max_rel_err(lam, ref["lam"]) <= eig_rel_tol(P.G)

@@ -250,3 +250,27 @@ def test_one_parallel_step_through_building_blocks(gemm):
         U = out[:, cols] / np.linalg.norm(out[:, cols], axis=0)
         Ur = ref["Gt"][:, cols] / np.linalg.norm(ref["Gt"][:, cols], axis=0)
         assert orth_residual(U) <= max(8 * oracle.TOL_DEFAULT, 10 * orth_residual(Ur))
+
+
+@pytest.mark.parametrize("gemm", [0, 1])
+def test_autotuned_block_width(gemm):
+    """block_width = JJ_BLOCK_AUTO: the first solve times one sweep per candidate
+    width and keeps the fastest; the result is the blocked solve with that width."""
+    jj = require_gpu()
+    import torch
+
+    P = synth.make_workload("plain_c128_n128", n=160)
+    m, n = P.G.shape
+    with jj.Handle(m, n, jj.JJ_C128, block_width=jj.JJ_BLOCK_AUTO, gemm=gemm) as h:
+        infos = []
+        for _ in range(2):
+            Gd = to_dev(P.G)
+            infos.append(h.jjacobi_solve(Gd, Gd.stride(1), P.J).as_dict())
+            lam = torch.empty(n, dtype=torch.float64, device="cuda")
+            h.jjacobi_extract(lam)
+            assert max_rel_err(lam.cpu().numpy(), P.lam_exact) <= eig_rel_tol(P.G)
+    b = infos[0]["block_width"]
+    assert b in ([8, 16] if gemm == 1 else [8, 16, 32])
+    assert infos[1]["block_width"] == b
+    fixed = solve_gpu(P.G, P.J, block_width=b, gemm=gemm)
+    assert fixed["info"]["sweeps"] == infos[1]["sweeps"]
