@@ -9,7 +9,8 @@ graded complex128 problem of order 4096 (G = D1 B D2, B = Q |Lambda|^{1/2} W,
 J = diag(+I_2560, -I_1536)).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--block-width B] [--gemm hybrid|ozaki|fp64] [--no-plain] [--no-cpu]
+                  [--block-width B] [--gemm hybrid|ozaki|fp64] [--strategy oriented|full]
+                  [--no-plain] [--no-cpu]
                   [--one-step]
 
 --impl reference times the CPU oracle (the plain one-sided J-Jacobi, in C,
@@ -275,7 +276,9 @@ def run_ours(args):
         G0 = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()  # column-major
         Gw = torch.empty_like(G0)
         lam = torch.empty(n, dtype=torch.float64, device="cuda")
-    h = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream)
+    strat = {"full": jj.JJ_FULL_BLOCK, "oriented": jj.JJ_BLOCK_ORIENTED}[args.strategy]
+    h = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
+                  block_strategy=strat)
 
     def step():
         Gw.copy_(G0)
@@ -327,7 +330,7 @@ def run_ours(args):
     # around every kernel family of every step, on the solve's stream) and the
     # dominant kernel's roofline
     hp_ = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
-                    profile=True, max_sweeps=args.profile_sweeps)
+                    profile=True, max_sweeps=args.profile_sweeps, block_strategy=strat)
     with torch.cuda.stream(stream):
         Gw.copy_(G0)
         pinfo_ = hp_.jjacobi_solve(Gw, Gw.stride(1), P.J, allow=(jj.JJ_OK, jj.JJ_NOT_CONVERGED))
@@ -381,7 +384,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "m": m, "n": n, "block_width": args.block_width,
-                       "gemm": args.gemm, "order": "round_robin", "sweeps": info["sweeps"],
+                       "gemm": args.gemm, "strategy": args.strategy, "order": "round_robin",
+                       "sweeps": info["sweeps"],
                        "steps_per_sweep": info["steps_per_sweep"],
                        "time_to_solution_s": ms / 1e3,
                        "l2": "inputs larger than L2 (G = 256 MiB; every step reads and writes it)",
@@ -465,7 +469,9 @@ def run_batched(args):
     mmax = max(P.m for P in probs)
     nmax = max(P.n for P in probs)
     bw = args.block_width if args.block_width_set else 0
-    h = jj.Handle(mmax, nmax, jj.JJ_C128, block_width=bw, gemm=gemm, stream=stream)
+    strat = {"full": jj.JJ_FULL_BLOCK, "oriented": jj.JJ_BLOCK_ORIENTED}[args.strategy]
+    h = jj.Handle(mmax, nmax, jj.JJ_C128, block_width=bw, gemm=gemm, stream=stream,
+                  block_strategy=strat)
 
     def step():
         for a, b in zip(Gw, G0):
@@ -497,6 +503,7 @@ def run_batched(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "batched_c128_512x", "problems": len(probs),
                    "n_range": [min(P.n for P in probs), nmax], "gemm": args.gemm,
+                   "strategy": args.strategy,
                    "block_widths": sorted(set(i.block_width for i in infos)),
                    "problems_per_s": len(probs) / (ms * 1e-3),
                    "sweeps_min_max": [min(sweeps), max(sweeps)],
@@ -561,6 +568,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-width", type=int, default=16)
     ap.add_argument("--gemm", default="hybrid", choices=["hybrid", "ozaki", "fp64"])
+    ap.add_argument("--strategy", default="oriented", choices=["oriented", "full"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-plain", dest="plain", action="store_false")
     ap.add_argument("--no-cpu", action="store_true")

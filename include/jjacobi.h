@@ -73,6 +73,16 @@ typedef enum {
     JJ_GEMM_AUTO = 3
 } jj_gemm;
 
+/* What the inner solve does with a pivot block (Sec. 5.3):
+ *   JJ_FULL_BLOCK      (F) the J-Jacobi method on R until its columns are
+ *                      orthogonal (at most inner_max_sweeps sweeps);
+ *   JJ_BLOCK_ORIENTED  (B) in the first parallel step of a sweep one sweep over
+ *                      all column pairs of R, in the other steps one pass over
+ *                      the off-diagonal block only (each pair (r in block i,
+ *                      s in block j) annihilated once, Alg. 3.4). Two-level
+ *                      only; pivots up to 128 real columns. */
+typedef enum { JJ_FULL_BLOCK = 0, JJ_BLOCK_ORIENTED = 1 } jj_block_strategy;
+
 /* block_width value that lets the library pick the block width: at the first
  * solve of the handle, one sweep of every candidate width (powers of two from
  * 8 up to the widest pivot the contraction form takes, at most n/4) is timed on
@@ -108,6 +118,7 @@ typedef struct {
     int32_t profile;           /* 1: time every kernel family of every step with CUDA events
                                   (sweeps then run without graph capture); see
                                   jjacobi_kernel_times */
+    int32_t block_strategy;    /* jj_block_strategy (blocked form) */
 } jj_params;
 
 typedef struct {

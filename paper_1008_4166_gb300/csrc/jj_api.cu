@@ -44,6 +44,7 @@ struct Three {
     int32_t *d_fail = nullptr;
     int32_t *d_mod = nullptr, *d_clean = nullptr, *d_flags = nullptr, *d_sweep = nullptr;
     unsigned long long *d_cnt = nullptr, *h_cnt = nullptr, *d_rot = nullptr;
+    unsigned long long *d_touched = nullptr;
     bool ozaki = false, ozaki_update = false;
     int32_t *d_cexp = nullptr, *d_cexp2 = nullptr, *d_wdexp = nullptr;
     unsigned long long *d_ozacc = nullptr;
@@ -90,6 +91,7 @@ struct jj_ctx {
     int32_t *d_cexp = nullptr;          // column exponents (Ozaki Gram)
     unsigned long long *d_ozacc = nullptr;  // int128 Gram accumulators
     unsigned long long *d_prob_rot = nullptr, *h_prob_rot = nullptr;  // [2 count]
+    unsigned long long *d_touched = nullptr;  // [pairs of a step][2] rotated-column masks
     // batched gather/scatter tables
     double **d_bptr = nullptr;
     int64_t *d_bld = nullptr, *d_brows = nullptr, *d_blamoff = nullptr;
@@ -172,6 +174,7 @@ void free_plan(jj_ctx *c) {
     dfree(c->d_flags);
     dfree(c->d_sweep);
     dfree(c->d_prob_rot);
+    dfree(c->d_touched);
     dfree(c->d_bptr);
     dfree(c->d_bld);
     dfree(c->d_brows);
@@ -196,6 +199,7 @@ void free_plan(jj_ctx *c) {
     dfree(T.d_sweep);
     dfree(T.d_cnt);
     dfree(T.d_rot);
+    dfree(T.d_touched);
     dfree(T.d_cexp);
     dfree(T.d_cexp2);
     dfree(T.d_wdexp);
@@ -334,6 +338,7 @@ int build_three(jj_ctx *c, const std::vector<int32_t> &tab) {
     JJ_CUDA(dmalloc(&T.d_sweep, 1));
     JJ_CUDA(dmalloc(&T.d_cnt, kNumCounters));
     JJ_CUDA(dmalloc(&T.d_rot, 2 * np));
+    JJ_CUDA(dmalloc(&T.d_touched, 2 * npi));
     JJ_CUDA(cudaMallocHost((void **)&T.h_cnt, kNumCounters * sizeof(unsigned long long)));
     if (T.ozaki) {
         JJ_CUDA(dmalloc(&T.d_cexp, xcols));
@@ -433,6 +438,9 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
     const bool oz_ok = ozaki_supported(c->cplx, P.kmax);
     if (!three && (c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM) && !oz_ok)
         return JJ_INVALID_ARG;
+    if (c->p.block_strategy == JJ_BLOCK_ORIENTED &&
+        (three || !inner_single_pass_supported(c->cplx, P.kmax)))
+        return JJ_INVALID_ARG;
     c->ozaki = oz_ok && c->p.gemm != JJ_GEMM_FP64;
     c->ozaki_update = c->ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
     c->oz_slices_update = ozaki_default_slices(false);
@@ -451,6 +459,7 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
     JJ_CUDA(dmalloc(&c->d_sweep, 1));
     JJ_CUDA(dmalloc(&c->d_perm, (size_t)P.ncols));
     JJ_CUDA(dmalloc(&c->d_Jw, (size_t)P.ncols));
+    JJ_CUDA(dmalloc(&c->d_touched, 2 * np));
     if (c->ozaki) {
         if (c->ozaki_update) {
             JJ_CUDA(dmalloc(&c->d_wdig, np * 16 * kUpdSliceBytes));
@@ -557,6 +566,7 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
                 ctl.prob = c->d_prob + s0;
                 ctl.prob_rot = c->d_prob_rot;
             }
+            if (!c->ozaki_update) ctl.touched = c->d_touched;
             if (mark(0)) return JJ_CUDA_ERROR;
             if (c->ozaki) {
                 JJ_CUDA(launch_colexp_pairs(c->cplx, c->Gw, P.ldw, mrows, pr, np, P.kmax, c->d_cexp,
@@ -578,9 +588,10 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
                 ud.cexp = c->d_cexp;
                 ud.slices = c->oz_slices_update;
             }
+            const int pass = c->p.block_strategy == JJ_BLOCK_ORIENTED ? (t == 0 ? 2 : 1) : 0;
             JJ_CUDA(launch_inner(c->cplx, c->Ablk, c->Wblk, P.kmax, pr, np, c->d_Jw, c->tol,
                                  c->inner_max_sweeps, c->p.inner_block_width, c->d_cnt, st, ctl,
-                                 ud));
+                                 ud, pass));
             if (mark(2)) return JJ_CUDA_ERROR;
             if (c->ozaki_update)
                 JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw, c->Gw, P.ldw, mrows, pr, np, c->Wblk,
@@ -682,6 +693,7 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
                 ic.slot_base = T.slot0[t][ti];
                 ic.prob = T.d_prob + sl;
                 ic.prob_rot = T.d_rot;
+                if (!T.ozaki_update) ic.touched = T.d_touched;
                 UpdDigits ud;
                 if (T.ozaki) {
                     // Gram exponents over the R rows; update exponents over R and W rows
@@ -1054,6 +1066,7 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
         p->block_width < JJ_BLOCK_AUTO || p->inner_block_width < 0 ||
         (p->order != JJ_ORDER_ROUND_ROBIN && p->order != JJ_ORDER_MODULUS) ||
         (p->gemm < JJ_GEMM_FP64 || p->gemm > JJ_GEMM_AUTO) || p->ozaki_slices < 0 ||
+        (p->block_strategy != JJ_FULL_BLOCK && p->block_strategy != JJ_BLOCK_ORIENTED) ||
         p->n > (int64_t)1 << 30)
         return JJ_INVALID_ARG;
     jj_ctx *c = new jj_ctx();

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) gram_fp64_kernel(const double *__restrict
 constexpr int VKA = 16;  // rows of W_P per stage
 
 template <bool CPLX, int NJ>
-__global__ void __launch_bounds__(256) update_fp64_kernel(const double *Gs, double *Gd, int64_t ld,
+__global__ void __launch_bounds__(256, 2) update_fp64_kernel(const double *Gs, double *Gd, int64_t ld,
                                                            int64_t m, const int32_t *__restrict__ pairs,
                                                            const double *__restrict__ W, int kmax,
                                                            int VR, StepCtl ctl) {
@@ -145,17 +145,39 @@ __global__ void __launch_bounds__(256) update_fp64_kernel(const double *Gs, doub
         return;
     }
     const int tid = threadIdx.x;
-    for (int idx = tid; idx < k * VR; idx += 256) {
+    // Only the columns the inner solve rotated change: W restricted to the
+    // others is the identity (their entries of W are exact zeros and ones),
+    // so Y_t = X_t W_tt over the rotated set t, with the same bits.
+    __shared__ int tcol[128];
+    __shared__ int s_nt;
+    int kk = k;
+    if (ctl.touched && k <= 128) {
+        if (tid == 0) {
+            const unsigned long long m0 = ctl.touched[2 * q], m1 = ctl.touched[2 * q + 1];
+            int nt = 0;
+            for (int c = 0; c < k; ++c)
+                if (((c < 64 ? m0 >> c : m1 >> (c - 64)) & 1ull) != 0ull) tcol[nt++] = c;
+            s_nt = nt;
+        }
+        __syncthreads();
+        kk = s_nt;
+        if (kk == 0) return;
+    } else {
+        for (int c = tid; c < k && c < 128; c += 256) tcol[c] = c;
+        __syncthreads();
+    }
+    auto cmap = [&](int i) -> int { return i < 128 ? tcol[i] : i; };
+    for (int idx = tid; idx < kk * VR; idx += 256) {
         const int a = idx / VR, r = idx % VR;
         const int64_t l = l0 + r;
-        const int64_t col = pivot_col(pd, a);
+        const int64_t col = pivot_col(pd, cmap(a));
 #pragma unroll
         for (int e = 0; e < E; ++e) xs[((size_t)a * VR + r) * E + e] = l < l1 ? Gs[(col * ld + l) * E + e] : 0.0;
     }
     const double *Wp = W + (size_t)q * kmax * kmax * E;
     const int rg = tid & 7, cg = tid >> 3;
     const int nri = VR / 8;  // rows per thread (<= 4)
-    for (int c0 = 0; c0 < k; c0 += KW) {
+    for (int c0 = 0; c0 < kk; c0 += KW) {
         double acc[4][NJ][E];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -163,18 +185,19 @@ __global__ void __launch_bounds__(256) update_fp64_kernel(const double *Gs, doub
             for (int j = 0; j < NJ; ++j)
 #pragma unroll
                 for (int e = 0; e < E; ++e) acc[i][j][e] = 0.0;
-        for (int a0 = 0; a0 < k; a0 += VKA) {
+        for (int a0 = 0; a0 < kk; a0 += VKA) {
             __syncthreads();  // X tile complete / previous W stage consumed
             for (int idx = tid; idx < VKA * KW; idx += 256) {
                 const int aa = idx % VKA, c = idx / VKA;
                 const int a = a0 + aa, b = c0 + c;
-                const bool ok = a < k && b < k;
+                const bool ok = a < kk && b < kk;
 #pragma unroll
                 for (int e = 0; e < E; ++e)
-                    ws[((size_t)aa * KW + c) * E + e] = ok ? Wp[((size_t)b * kmax + a) * E + e] : 0.0;
+                    ws[((size_t)aa * KW + c) * E + e] =
+                        ok ? Wp[((size_t)cmap(b) * kmax + cmap(a)) * E + e] : 0.0;
             }
             __syncthreads();
-            const int na = min(VKA, k - a0);
+            const int na = min(VKA, kk - a0);
             for (int aa = 0; aa < na; ++aa) {
                 const double *xa = xs + (size_t)(a0 + aa) * VR * E;
                 const double *wa = ws + (size_t)aa * KW * E;
@@ -210,8 +233,8 @@ __global__ void __launch_bounds__(256) update_fp64_kernel(const double *Gs, doub
 #pragma unroll
             for (int j = 0; j < NJ; ++j) {
                 const int b = c0 + cg + 32 * j;
-                if (b < k) {
-                    const int64_t col = pivot_col(pd, b);
+                if (b < kk) {
+                    const int64_t col = pivot_col(pd, cmap(b));
 #pragma unroll
                     for (int e = 0; e < E; ++e) Gd[(col * ld + l) * E + e] = acc[i][j][e];
                 }
@@ -463,7 +486,7 @@ template <bool CPLX, int ROWS>
 __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double *__restrict__ A, double *__restrict__ Wb, int kmax, const int32_t *__restrict__ pairs,
     const int8_t *__restrict__ J, double tol, int max_sweeps,
-    unsigned long long *__restrict__ counters, StepCtl ctl, UpdDigits ud) {
+    unsigned long long *__restrict__ counters, StepCtl ctl, UpdDigits ud, int pass) {
     constexpr int E = CPLX ? 2 : 1;
     extern __shared__ double2 smem4[];
     double *sm = reinterpret_cast<double *>(smem4);
@@ -479,9 +502,11 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     __shared__ int s_rot, s_fail;
     __shared__ double s_piv;
     __shared__ double s_max[SW];
+    __shared__ unsigned long long s_tmask[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *Ag = A + (int64_t)blockIdx.x * kmax * kmax * E;
     for (int a = tid; a < k; a += ST) jsh[a] = J[pivot_col(pd, a)];
+    if (tid < 2) s_tmask[tid] = 0ull;
     // load the upper triangle of A_P, zero below
     for (int t = tid; t < k * k; t += ST) {
         const int a = t % k, b = t / k;
@@ -538,6 +563,10 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
             atomicOr(&counters[kCntErr], kErrNotPosdef);
             pair_record(ctl, pd, blockIdx.x, false, true);
             pair_flag_prob(ctl, blockIdx.x, kErrNotPosdef);
+            if (ctl.touched) {
+                ctl.touched[2 * blockIdx.x] = 0ull;
+                ctl.touched[2 * blockIdx.x + 1] = 0ull;
+            }
         }
         for (int t = tid; t < k * k; t += ST) {
             const int a = t % k, b = t / k;
@@ -559,7 +588,29 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     __syncthreads();
     const int npl = k + (k & 1);
     const int P = npl - 1;
-    const int nq = npl / 2;  // column pairs per inner step (<= 32 for k <= 64, <= 64 for k <= 128)
+    // Passes (Sec. 5.3): pass 0 (full block, 2F) repeats round-robin sweeps
+    // over all column pairs of R until one applies no rotation; pass 2 is one
+    // such sweep; pass 1 (block-oriented, 2B, after the first step of a sweep)
+    // annihilates the off-diagonal block once: round rho pairs column r of the
+    // first block with column (r + rho) mod max(n_i, n_j) of the second.
+    const int ni = pd[1], nj = pd[3];
+    const bool offd = pass == 1;
+    const int NB = ni > nj ? ni : nj;
+    const int S = offd ? NB : P;            // inner steps per pass
+    const int nq = offd ? ni : npl / 2;     // column pairs per inner step (<= 64)
+    const int npass = pass == 0 ? max_sweeps : 1;
+    auto pair_at = [&](int st, int qi, int &a, int &b) -> bool {
+        if (offd) {
+            const int s2 = (qi + st) % NB;
+            a = qi;
+            b = ni + s2;
+            return qi < ni && s2 < nj;
+        }
+        a = qi == 0 ? P : (st + qi) % P;
+        b = qi == 0 ? st : (st - qi + P) % P;
+        if (a > b) { const int t = a; a = b; b = t; }
+        return b < k;
+    };
     unsigned long long total_rot = 0;
     double maxoff = 0.0;
     // per-step scratch: dot products and rotation parameters of every pair
@@ -571,9 +622,8 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         for (int qi = w0; qi < nq; qi += nw) {
             const double *pp = par + 7 * qi;
             if (pp[6] == 0.0) continue;
-            int a = qi == 0 ? P : (st + qi) % P;
-            int b = qi == 0 ? st : (st - qi + P) % P;
-            if (a > b) { const int t = a; a = b; b = t; }
+            int a, b;
+            pair_at(st, qi, a, b);
             Rot Q;
             Q.ce_re = pp[0]; Q.ce_im = pp[1]; Q.se_re = pp[2]; Q.se_im = pp[3]; Q.c = pp[4]; Q.hs = pp[5];
 #pragma unroll
@@ -596,7 +646,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
             }
         }
     };
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int sweep = 0; sweep < npass; ++sweep) {
         for (int c = warp; c < k; c += SW) {
             double acc = 0.0;
 #pragma unroll
@@ -617,14 +667,13 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         if (tid == 0) s_rot = 0;
         __syncthreads();
         int my_rot = 0;
-        for (int step = 0; step < P; ++step) {
+        for (int step = 0; step < S; ++step) {
             // (1) dot products a_ab = r_a^* r_b: one warp per pair, lanes over rows
             for (int qi = warp; qi < nq; qi += SW) {
-                int a = qi == 0 ? P : (step + qi) % P;
-                int b = qi == 0 ? step : (step - qi + P) % P;
-                if (a > b) { const int t = a; a = b; b = t; }
+                int a, b;
+                const bool valid = pair_at(step, qi, a, b);
                 double sr = 0.0, si = 0.0;
-                if (b < k) {
+                if (valid) {
 #pragma unroll
                     for (int i = 0; i < ROWS; ++i) {
                         const int l = lane + 32 * i;
@@ -658,11 +707,10 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
             if (warp != 0 && step > 0) apply_w(step - 1, spar0 + 7 * 64 * ((step - 1) & 1), warp - 1, SW - 1);
             if (warp == 0) {
                 for (int qi = lane; qi < nq; qi += 32) {
-                    int a = qi == 0 ? P : (step + qi) % P;
-                    int b = qi == 0 ? step : (step - qi + P) % P;
-                    if (a > b) { const int t = a; a = b; b = t; }
+                    int a, b;
+                    const bool valid = pair_at(step, qi, a, b);
                     double flag = 0.0;
-                    if (b < k) {
+                    if (valid) {
                         const double sr = sdot[2 * qi], si = sdot[2 * qi + 1];
                         const double da = dsh[a], db = dsh[b];
                         const double absa = CPLX ? sqrt(sr * sr + si * si) : fabs(sr);
@@ -682,6 +730,8 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
                                     dsh[b] = Q.ds;
                                     flag = 1.0;
                                     ++my_rot;
+                                    atomicOr(&s_tmask[a >> 6], 1ull << (a & 63));
+                                    atomicOr(&s_tmask[b >> 6], 1ull << (b & 63));
                                 } else {
                                     atomicOr(&counters[kCntErr], kErrNotPosdef);
                                     pair_flag_prob(ctl, blockIdx.x, kErrNotPosdef);
@@ -697,9 +747,8 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
             for (int qi = warp; qi < nq; qi += SW) {
                 const double *pp = spar + 7 * qi;
                 if (pp[6] == 0.0) continue;
-                int a = qi == 0 ? P : (step + qi) % P;
-                int b = qi == 0 ? step : (step - qi + P) % P;
-                if (a > b) { const int t = a; a = b; b = t; }
+                int a, b;
+                pair_at(step, qi, a, b);
                 Rot Q;
                 Q.ce_re = pp[0]; Q.ce_im = pp[1]; Q.se_re = pp[2]; Q.se_im = pp[3]; Q.c = pp[4]; Q.hs = pp[5];
 #pragma unroll
@@ -723,8 +772,8 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
             }
             __syncthreads();
         }
-        // W part of the sweep's last step
-        apply_w(P - 1, spar0 + 7 * 64 * ((P - 1) & 1), warp, SW);
+        // W part of the pass's last step
+        apply_w(S - 1, spar0 + 7 * 64 * ((S - 1) & 1), warp, SW);
         __syncthreads();
         if (warp == 0) {
 #pragma unroll
@@ -812,6 +861,10 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         if (total_rot) atomicAdd(&counters[kCntPairsRot], 1ull);
         pair_record(ctl, pd, blockIdx.x, total_rot > 0, false);
         pair_count_prob(ctl, blockIdx.x, total_rot);
+        if (ctl.touched) {
+            ctl.touched[2 * blockIdx.x] = s_tmask[0];
+            ctl.touched[2 * blockIdx.x + 1] = s_tmask[1];
+        }
     }
 }
 
@@ -876,7 +929,7 @@ cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
                          int npairs, const int8_t *J, double tol, int inner_max_sweeps,
                          int inner_block, unsigned long long *counters, cudaStream_t st,
-                         StepCtl ctl, UpdDigits ud) {
+                         StepCtl ctl, UpdDigits ud, int pass) {
     (void)inner_block;
     if (npairs <= 0) return cudaSuccess;
     // Shared-memory resident form when R and W fit (227 KB per block).
@@ -888,7 +941,7 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)smb);                                       \
         if (e != cudaSuccess) return e;                                                       \
-        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl, ud); \
+        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl, ud, pass); \
         return cudaGetLastError();                                                            \
     } while (0)
         const int rows = (kmax + 31) / 32;
@@ -904,12 +957,18 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
         }
 #undef JJ_INNER_SMEM
     }
+    if (pass != 0) return cudaErrorNotSupported;  // single passes need the shared-memory form
     const size_t sh = (size_t)kmax * sizeof(double) + (size_t)kmax * sizeof(int);
     if (cplx)
         inner_kernel<true><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl);
     else
         inner_kernel<false><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl);
     return cudaGetLastError();
+}
+
+bool inner_single_pass_supported(bool cplx, int kmax) {
+    return inner_smem_bytes(cplx, kmax) <= 227 * 1024 && kmax <= 128 &&
+           (kmax + 31) / 32 <= (cplx ? 3 : 4);
 }
 
 }  // namespace jj

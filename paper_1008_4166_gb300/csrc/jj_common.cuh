@@ -116,6 +116,9 @@ struct StepCtl {
     const int32_t *rows = nullptr;    // [npairs]: rows of the pair's problem (nullptr: all m)
     const int32_t *prob = nullptr;    // [npairs]: problem of the pair
     unsigned long long *prob_rot = nullptr;  // [2 problems]: rotations, error flags (this sweep)
+    // [npairs][2]: bit c set when the inner solve rotated column c of the pair
+    // (columns never rotated keep W's column e_c, so the update can skip them)
+    unsigned long long *touched = nullptr;
 };
 constexpr int kPairSkipped = 1;
 constexpr int kPairIdentity = 2;
@@ -197,10 +200,13 @@ cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
                          int npairs, const int8_t *J, double tol, int inner_max_sweeps,
                          int inner_block, unsigned long long *counters, cudaStream_t st,
-                         StepCtl ctl = StepCtl(), UpdDigits ud = UpdDigits());
+                         StepCtl ctl = StepCtl(), UpdDigits ud = UpdDigits(), int pass = 0);
 cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int64_t ld,
                           int64_t m, const int32_t *pairs, int npairs, const double *W,
                           int kmax, cudaStream_t st, StepCtl ctl = StepCtl());
+
+// Whether the inner solve can run single passes (block-oriented strategy).
+bool inner_single_pass_supported(bool cplx, int kmax);
 
 // Split-precision (fp16 digit) forms on the tensor cores (jj_ozaki.cu).
 int ozaki_default_slices(bool gram);

@@ -274,3 +274,51 @@ def test_autotuned_block_width(gemm):
     assert infos[1]["block_width"] == b
     fixed = solve_gpu(P.G, P.J, block_width=b, gemm=gemm)
     assert fixed["info"]["sweeps"] == infos[1]["sweeps"]
+
+
+@pytest.mark.parametrize("gemm", [0, 1, 2])
+def test_block_oriented_real_matches_oracle(gemm):
+    """Block-oriented strategy (B, Sec. 5.3 / Alg. 3.4): one full pass over each
+    pivot in the first step of a sweep, one pass over the off-diagonal block in
+    the others."""
+    require_gpu()
+    from paper_1008_4166_gb300 import jjacobi as jj
+
+    P = synth.make_workload("blocked_f64_n2048_b32", n=256)
+    ref = oracle.solve_plain(P.G, P.J)
+    got = solve_gpu(P.G, P.J, block_width=32, gemm=gemm, want_U=True,
+                    block_strategy=jj.JJ_BLOCK_ORIENTED)
+    tol = eig_rel_tol(P.G)
+    assert got["info"]["status"] == 0
+    assert max_rel_err(got["lam"], ref["lam"]) <= tol
+    assert max_rel_err(got["lam"], P.lam_exact) <= tol
+    assert orth_residual(got["U"]) <= 8 * oracle.TOL_DEFAULT
+    assert reconstruction_residual(P.G, P.J, got["lam"], got["U"]) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_block_oriented_complex_ragged_and_graded(order):
+    """Unequal block sizes (150 columns, b = 11: off-diagonal blocks of 10 x 11)
+    and the graded recipe held to 1e-10 (hybrid form)."""
+    require_gpu()
+    from paper_1008_4166_gb300 import jjacobi as jj
+
+    P = synth.make_workload("plain_c128_n128", n=150)
+    ref = oracle.solve_plain(P.G, P.J)
+    got = solve_gpu(P.G, P.J, block_width=11, gemm=0, order=order,
+                    block_strategy=jj.JJ_BLOCK_ORIENTED)
+    assert got["info"]["status"] == 0
+    assert max_rel_err(got["lam"], ref["lam"]) <= eig_rel_tol(P.G)
+    Pg = synth.make_workload("graded_c128_n4096_b64", n=192)
+    refg = oracle.solve_plain(Pg.G, Pg.J)
+    gg = solve_gpu(Pg.G, Pg.J, block_width=16, gemm=2, order=order,
+                   block_strategy=jj.JJ_BLOCK_ORIENTED)
+    assert gg["info"]["status"] == 0
+    assert max_rel_err(gg["lam"], refg["lam"]) <= 1e-10
+
+
+def test_block_oriented_rejects_three_level():
+    jj = require_gpu()
+    with pytest.raises(jj.JJError):
+        jj.Handle(256, 256, jj.JJ_F64, block_width=32, inner_block_width=8,
+                  block_strategy=jj.JJ_BLOCK_ORIENTED)
