@@ -361,29 +361,27 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         ph[b] ^= 1u;
         pending[b] = false;
     };
-    // digits of rows [row0 + 64 i, +64) of the K2 real columns into buffer b;
-    // thread -> (column a, row pair): rows l, l+1 packed into one 32-bit store.
-    // All loads of a thread are issued before any digit work (one memory
-    // latency per 64 rows instead of one per item).
-    constexpr int GZ_ITEMS = 64 * (GZ_KC / 2) / GZ_THREADS;
-    constexpr int GZ_BATCH = 2;
+    // digits of rows [row0 + 64 i, +64) of the K2 real columns into buffer b,
+    // by warps 1..15 (warp 0 issues the tensor-core products meanwhile);
+    // item -> (column a, row pair): rows l, l+1 packed into one 32-bit store.
+    // Two items per thread at a time, loads first (the 64 accumulator
+    // registers of the drain leave no room for more).
+    constexpr int GZ_BUILDERS = GZ_THREADS - 32;
+    constexpr int GZ_NITEMS = 64 * (GZ_KC / 2);
     auto build = [&](int i, int b) {
         const int64_t c0 = row0 + (int64_t)i * GZ_KC;
         const int nrow = (int)min((int64_t)GZ_KC, row1 - c0);
         uint8_t *buf = sm + (size_t)b * GZ_BUF_BYTES;
-        // two batches of loads: the 64 accumulator registers of the flush
-        // leave no room for all of them at once
+        for (int base = tid - 32; base < GZ_NITEMS; base += 2 * GZ_BUILDERS) {
+            double xv0[2], xv1[2];
 #pragma unroll
-        for (int h = 0; h < GZ_ITEMS; h += GZ_BATCH) {
-            double xv0[GZ_BATCH], xv1[GZ_BATCH];
-#pragma unroll
-            for (int u = 0; u < GZ_BATCH; ++u) {
-                const int idx = tid + (h + u) * GZ_THREADS;
+            for (int u = 0; u < 2; ++u) {
+                const int idx = base + u * GZ_BUILDERS;
                 const int a = idx / (GZ_KC / 2);
                 const int lp = (idx % (GZ_KC / 2)) * 2;
                 xv0[u] = 0.0;
                 xv1[u] = 0.0;
-                if (a < K2) {
+                if (idx < GZ_NITEMS && a < K2) {
                     const int c = CPLX ? (a < k ? a : a - k) : a;
                     const int64_t col = c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
                     const int ri = (CPLX && a >= k) ? 1 : 0;
@@ -393,11 +391,11 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
                 }
             }
 #pragma unroll
-            for (int u = 0; u < GZ_BATCH; ++u) {
-                const int idx = tid + (h + u) * GZ_THREADS;
+            for (int u = 0; u < 2; ++u) {
+                const int idx = base + u * GZ_BUILDERS;
                 const int a = idx / (GZ_KC / 2);
                 const int lp = (idx % (GZ_KC / 2)) * 2;
-                if (a >= K2) continue;
+                if (idx >= GZ_NITEMS || a >= K2) continue;
                 const int e = sexp[a];
                 const unsigned long long q0 = fixed63(xv0[u], e), q1 = fixed63(xv1[u], e);
                 const bool n0 = neg_bits(xv0[u]), n1 = neg_bits(xv1[u]);
@@ -410,7 +408,7 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         }
     };
 
-    if (nsc > 0) build(0, 0);
+    if (nsc > 0 && warp != 0) build(0, 0);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -441,7 +439,7 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         pending[b] = true;
         if (i + 1 < nsc) {
             wait_buf(b ^ 1);  // the products that read the other buffer are done
-            build(i + 1, b ^ 1);
+            if (warp != 0) build(i + 1, b ^ 1);
             fence_async_smem();
         }
         if ((i & 1) == 1 || i == nsc - 1) {
@@ -449,23 +447,32 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
             wait_buf(b);
             tc_fence_after();
             if (!s_abort) {
+                // two groups (32 columns of this thread) per TMEM round trip
 #pragma unroll
-                for (int d = 2; d <= GZ_SLICES + 1; ++d) {
-                    const int sh = kBeta * (GZ_SLICES + 1 - d);
-                    const long long mul = 1ll << (sh & 31);
+                for (int d0 = 2; d0 <= GZ_SLICES + 1; d0 += 2) {
+                    uint32_t v[4][8];
 #pragma unroll
-                    for (int j0 = 0; j0 < 16; j0 += 8) {
-                        uint32_t v[8];
-                        tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((d - 2) * 64 + cq * 16 + j0), v);
-                        tmem_wait_ld();
+                    for (int g = 0; g < 2; ++g)
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int iv = __float2int_rn(__uint_as_float(v[j]));  // exact, |v| < 2^24
-                            if (sh >= 32)
-                                w1[j0 + j] += (long long)iv * mul;
-                            else
-                                w0[j0 + j] += (long long)iv * mul;
-                        }
+                        for (int h = 0; h < 2; ++h)
+                            tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) +
+                                         (uint32_t)((d0 + g - 2) * 64 + cq * 16 + 8 * h),
+                                     v[2 * g + h]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        const int sh = kBeta * (GZ_SLICES + 1 - (d0 + g));
+                        const long long mul = 1ll << (sh & 31);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int iv = __float2int_rn(__uint_as_float(v[2 * g + h][j]));  // exact, |v| < 2^24
+                                if (sh >= 32)
+                                    w1[8 * h + j] += (long long)iv * mul;
+                                else
+                                    w0[8 * h + j] += (long long)iv * mul;
+                            }
                     }
                 }
             }
@@ -784,21 +791,34 @@ __global__ void __launch_bounds__(UZ_THREADS, 1) update_ozaki_kernel(
         long long acc[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = 0;
-        for (int d = 2; d <= s + 1; ++d) {
-            const int sh = UZ_F - kBeta * d;  // may be negative for the lowest digits
+        // two groups (up to 32 values of this thread) per TMEM round trip
+        for (int d0 = 2; d0 <= s + 1; d0 += 2) {
+            uint32_t v[2][2][8];
 #pragma unroll
-            for (int j0 = 0; j0 < 16; j0 += 8) {
-                if (jbase + j0 >= NP) break;
-                uint32_t v[8];
-                tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((d - 2) * NP + jbase + j0), v);
-                tmem_wait_ld();
+            for (int g = 0; g < 2; ++g)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const long long iv = (long long)__float2int_rn(__uint_as_float(v[j]));
-                    if (sh >= 0)
-                        acc[j0 + j] += iv << sh;
-                    else if (sh > -62)
-                        acc[j0 + j] += (iv + (1ll << (-sh - 1))) >> (-sh);
+                for (int h = 0; h < 2; ++h)
+                    if (d0 + g <= s + 1 && jbase + 8 * h < NP)
+                        tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) +
+                                     (uint32_t)((d0 + g - 2) * NP + jbase + 8 * h),
+                                 v[g][h]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const int d = d0 + g;
+                if (d > s + 1) break;
+                const int sh = UZ_F - kBeta * d;  // may be negative for the lowest digits
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (jbase + 8 * h >= NP) break;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const long long iv = (long long)__float2int_rn(__uint_as_float(v[g][h][j]));
+                        if (sh >= 0)
+                            acc[8 * h + j] += iv << sh;
+                        else if (sh > -62)
+                            acc[8 * h + j] += (iv + (1ll << (-sh - 1))) >> (-sh);
+                    }
                 }
             }
         }
