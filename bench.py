@@ -181,13 +181,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def src_hash() -> str:
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1008_4166_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+def captured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.txt, if the
+    kernel's source files are unchanged since the capture (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) != 4 or line.startswith("#") or parts[0] != kernel:
+                    continue
+                h = hashlib.sha256()
+                for name in parts[2].split(","):
+                    with open(os.path.join(ROOT, "paper_1008_4166_gb300", "csrc", name), "rb") as fh:
+                        h.update(fh.read())
+                return int(parts[1]) if h.hexdigest()[:16] == parts[3] else None
+    except OSError:
+        return None
+    return None
 
 
 def gram_products(s: int) -> int:
@@ -340,15 +350,9 @@ def run_ours(args):
     hp_.close()
     roof = kernel_roofline(jj, P, times, pinfo_.as_dict(), g_gram == jj.JJ_GEMM_OZAKI_FP16,
                            g_upd == jj.JJ_GEMM_OZAKI_FP16, _peaks())
-    roof["traffic"] = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            tr = json.load(f)
-        ent = tr.get(roof["kernel"])
-        if ent and ent.get("src_hash") == src_hash():
-            roof["traffic"] = ent["bytes_per_launch"]
-    except Exception:
-        pass
+    # DRAM bytes per launch from the ncu capture of the same kernel (one step of
+    # this workload; per launch, like `achieved`), null once the kernel changed
+    roof["traffic"] = captured_traffic(roof["kernel"])
 
     # the plain form on the same input, same accuracy target
     plain = None

@@ -2,6 +2,7 @@
 // sweep loop (one CUDA graph per sweep), convergence test, extraction.
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <cstdio>
 #include <cstring>
 #include <numeric>
@@ -116,6 +117,7 @@ struct jj_ctx {
     cudaGraphExec_t graph = nullptr;  // one sweep of the current plan
     double three_maxoff = 0.0;
     int tuned_bw = 0;                 // block width chosen (0: not yet tuned)
+    std::map<int, int> class_bw;      // batched autotuner: size class -> block width
     cudaEvent_t ev_legacy = nullptr;  // orders a private stream after the legacy stream
     // profiling (params.profile): events around each kernel family of each step
     std::vector<cudaEvent_t> pev;
@@ -923,6 +925,103 @@ int autotune(jj_ctx *c, const void *G, int64_t ldg, const std::vector<int32_t> &
     return build_plan(c, 1, &m, &n, &best_b, false);
 }
 
+// The problems of a batched plan into the work matrix: J-sorted column order
+// (Sec. 2.3), J in work order, gather, fresh skip state.
+int batch_load(jj_ctx *c, int count, void *const *G, const int64_t *n, const int64_t *ldg,
+               const int8_t *const *J) {
+    const Plan &P = c->P;
+    cudaStream_t st = c->stream;
+    std::vector<int32_t> srccol(P.ncols), perm;
+    std::vector<int8_t> Jw(P.ncols);
+    for (int p = 0; p < count; ++p) {
+        if (!j_sort(J[p], n[p], perm)) return JJ_INVALID_ARG;
+        for (int64_t i = 0; i < n[p]; ++i) {
+            srccol[P.coff[p] + i] = perm[i];
+            Jw[P.coff[p] + i] = J[p][perm[i]];
+        }
+    }
+    JJ_CUDA(cudaMemcpyAsync(c->d_perm, srccol.data(), P.ncols * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    JJ_CUDA(cudaMemcpyAsync(c->d_Jw, Jw.data(), P.ncols, cudaMemcpyHostToDevice, st));
+    JJ_CUDA(cudaMemcpyAsync(c->d_bptr, G, count * sizeof(void *), cudaMemcpyHostToDevice, st));
+    JJ_CUDA(cudaMemcpyAsync(c->d_bld, ldg, count * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    JJ_CUDA(launch_batch_gather(c->cplx, c->d_bptr, c->d_bld, c->d_brows, c->d_bcolprob, c->d_perm,
+                                c->Gw, P.ldw, P.ncols, st));
+    JJ_CUDA(cudaStreamSynchronize(st));  // the host tables above are temporaries
+    return reset_skip_state(c);
+}
+
+// Size class of a batched problem for the autotuner: floor(log2 n).
+int size_class(int64_t n) {
+    int b = 0;
+    while ((int64_t)2 << b <= n) ++b;
+    return b;
+}
+
+// Batched autotuner (block_width = JJ_BLOCK_AUTO): for every size class
+// present, one sweep of the sub-batch of that class is timed (CUDA events
+// around the sweep's graph, inputs gathered into the work matrix, the caller's
+// G untouched) with every candidate width, and the fastest is kept for the
+// class, in this and later calls of the handle.
+int batch_autotune(jj_ctx *c, int count, void *const *G, const int64_t *m, const int64_t *n,
+                   const int64_t *ldg, const int8_t *const *J, std::vector<int> &bws) {
+    std::map<int, std::vector<int>> classes;
+    for (int p = 0; p < count; ++p) classes[size_class(n[p])].push_back(p);
+    cudaStream_t st = c->stream;
+    cudaEvent_t e0, e1;
+    JJ_CUDA(cudaEventCreate(&e0));
+    JJ_CUDA(cudaEventCreate(&e1));
+    int rc = JJ_OK;
+    const bool digits = c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM;
+    const int bmax = digits ? (c->cplx ? 16 : 32) : 64;
+    for (auto &kv : classes) {
+        if (c->class_bw.count(kv.first)) continue;
+        const std::vector<int> &idx = kv.second;
+        std::vector<void *> g;
+        std::vector<int64_t> mm, nn, ll;
+        std::vector<const int8_t *> jj;
+        int64_t nmax = 0;
+        for (int p : idx) {
+            g.push_back(G[p]);
+            mm.push_back(m[p]);
+            nn.push_back(n[p]);
+            ll.push_back(ldg[p]);
+            jj.push_back(J[p]);
+            nmax = std::max(nmax, n[p]);
+        }
+        float best = 0.f;
+        int best_b = 0;
+        for (int b = 8; b <= bmax; b *= 2) {
+            if (b > 8 && 2 * (int64_t)b > nmax) break;  // wider than the class's problems
+            std::vector<int> w(idx.size());
+            for (size_t i = 0; i < idx.size(); ++i) w[i] = (int)std::min<int64_t>(b, (nn[i] + 1) / 2);
+            if ((rc = build_plan(c, (int)idx.size(), mm.data(), nn.data(), w.data(), true)) != JJ_OK ||
+                (rc = batch_load(c, (int)idx.size(), g.data(), nn.data(), ll.data(), jj.data())) != JJ_OK ||
+                (rc = build_graph(c, false)) != JJ_OK)
+                break;
+            float ms = 0.f;
+            cudaEventRecord(e0, st);
+            cudaGraphLaunch(c->graph, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = JJ_CUDA_ERROR;
+                break;
+            }
+            if (best_b == 0 || ms < best) {
+                best = ms;
+                best_b = b;
+            }
+        }
+        if (rc != JJ_OK) break;
+        c->class_bw[kv.first] = best_b;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != JJ_OK) return rc;
+    for (int p = 0; p < count; ++p)
+        bws[p] = (int)std::min<int64_t>(c->class_bw[size_class(n[p])], (n[p] + 1) / 2);
+    return JJ_OK;
+}
+
 // Batched solve, second phase: problems whose blocked sweeps failed because a
 // pivot Gram block was not positive definite in working precision (its
 // columns' scaled condition squared above ~1/u; the non-blocked method never
@@ -1310,7 +1409,16 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
                       std::equal(n, n + count, P0.pn.begin());
     if (!same) {
         std::vector<int> bws(count);
-        for (int p = 0; p < count; ++p) bws[p] = batch_block_width(c, n[p]);
+        if (c->p.block_width == JJ_BLOCK_AUTO) {
+            if (order_after_legacy(c) != JJ_OK) return JJ_CUDA_ERROR;
+            const int r = batch_autotune(c, count, G, m, n, ldg, J, bws);
+            if (r != JJ_OK) {
+                free_plan(c);
+                return r;
+            }
+        } else {
+            for (int p = 0; p < count; ++p) bws[p] = batch_block_width(c, n[p]);
+        }
         const int r = build_plan(c, count, m, n, bws.data(), true);
         if (r != JJ_OK) {
             free_plan(c);
@@ -1319,24 +1427,11 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
     }
     const Plan &P = c->P;
     cudaStream_t st = c->stream;
-    // J-sorted work order of every problem
-    std::vector<int32_t> srccol(P.ncols), perm;
-    std::vector<int8_t> Jw(P.ncols);
-    for (int p = 0; p < count; ++p) {
-        if (!j_sort(J[p], n[p], perm)) return JJ_INVALID_ARG;
-        for (int64_t i = 0; i < n[p]; ++i) {
-            srccol[P.coff[p] + i] = perm[i];
-            Jw[P.coff[p] + i] = J[p][perm[i]];
-        }
-    }
     if (order_after_legacy(c) != JJ_OK) return JJ_CUDA_ERROR;
-    JJ_CUDA(cudaMemcpyAsync(c->d_perm, srccol.data(), P.ncols * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    JJ_CUDA(cudaMemcpyAsync(c->d_Jw, Jw.data(), P.ncols, cudaMemcpyHostToDevice, st));
-    JJ_CUDA(cudaMemcpyAsync(c->d_bptr, G, count * sizeof(void *), cudaMemcpyHostToDevice, st));
-    JJ_CUDA(cudaMemcpyAsync(c->d_bld, ldg, count * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    JJ_CUDA(launch_batch_gather(c->cplx, c->d_bptr, c->d_bld, c->d_brows, c->d_bcolprob, c->d_perm,
-                                c->Gw, P.ldw, P.ncols, st));
-    if (reset_skip_state(c) != JJ_OK) return JJ_CUDA_ERROR;
+    {
+        const int r = batch_load(c, count, G, n, ldg, J);
+        if (r != JJ_OK) return r;
+    }
     std::vector<jj_info> inf(count);
     std::vector<char> done(count, 0);
     int ndone = 0;

@@ -152,3 +152,30 @@ def test_batched_ill_conditioned_problem_finished_by_plain_method():
     for P, lam in zip(probs, lams):
         ref = oracle.solve_plain(P.G, P.J)
         assert max_rel_err(lam, ref["lam"]) <= eig_rel_tol(P.G)
+
+
+def test_batched_autotuned_widths_per_size_class():
+    """block_width = JJ_BLOCK_AUTO: one width per size class (floor(log2 n)),
+    chosen by timing one sweep of that class's sub-batch per candidate; results
+    as accurate as with fixed widths, and the second call reuses the choice."""
+    jj = require_gpu()
+    import torch
+
+    probs = _problems(True, [20, 28, 40, 60, 100, 120, 130, 200], 314)
+    mmax, nmax = max(P.m for P in probs), max(P.n for P in probs)
+    with jj.Handle(mmax, nmax, jj.JJ_C128, block_width=jj.JJ_BLOCK_AUTO, gemm=1) as h:
+        for call in range(2):
+            Gs = [to_dev(P.G) for P in probs]
+            lam = torch.empty(sum(P.n for P in probs), dtype=torch.float64, device="cuda")
+            rc, infos = h.jjacobi_solve_batched(Gs, [P.J for P in probs], lam)
+            assert rc == 0
+            widths = [i.as_dict()["block_width"] for i in infos]
+            if call == 0:
+                first = widths
+            assert widths == first
+            lam = lam.cpu().numpy()
+            off = 0
+            for P, w in zip(probs, widths):
+                assert w in (0, 8, 16) or w == (P.n + 1) // 2
+                assert max_rel_err(np.sort(lam[off:off + P.n]), np.sort(P.lam_exact)) <= eig_rel_tol(P.G)
+                off += P.n
