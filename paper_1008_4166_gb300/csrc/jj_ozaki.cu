@@ -417,21 +417,27 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         const int b = i & 1;
         const bool first = (i & 1) == 0;  // first 64 rows of a 128-row accumulation
         if (tid == 0) {
+            // For each A digit t, the B tiles of digits u, u + 1, ... are
+            // adjacent in shared memory and their diagonals t + u, t + u + 1, ...
+            // are adjacent 64-column groups in TMEM: one product with
+            // N = 64 * run covers a run of up to four (rows of a digit tile
+            // beyond K2 are zero, so the columns beyond K2 of each group receive
+            // zeros). Digit t = 1 meets every diagonal once, so its products
+            // (accumulate = 0 in the first chunk of a 128-row accumulation)
+            // initialize all groups.
             const uint32_t base = sbase + (uint32_t)(b * GZ_BUF_BYTES);
-            for (int d = 2; d <= GZ_SLICES + 1; ++d) {
-                const uint32_t dt = tmem + (uint32_t)((d - 2) * 64);
-                bool acc = !first;
-                for (int t = 1; t <= GZ_SLICES; ++t) {
-                    const int u = d - t;
-                    if (u < 1 || u > GZ_SLICES) continue;
-                    const uint32_t a0 = base + (uint32_t)((t - 1) * GZ_SLICE_BYTES);
+            for (int t = 1; t <= GZ_SLICES; ++t) {
+                const int umax = GZ_SLICES + 1 - t;
+                const uint32_t a0 = base + (uint32_t)((t - 1) * GZ_SLICE_BYTES);
+                for (int u = 1; u <= umax; u += 4) {
+                    const int run = min(4, umax - u + 1);  // adjacent tiles in one product
+                    const uint32_t id = run == 1 ? idesc : idesc_f16(64, 64 * run);
+                    const uint32_t dt = tmem + (uint32_t)((t + u - 2) * 64);
                     const uint32_t b0 = base + (uint32_t)((u - 1) * GZ_SLICE_BYTES);
 #pragma unroll
-                    for (int ks = 0; ks < GZ_KC / 16; ++ks) {
-                        mma_f16(dt, desc_sw128(a0 + ks * 32), desc_sw128(b0 + ks * 32), idesc,
-                                acc ? 1u : 0u);
-                        acc = true;
-                    }
+                    for (int ks = 0; ks < GZ_KC / 16; ++ks)
+                        mma_f16(dt, desc_sw128(a0 + ks * 32), desc_sw128(b0 + ks * 32), id,
+                                (first && t == 1 && ks == 0) ? 0u : 1u);
                 }
             }
             mma_commit(su32(&bar_mma[b]));
@@ -762,19 +768,24 @@ __global__ void __launch_bounds__(UZ_THREADS, 1) update_ozaki_kernel(
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
     if (tid == 0) {
+        // As in the Gram: with N = 64 the B tiles of digits u, u + 1, ... (64-row
+        // slices) and the groups t + u, t + u + 1, ... are adjacent, so one
+        // product with N = 64 * run covers a run of up to four; digit t = 1
+        // initializes every group.
         const uint32_t idesc = idesc_f16(UZ_M, NP);
+        const bool mergeable = NP == 64;
         const uint32_t a_base = su32(sA), b_base = su32(sB);
-        for (int d = 2; d <= s + 1; ++d) {
-            const uint32_t dt = tmem + (uint32_t)((d - 2) * NP);
-            bool first = true;
-            for (int t = 1; t <= s; ++t) {
-                const int u = d - t;
-                if (u < 1 || u > s) continue;
-                for (int ks = 0; ks < KP / 16; ++ks) {
+        for (int t = 1; t <= s; ++t) {
+            const int umax = s + 1 - t;
+            for (int u = 1; u <= umax;) {
+                const int run = mergeable ? min(4, umax - u + 1) : 1;
+                const uint32_t id = run == 1 ? idesc : idesc_f16(UZ_M, 64 * run);
+                const uint32_t dt = tmem + (uint32_t)((t + u - 2) * NP);
+                for (int ks = 0; ks < KP / 16; ++ks)
                     mma_f16(dt, desc_sw128(a_base + (t - 1) * UZ_ASLICE + ks * 32),
-                            desc_sw128(b_base + (u - 1) * UZ_BSLICE + ks * 32), idesc, first ? 0u : 1u);
-                    first = false;
-                }
+                            desc_sw128(b_base + (u - 1) * UZ_BSLICE + ks * 32), id,
+                            (t == 1 && ks == 0) ? 0u : 1u);
+                u += run;
             }
         }
         mma_commit(su32(&bar_done));
