@@ -543,6 +543,8 @@ def run_threelevel(args):
         Gw = torch.empty_like(G0)
     out = {}
     for name, kw in (("three_level", dict(block_width=128, inner_block_width=16, gemm=gemm)),
+                     ("three_level_oriented", dict(block_width=128, inner_block_width=16, gemm=gemm,
+                                                   block_strategy=jj.JJ_BLOCK_ORIENTED)),
                      ("two_level", dict(block_width=128, gemm=jj.JJ_GEMM_FP64)),
                      ("plain", dict(block_width=0))):
         if name not in args.forms:
@@ -583,7 +585,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--max-sweeps", type=int, default=0,
                     help="cap the sweeps of each solve (0: to convergence; for short profiling runs)")
-    ap.add_argument("--forms", default="three_level,two_level,plain")
+    ap.add_argument("--forms", default="three_level,three_level_oriented,two_level,plain")
     args = ap.parse_args()
     args.block_width_set = any(a.startswith("--block-width") for a in sys.argv[1:])
     if args.one_step:

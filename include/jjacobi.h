@@ -79,8 +79,12 @@ typedef enum {
  *   JJ_BLOCK_ORIENTED  (B) in the first parallel step of a sweep one sweep over
  *                      all column pairs of R, in the other steps one pass over
  *                      the off-diagonal block only (each pair (r in block i,
- *                      s in block j) annihilated once, Alg. 3.4). Two-level
- *                      only; pivots up to 128 real columns. */
+ *                      s in block j) annihilated once, Alg. 3.4). In the
+ *                      three-level form (3B, Alg. 5.1) the same at both levels:
+ *                      the first step's inner pass covers every inner block
+ *                      pair, the others only the cross pairs (inner blocks of
+ *                      block i against those of block j). Two-level pivots up
+ *                      to 128 real columns. */
 typedef enum { JJ_FULL_BLOCK = 0, JJ_BLOCK_ORIENTED = 1 } jj_block_strategy;
 
 /* block_width value that lets the library pick the block width: at the first

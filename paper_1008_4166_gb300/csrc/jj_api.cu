@@ -274,24 +274,41 @@ int build_three(jj_ctx *c, const std::vector<int32_t> &tab) {
         std::vector<std::vector<int32_t>> offs(np), sizes(np), sched(np);
         std::vector<int> nbl(np, 0), steps(np, 0);
         int smax = 0;
+        // B strategy, steps after the first: only the off-diagonal block (Alg. 5.1)
+        const bool cross = c->p.block_strategy == JJ_BLOCK_ORIENTED && t > 0;
         for (int q = 0; q < np; ++q) {
-            const int k = tab[4 * (s0 + q) + 1] + tab[4 * (s0 + q) + 3];
-            int nb = 2 * ((k + 2 * T.ib - 1) / (2 * T.ib));
-            if (nb > k - (k & 1)) nb = k - (k & 1);
-            if (nb < 2) nb = 2;
-            nbl[q] = nb;
-            const int br = k % nb, nmin = k / nb;
-            sizes[q].resize(nb);
-            offs[q].resize(nb + 1);
+            // inner blocks respect the outer boundary (Alg. 3.4's assumption):
+            // nb blocks of each outer block, uniform partitions (3.3)
+            const int ni = tab[4 * (s0 + q) + 1], nj = tab[4 * (s0 + q) + 3];
+            int nb = std::max((ni + T.ib - 1) / T.ib, (nj + T.ib - 1) / T.ib);
+            nb = std::max(1, std::min(nb, std::min(ni, nj)));
+            const int nb2 = 2 * nb;
+            nbl[q] = nb2;
+            sizes[q].resize(nb2);
+            offs[q].resize(nb2 + 1);
             offs[q][0] = 0;
-            for (int l = 0; l < nb; ++l) {
-                sizes[q][l] = l < br ? nmin + 1 : nmin;
-                offs[q][l + 1] = offs[q][l] + sizes[q][l];
+            for (int h = 0; h < 2; ++h) {
+                const int w = h == 0 ? ni : nj, br = w % nb, nmin = w / nb;
+                for (int l = 0; l < nb; ++l) {
+                    sizes[q][h * nb + l] = l < br ? nmin + 1 : nmin;
+                    T.kmax_in = std::max(T.kmax_in, 2 * (nmin + (br ? 1 : 0)));
+                }
             }
-            T.kmax_in = std::max(T.kmax_in, 2 * (nmin + (br ? 1 : 0)));
-            sched[q].resize((size_t)2 * nb * nb);
-            steps[q] = schedule_pairs(nb, c->p.order, 1, sched[q].data());
-            if (steps[q] < 0) return JJ_INVALID_ARG;
+            for (int l = 0; l < nb2; ++l) offs[q][l + 1] = offs[q][l] + sizes[q][l];
+            if (cross) {
+                // round rho pairs inner block r of block i with (r + rho) mod nb of block j
+                steps[q] = nb;
+                sched[q].resize((size_t)2 * nb * nb);
+                for (int rho = 0; rho < nb; ++rho)
+                    for (int r = 0; r < nb; ++r) {
+                        sched[q][2 * ((size_t)rho * nb + r)] = r;
+                        sched[q][2 * ((size_t)rho * nb + r) + 1] = nb + (r + rho) % nb;
+                    }
+            } else {
+                sched[q].resize((size_t)2 * nb2 * nb2);
+                steps[q] = schedule_pairs(nb2, c->p.order, 1, sched[q].data());
+                if (steps[q] < 0) return JJ_INVALID_ARG;
+            }
             smax = std::max(smax, steps[q]);
         }
         T.steps.push_back(smax);
@@ -321,6 +338,8 @@ int build_three(jj_ctx *c, const std::vector<int32_t> &tab) {
         }
         T.max_slots = std::max(T.max_slots, slots);
     }
+    if (c->p.block_strategy == JJ_BLOCK_ORIENTED && !inner_single_pass_supported(c->cplx, T.kmax_in))
+        return JJ_INVALID_ARG;
     T.ozaki = ozaki_supported(c->cplx, T.kmax_in) && c->p.gemm != JJ_GEMM_FP64;
     T.ozaki_update = T.ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
     const size_t np = (size_t)std::max(P.maxnp, 1), npi = (size_t)std::max(T.max_np, 1);
@@ -440,8 +459,8 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
     const bool oz_ok = ozaki_supported(c->cplx, P.kmax);
     if (!three && (c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM) && !oz_ok)
         return JJ_INVALID_ARG;
-    if (c->p.block_strategy == JJ_BLOCK_ORIENTED &&
-        (three || !inner_single_pass_supported(c->cplx, P.kmax)))
+    if (c->p.block_strategy == JJ_BLOCK_ORIENTED && !three &&
+        !inner_single_pass_supported(c->cplx, P.kmax))
         return JJ_INVALID_ARG;
     c->ozaki = oz_ok && c->p.gemm != JJ_GEMM_FP64;
     c->ozaki_update = c->ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
@@ -674,7 +693,12 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
         JJ_CUDA(cudaMemsetAsync(T.d_rot, 0, 2 * (size_t)std::max(P.maxnp, 1) * sizeof(unsigned long long), st));
         L += 1;
         const int ts = T.steps[t];
-        for (int sw = 1; sw <= c->inner_max_sweeps; ++sw) {
+        // F: inner sweeps until one applies no rotation; B: one pass (the first
+        // outer step of a sweep over every inner block pair, recursively
+        // block-oriented; the other steps over the cross pairs only)
+        const bool bo = c->p.block_strategy == JJ_BLOCK_ORIENTED;
+        const int inner_sweeps = bo ? 1 : c->inner_max_sweeps;
+        for (int sw = 1; sw <= inner_sweeps; ++sw) {
             JJ_CUDA(cudaMemsetAsync(T.d_cnt, 0, kNumCounters * sizeof(unsigned long long), st));
             sweep_begin_kernel<<<1, 1, 0, st>>>(T.d_sweep);
             JJ_CUDA(cudaGetLastError());
@@ -716,8 +740,9 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
                     JJ_CUDA(launch_gram(c->cplx, c->p.gemm, T.X, T.ldx, P.kmax, ip, ni, T.Ain, T.kmax_in, st, ic));
                     L += 1;
                 }
+                const int ipass = bo ? ((t == 0 && ti == 0) ? 2 : 1) : 0;
                 JJ_CUDA(launch_inner(c->cplx, T.Ain, T.Win, T.kmax_in, ip, ni, T.d_JX, c->tol,
-                                     c->inner_max_sweeps, 0, T.d_cnt, st, ic, ud));
+                                     c->inner_max_sweeps, 0, T.d_cnt, st, ic, ud, ipass));
                 if (T.ozaki_update)
                     JJ_CUDA(launch_update_ozaki(c->cplx, T.X, T.X, T.ldx, 2 * P.kmax, ip, ni, T.Win,
                                                 T.kmax_in, T.d_cexp2, ozaki_default_slices(false),

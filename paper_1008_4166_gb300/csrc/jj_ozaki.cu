@@ -429,8 +429,10 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
             for (int t = 1; t <= GZ_SLICES; ++t) {
                 const int umax = GZ_SLICES + 1 - t;
                 const uint32_t a0 = base + (uint32_t)((t - 1) * GZ_SLICE_BYTES);
-                for (int u = 1; u <= umax; u += 4) {
-                    const int run = min(4, umax - u + 1);  // adjacent tiles in one product
+                for (int u = 1; u <= umax;) {
+                    // adjacent tiles in one product (only when a tile has no
+                    // padding rows, which a wider N would multiply)
+                    const int run = NP == 64 ? min(4, umax - u + 1) : 1;
                     const uint32_t id = run == 1 ? idesc : idesc_f16(64, 64 * run);
                     const uint32_t dt = tmem + (uint32_t)((t + u - 2) * 64);
                     const uint32_t b0 = base + (uint32_t)((u - 1) * GZ_SLICE_BYTES);
@@ -438,6 +440,7 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
                     for (int ks = 0; ks < GZ_KC / 16; ++ks)
                         mma_f16(dt, desc_sw128(a0 + ks * 32), desc_sw128(b0 + ks * 32), id,
                                 (first && t == 1 && ks == 0) ? 0u : 1u);
+                    u += run;
                 }
             }
             mma_commit(su32(&bar_mma[b]));

@@ -317,8 +317,10 @@ def test_block_oriented_complex_ragged_and_graded(order):
     assert max_rel_err(gg["lam"], refg["lam"]) <= 1e-10
 
 
-def test_block_oriented_rejects_three_level():
+def test_block_oriented_rejects_pivots_beyond_shared_memory():
+    """Single passes run in the shared-memory inner kernel: a two-level
+    block-oriented solve with 256-column pivots is refused (the three-level
+    form takes such pivots)."""
     jj = require_gpu()
     with pytest.raises(jj.JJError):
-        jj.Handle(256, 256, jj.JJ_F64, block_width=32, inner_block_width=8,
-                  block_strategy=jj.JJ_BLOCK_ORIENTED)
+        jj.Handle(1024, 1024, jj.JJ_F64, block_width=128, block_strategy=jj.JJ_BLOCK_ORIENTED)

@@ -57,6 +57,42 @@ def test_three_level_agrees_with_two_level_wide_pivot():
     assert max_rel_err(three["lam"], two["lam"]) <= tol
 
 
+@pytest.mark.parametrize("gemm", [0, 1, 2])
+def test_three_level_block_oriented_matches_oracle(gemm):
+    """3B (Sec. 5.2-5.3, Alg. 5.1): in the first step of a sweep one
+    block-oriented inner pass over every inner block pair of the pivot, in the
+    other steps one pass over the cross pairs (inner blocks of block i against
+    inner blocks of block j) only."""
+    jj = require_gpu()
+    P = synth.make_workload("threelevel_f64_n16384_b128", n=256)
+    ref = oracle.solve_plain(P.G, P.J)
+    got = solve_gpu(P.G, P.J, block_width=32, inner_block_width=8, gemm=gemm,
+                    block_strategy=jj.JJ_BLOCK_ORIENTED, want_U=True)
+    tol = eig_rel_tol(P.G)
+    assert got["info"]["status"] == 0
+    assert max_rel_err(got["lam"], ref["lam"]) <= tol
+    assert max_rel_err(got["lam"], P.lam_exact) <= tol
+    assert orth_residual(got["U"]) <= 8 * oracle.TOL_DEFAULT
+    assert reconstruction_residual(P.G, P.J, got["lam"], got["U"]) <= 1e-12
+
+
+def test_three_level_block_oriented_complex_ragged_wide():
+    """3B with unequal outer blocks and ragged inner blocks (complex, 150
+    columns, b = 20, inner 6), and with 256-column outer pivots (n = 1024)."""
+    jj = require_gpu()
+    P = synth.make_workload("plain_c128_n128", n=150)
+    ref = oracle.solve_plain(P.G, P.J)
+    got = solve_gpu(P.G, P.J, block_width=20, inner_block_width=6, gemm=1,
+                    block_strategy=jj.JJ_BLOCK_ORIENTED)
+    assert got["info"]["status"] == 0
+    assert max_rel_err(got["lam"], ref["lam"]) <= eig_rel_tol(P.G)
+    Q = synth.make_workload("threelevel_f64_n16384_b128", n=1024)
+    w = solve_gpu(Q.G, Q.J, block_width=128, inner_block_width=16, gemm=1,
+                  block_strategy=jj.JJ_BLOCK_ORIENTED)
+    assert w["info"]["status"] == 0
+    assert max_rel_err(w["lam"], Q.lam_exact) <= eig_rel_tol(Q.G)
+
+
 def test_three_level_inner_width_not_below_pivot_is_two_level():
     """inner_block_width >= half the pivot: the two-level form runs (same bits)."""
     require_gpu()
