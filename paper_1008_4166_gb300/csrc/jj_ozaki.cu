@@ -29,8 +29,6 @@
 // chunks of row r XOR-ed with r mod 8. They are written by the producer
 // threads (the digits are computed, not copied), then fenced to the async
 // proxy before the single issuing thread launches tcgen05.mma.
-#include <cuda_fp16.h>
-
 #include "jj_common.cuh"
 
 namespace jj {
@@ -160,24 +158,6 @@ __device__ __forceinline__ unsigned long long fixed63(double x, int e) {
     if (sh >= 0) return mant << sh;
     if (sh <= -64) return 0ull;
     return mant >> (-sh);
-}
-
-// Two digits t (1-based) of two fixed-point values as a packed fp16 pair, with
-// the signs of their sources. A digit d <= 127 is formed exactly as
-// (1024 + d) - 1024 in fp16 ((1024 + d) has the bit pattern 0x6400 | d), and the
-// sign is set on the bit pattern: integer and fp16 ALU work only.
-__device__ __forceinline__ __half2 digits2(unsigned long long q0, bool n0, unsigned long long q1,
-                                          bool n1, int t) {
-    const uint32_t d0 = (uint32_t)((q0 >> (63 - kBeta * t)) & 127ull);
-    const uint32_t d1 = (uint32_t)((q1 >> (63 - kBeta * t)) & 127ull);
-    const uint32_t biased = (0x6400u | d0) | ((0x6400u | d1) << 16);
-    __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&biased), __half2(__half(1024.f), __half(1024.f)));
-    uint32_t bits = *reinterpret_cast<uint32_t *>(&h);
-    bits ^= (n0 ? 0x8000u : 0u) | (n1 ? 0x80000000u : 0u);
-    return *reinterpret_cast<__half2 *>(&bits);
-}
-__device__ __forceinline__ __half digit(unsigned long long q, bool neg, int t) {
-    return __low2half(digits2(q, neg, 0ull, false, t));
 }
 
 // v * 2^e as a double, built from the integer's bits (normalize, round to
@@ -727,14 +707,18 @@ __global__ void __launch_bounds__(UZ_THREADS, 1) update_ozaki_kernel(
     if (!wpre) {
         // digits of the columns of D W2: B operand row j, K position a;
         // (D W2)_aj < 2^w_j  <=>  W2_aj < 2^(w_j - e_a)
-        for (int idx = tid; idx < K2 * K2; idx += UZ_THREADS) {
-            const int a = idx % K2, j = idx / K2;
-            const double x = w2val(a, j);
-            const unsigned long long q = fixed63(x, wexp[j] - xexp[a]);
+        // K positions a, a + 1 per thread: one 32-bit shared store per digit
+        const int K2h = (K2 + 1) / 2;
+        for (int idx = tid; idx < K2 * K2h; idx += UZ_THREADS) {
+            const int a = (idx % K2h) * 2, j = idx / K2h;
+            const double x0 = w2val(a, j);
+            const double x1 = a + 1 < K2 ? w2val(a + 1, j) : 0.0;
+            const unsigned long long q0 = fixed63(x0, wexp[j] - xexp[a]);
+            const unsigned long long q1 = a + 1 < K2 ? fixed63(x1, wexp[j] - xexp[a + 1]) : 0ull;
             const uint32_t off = sw128_off(j, a * 2);
-            const bool ng = neg_bits(x);
             for (int t = 1; t <= s; ++t)
-                *reinterpret_cast<__half *>(sB + (t - 1) * UZ_BSLICE + off) = digit(q, ng, t);
+                *reinterpret_cast<uint32_t *>(sB + (t - 1) * UZ_BSLICE + off) =
+                    dg_digits2_bits(q0, neg_bits(x0), q1, neg_bits(x1), t);
         }
     }
     // digits of X rows: A operand row r, K positions a, a+1 (consecutive threads
