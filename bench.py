@@ -154,6 +154,14 @@ def cpu_baseline(P, budget_s: float = 15.0):
     return best
 
 
+def bench_config(args, P, world: int = 1) -> dict:
+    """The workload and launch configuration both arms report."""
+    return {"workload": args.workload, "m": P.m, "n": P.n, "block_width": args.block_width,
+            "gemm": args.gemm, "strategy": args.strategy, "order": "round_robin",
+            "l2": "inputs larger than L2 (G = 256 MiB; every step reads and writes it)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     rank, world, local = _dist()
     if rank != 0:
@@ -172,7 +180,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.median(x[2] for x in vals) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": P.n, "m": P.m, "form": "plain oracle sample"},
+        "config": bench_config(args, P, world),
         "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                          "sample": f"one row-cyclic plain sweep on the leading {vals[0][1]} "
                                    f"columns (all {P.m} rows) of the n={P.n} input"},
@@ -388,13 +396,9 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "m": m, "n": n, "block_width": args.block_width,
-                       "gemm": args.gemm, "strategy": args.strategy, "order": "round_robin",
-                       "sweeps": info["sweeps"],
-                       "steps_per_sweep": info["steps_per_sweep"],
-                       "time_to_solution_s": ms / 1e3, "max_sweeps": args.max_sweeps or None,
-                       "l2": "inputs larger than L2 (G = 256 MiB; every step reads and writes it)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": dict(bench_config(args, P, world), sweeps=info["sweeps"],
+                           steps_per_sweep=info["steps_per_sweep"], time_to_solution_s=ms / 1e3,
+                           max_sweeps=args.max_sweeps or None),
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "plain": plain,
         }
