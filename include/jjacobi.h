@@ -187,10 +187,12 @@ int jjacobi_solve_host(jj_handle h, const void *G_host, int64_t ldg, const int8_
  * sweeps stop on a pivot Gram block that is not positive definite in working
  * precision (columns too close to dependent for A_P = G_P^* G_P, Sec. 3.2) is
  * finished by the plain method from its current columns; its jj_info then
- * reports block_width 0. infos (may be NULL)
- * receives one jj_info per problem (pairs_evaluated, pairs_rotated,
- * kernel_launches, seconds and last_max_offdiag are batch totals). Returns the
- * first non-OK problem status, else JJ_OK. jjacobi_extract does not apply. */
+ * reports block_width 0. infos (may be NULL) receives one jj_info per problem
+ * (pairs_evaluated, pairs_rotated, kernel_launches, seconds and
+ * last_max_offdiag are batch totals). A batch whose parallel step would hold
+ * more than 65535 block pairs is refused with JJ_INVALID_ARG (split it).
+ * Returns the first non-OK problem status, else JJ_OK. jjacobi_extract does
+ * not apply. */
 int jjacobi_solve_batched(jj_handle h, int32_t count, void *const *G, const int64_t *m,
                           const int64_t *n, const int64_t *ldg, const int8_t *const *J,
                           double *lambda_out, jj_info *infos);

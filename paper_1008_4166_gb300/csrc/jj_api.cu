@@ -340,6 +340,7 @@ int build_three(jj_ctx *c, const std::vector<int32_t> &tab) {
     }
     if (c->p.block_strategy == JJ_BLOCK_ORIENTED && !inner_single_pass_supported(c->cplx, T.kmax_in))
         return JJ_INVALID_ARG;
+    if (T.max_np > 65535) return JJ_INVALID_ARG;
     T.ozaki = ozaki_supported(c->cplx, T.kmax_in) && c->p.gemm != JJ_GEMM_FP64;
     T.ozaki_update = T.ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
     const size_t np = (size_t)std::max(P.maxnp, 1), npi = (size_t)std::max(T.max_np, 1);
@@ -451,6 +452,8 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
         P.maxnp = std::max(P.maxnp, np);
     }
     c->plan_batched = batched;
+    // the pair kernels index pairs with blockIdx.y (at most 65535 per launch)
+    if (P.maxnp > 65535) return JJ_INVALID_ARG;
     // three-level: the inner method blocked with inner_block_width columns
     const int ib = c->p.inner_block_width;
     const bool three = !batched && ib > 0 && P.kmax > 2 * ib;
