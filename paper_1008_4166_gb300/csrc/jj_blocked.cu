@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(IT) inner_kernel(double *__restrict__ A, doubl
 constexpr int ST = 512;  // threads per block
 constexpr int SW = ST / 32;
 
-template <bool CPLX, int ROWS>
+template <bool CPLX, int ROWS, bool OFFD>
 __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double *__restrict__ A, double *__restrict__ Wb, int kmax, const int32_t *__restrict__ pairs,
     const int8_t *__restrict__ J, double tol, int max_sweeps,
@@ -502,11 +502,11 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     __shared__ int s_rot, s_fail;
     __shared__ double s_piv;
     __shared__ double s_max[SW];
-    __shared__ unsigned long long s_tmask[2];
+    __shared__ unsigned char s_tcol[128];  // column rotated (one writer per column and step)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *Ag = A + (int64_t)blockIdx.x * kmax * kmax * E;
     for (int a = tid; a < k; a += ST) jsh[a] = J[pivot_col(pd, a)];
-    if (tid < 2) s_tmask[tid] = 0ull;
+    if (tid < 128) s_tcol[tid] = 0;
     // load the upper triangle of A_P, zero below
     for (int t = tid; t < k * k; t += ST) {
         const int a = t % k, b = t / k;
@@ -594,13 +594,13 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     // annihilates the off-diagonal block once: round rho pairs column r of the
     // first block with column (r + rho) mod max(n_i, n_j) of the second.
     const int ni = pd[1], nj = pd[3];
-    const bool offd = pass == 1;
+    constexpr bool offd = OFFD;  // pass 1 (compile-time: the full passes keep the plain mapping)
     const int NB = ni > nj ? ni : nj;
     const int S = offd ? NB : P;            // inner steps per pass
     const int nq = offd ? ni : npl / 2;     // column pairs per inner step (<= 64)
     const int npass = pass == 0 ? max_sweeps : 1;
     auto pair_at = [&](int st, int qi, int &a, int &b) -> bool {
-        if (offd) {
+        if constexpr (offd) {
             const int s2 = (qi + st) % NB;
             a = qi;
             b = ni + s2;
@@ -730,8 +730,8 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
                                     dsh[b] = Q.ds;
                                     flag = 1.0;
                                     ++my_rot;
-                                    atomicOr(&s_tmask[a >> 6], 1ull << (a & 63));
-                                    atomicOr(&s_tmask[b >> 6], 1ull << (b & 63));
+                                    s_tcol[a] = 1;
+                                    s_tcol[b] = 1;
                                 } else {
                                     atomicOr(&counters[kCntErr], kErrNotPosdef);
                                     pair_flag_prob(ctl, blockIdx.x, kErrNotPosdef);
@@ -862,8 +862,14 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         pair_record(ctl, pd, blockIdx.x, total_rot > 0, false);
         pair_count_prob(ctl, blockIdx.x, total_rot);
         if (ctl.touched) {
-            ctl.touched[2 * blockIdx.x] = s_tmask[0];
-            ctl.touched[2 * blockIdx.x + 1] = s_tmask[1];
+            unsigned long long m0 = 0ull, m1 = 0ull;
+            for (int c = 0; c < k && c < 128; ++c)
+                if (s_tcol[c]) {
+                    if (c < 64) m0 |= 1ull << c;
+                    else m1 |= 1ull << (c - 64);
+                }
+            ctl.touched[2 * blockIdx.x] = m0;
+            ctl.touched[2 * blockIdx.x + 1] = m1;
         }
     }
 }
@@ -937,7 +943,7 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
     if (smb <= 227 * 1024 && kmax <= 128) {
 #define JJ_INNER_SMEM(C, RW)                                                                  \
     do {                                                                                      \
-        auto kern = inner_smem_kernel<C, RW>;                                                 \
+        auto kern = pass == 1 ? inner_smem_kernel<C, RW, true> : inner_smem_kernel<C, RW, false>; \
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)smb);                                       \
         if (e != cudaSuccess) return e;                                                       \
