@@ -18,6 +18,8 @@ single-threaded) on a bounded sample of the same workload.
 --one-step runs only the first parallel step of the sweep (column exponents,
 Gram, inner solve, update of every block pair) through the building-block
 entry points, K times: the small case for kernel profiles.
+--study orders,crossover times round-robin against modulus ordering and the
+plain form against the blocked forms over n (graded complex recipe).
 """
 from __future__ import annotations
 
@@ -571,6 +573,50 @@ def run_threelevel(args):
           flush=True)
 
 
+def run_study(args):
+    """Two studies on the graded complex recipe (one solve per point, CUDA events):
+    round-robin against modulus ordering at the headline size, and the plain
+    form against the blocked forms over n (the crossover; time / n^3)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    from paper_1008_4166_gb300 import jjacobi as jj
+
+    def solve(P, **kw):
+        G = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()
+        with jj.Handle(P.m, P.n, jj.JJ_C128, **kw) as h:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = h.jjacobi_solve(G, G.stride(1), P.J)
+            e1.record()
+            torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, info.sweeps
+
+    out = {"orders": {}, "crossover": {}}
+    hyb = dict(block_width=16, gemm=jj.JJ_GEMM_OZAKI_GRAM, block_strategy=jj.JJ_BLOCK_ORIENTED)
+    dig = dict(block_width=16, gemm=jj.JJ_GEMM_OZAKI_FP16, block_strategy=jj.JJ_BLOCK_ORIENTED)
+    if "orders" in args.study:
+        P = synth.make_workload("graded_c128_n4096_b64", precision="f64")
+        for name, order in (("round_robin", jj.JJ_ORDER_ROUND_ROBIN), ("modulus", jj.JJ_ORDER_MODULUS)):
+            t, sw = solve(P, order=order, **hyb)
+            out["orders"][name] = {"seconds": t, "sweeps": sw}
+        print(json.dumps(out), flush=True)
+    if "crossover" in args.study:
+        for n in (256, 512, 1024, 2048):
+            P = synth.make_workload("graded_c128_n4096_b64", n=n, precision="f64")
+            row = {}
+            for name, kw in (("plain", dict(block_width=0)), ("blocked_hybrid", hyb), ("blocked_digit", dig)):
+                t, sw = solve(P, **kw)
+                row[name] = {"seconds": t, "sweeps": sw, "c_ns_per_n3": t / n ** 3 * 1e9}
+            out["crossover"][n] = row
+            print(json.dumps({"n": n, **row}), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -590,9 +636,12 @@ def main():
     ap.add_argument("--max-sweeps", type=int, default=0,
                     help="cap the sweeps of each solve (0: to convergence; for short profiling runs)")
     ap.add_argument("--forms", default="three_level,three_level_oriented,two_level,plain")
+    ap.add_argument("--study", default="", help="orders,crossover: ordering and crossover studies")
     args = ap.parse_args()
     args.block_width_set = any(a.startswith("--block-width") for a in sys.argv[1:])
-    if args.one_step:
+    if args.study:
+        run_study(args)
+    elif args.one_step:
         run_one_step(args)
     elif args.workload == "batched_c128_512x":
         run_batched(args)
