@@ -139,3 +139,96 @@ def test_transitions_move_one_block_per_process():
                             assert tr[t][x.send_to].recv == x.send
                             assert tr[t][x.send_to].recv_from == q
                         assert have == set(int(v) for v in nlay[q])
+
+
+class _DroppingDist:
+    """torch.distributed with the first point-to-point send of this rank dropped
+    (the message never leaves: a lost message on the host side)."""
+
+    def __init__(self, dist):
+        self._d = dist
+        self.dropped = False
+
+    def isend(self, tensor, dst, tag=0):
+        if not self.dropped:
+            self.dropped = True
+
+            class _Done:
+                def wait(self):
+                    return True
+            return _Done()
+        return self._d.isend(tensor, dst, tag=tag)
+
+    def __getattr__(self, name):
+        return getattr(self._d, name)
+
+
+def _worker_fault(rank, world, port, mode, q):
+    import time as _t
+
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1008_4166_gb300 import ring
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world, timeout=timedelta(seconds=5))
+    P, perm, Gp, Jp, nbl, sizes, offs = _setup(32, 4)
+    tab = ring.schedule(nbl, 0, 1)
+    blocks = {}
+    for qq in range(nbl // 2):
+        if qq % world == rank:
+            for blk in tab[0][qq]:
+                blocks[int(blk)] = torch.from_numpy(np.ascontiguousarray(Gp[:, offs[blk]:offs[blk + 1]]))
+    late = {"done": False}
+
+    def pair_fn(i, j, Xi, Xj):
+        if mode == "late" and rank == 1 and not late["done"]:
+            late["done"] = True
+            _t.sleep(12)  # beyond the group's 5 s timeout, before its first exchange
+        cols = np.concatenate([np.arange(offs[i], offs[i + 1]), np.arange(offs[j], offs[j + 1])])
+        GP = np.asfortranarray(np.concatenate([Xi.numpy(), Xj.numpy()], axis=1))
+        res = oracle.inner_solve(oracle.cholesky_upper(oracle.gram(GP)), Jp[cols])
+        out = oracle.update(GP, res["W"])
+        Xi.copy_(torch.from_numpy(np.ascontiguousarray(out[:, :sizes[i]])))
+        Xj.copy_(torch.from_numpy(np.ascontiguousarray(out[:, sizes[i]:])))
+        return res["rotations"]
+
+    d = _DroppingDist(dist) if (mode == "drop_message" and rank == 1) else dist
+    t0 = _t.time()
+    status, sweeps = ring.ring_sweeps(rank, world, blocks, list(sizes), nbl, 0, pair_fn, dist=d)
+    q.put((rank, status, _t.time() - t0))
+
+
+def _run_fault(mode):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_fault, args=(r, 2, port, mode, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = []
+    for _ in range(2):
+        try:
+            out.append(q.get(timeout=120))
+        except Exception:
+            break
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+    return sorted(out)
+
+
+@pytest.mark.parametrize("mode", ["drop_message", "late"])
+def test_ring_lost_message_or_late_rank_returns_error(mode):
+    """A block that never arrives (rank 1 drops its first send), or a rank that
+    is late beyond the group timeout: the waiting rank's exchange fails within
+    the timeout and ring_sweeps returns RING_PEER_LOST instead of hanging."""
+    from paper_1008_4166_gb300 import ring
+
+    res = _run_fault(mode)
+    assert res, "no rank reported"
+    waiting = [r for r in res if r[0] == 0]
+    assert waiting and waiting[0][1] == ring.RING_PEER_LOST
+    assert waiting[0][2] < 60
