@@ -21,6 +21,10 @@ Contents
   solve_blocked(...)   the two-level full-block algorithm (2F) of Alg. 5.2 on one
                        address space: Gram (3.6), Cholesky, inner Alg. 3.2 on R
                        with explicit accumulation of W (3.12), update (2.9).
+  solve_block_oriented(...)  the two-level block-oriented algorithm (2B: one
+                       pass per pivot, Alg. 3.4 / Sec. 5.3).
+  solve_three_level(...)     the three-level algorithms (3F, 3B: the inner
+                       method on R blocked, Algs. 3.3 and 5.1).
 
 Every function is pinned by tests/test_oracle_*.py against closed forms,
 invariants, constructions with known eigenvalues, LAPACK special cases and
@@ -136,7 +140,7 @@ def _as_work(G: np.ndarray, precision: str) -> np.ndarray:
 def solve_plain(G: np.ndarray, J: Sequence[int], tol: float = TOL_DEFAULT,
                 max_sweeps: int = 60, order: int = ORDER_ROW_CYCLIC,
                 accumulate: bool = False, precision: str = "f64",
-                mutation: int = 0) -> Dict[str, object]:
+                mutation: int = 0, table: Optional[np.ndarray] = None) -> Dict[str, object]:
     """Non-blocked one-sided J-Jacobi (Alg. 3.2 with Alg. 3.1 as the sweep).
 
     G is m x n (m >= n, full column rank), J a vector of +-1. Returns a dict with
@@ -158,9 +162,13 @@ def solve_plain(G: np.ndarray, J: Sequence[int], tol: float = TOL_DEFAULT,
     rots = np.zeros(1, dtype=np.int64)
     R = np.longdouble if precision == "ld" else np.float64
     maxoff = np.zeros(1, dtype=R)
-    table = None
     nsteps = 0
-    if order == ORDER_ROUND_ROBIN:
+    if table is not None:
+        # an explicit sweep: [steps][n_pad/2][2] column pairs, entries >= n skipped
+        order = ORDER_ROUND_ROBIN
+        nsteps = int(table.shape[0])
+        table = np.ascontiguousarray(np.asarray(table, dtype=np.int32))
+    elif order == ORDER_ROUND_ROBIN:
         tab = column_rr_table(n)
         nsteps = tab.shape[0]
         table = np.ascontiguousarray(tab.astype(np.int32))
@@ -442,3 +450,204 @@ def solve_blocked(G: np.ndarray, J: Sequence[int], block_width: int,
     lam, U = eigenpairs(Gt, Jv)
     return dict(Gt=Gt, lam=lam, U=U, status=status, sweeps=sweeps, rotations=total_rot,
                 nbl=nbl, sizes=sizes)
+
+
+# ---------------------------------------------------------------------------
+# Block-oriented strategy (Alg. 3.4, Sec. 5.3 case B) and the three-level
+# forms (Sec. 5.1-5.2, Algs. 3.3 and 5.1), sequentially
+# ---------------------------------------------------------------------------
+
+def pass_table(n: int, pairs: Sequence[Tuple[int, int]]) -> np.ndarray:
+    """A sweep table for solve_plain that visits `pairs` once, in the given
+    order (one pair per table step, the other slots dummies >= n)."""
+    npl = n + (n & 1)
+    tab = np.full((max(len(pairs), 1), npl // 2, 2), n, dtype=np.int32)
+    for t, (r, s) in enumerate(pairs):
+        tab[t, 0] = (r, s)
+    return tab
+
+
+def block_oriented_pairs(ni: int, nj: int, whole: bool) -> List[Tuple[int, int]]:
+    """Column pairs of one block-oriented pass over the pivot [G_i G_j] (Alg. 3.4):
+    whole = True (the first step of a sweep): the pairs inside block i, inside
+    block j (each row-cyclic), then the off-diagonal block; whole = False: the
+    off-diagonal block only, columns s of block j outer, r of block i inner."""
+    out = []
+    if whole:
+        for base, w in ((0, ni), (ni, nj)):
+            for r in range(w - 1):
+                for q in range(r + 1, w):
+                    out.append((base + r, base + q))
+    for q in range(nj):
+        for r in range(ni):
+            out.append((r, ni + q))
+    return out
+
+
+def _inner_pass(R: np.ndarray, JP, pairs, tol: float) -> Dict[str, object]:
+    """One pass of Alg. 3.1 rotations over the given column pairs of R, with the
+    transformation accumulated explicitly (3.12)."""
+    n = R.shape[1]
+    res = solve_plain(R, JP, tol=tol, max_sweeps=1, accumulate=True, table=pass_table(n, pairs))
+    return dict(Rt=res["Gt"], W=res["W"], status=res["status"], rotations=res["rotations"])
+
+
+def solve_block_oriented(G: np.ndarray, J: Sequence[int], block_width: int,
+                         strategy: int = STRATEGY_ROUND_ROBIN, tol: float = TOL_DEFAULT,
+                         max_sweeps: int = 60, whole_first: bool = True) -> Dict[str, object]:
+    """Two-level block-oriented algorithm (Sec. 5.3 case B, the sweeps of
+    Alg. 3.4 distributed over the parallel steps of Sec. 4): for every pivot pair
+    (i, j) of a step, A_P = [G_i G_j]^*[G_i G_j] (3.6), A_P = R^*R, then ONE pass
+    of rotations on the columns of R (the whole pivot in the first step of a
+    sweep, the off-diagonal block in the others), W accumulated (3.12), and
+    [G_i G_j] <- [G_i G_j] W (2.9). A sweep with no rotation ends it.
+    whole_first=False plants a mistake for the pin tests (no whole-pivot pass:
+    column pairs inside one block are never rotated)."""
+    G = np.asarray(G)
+    m, n = G.shape
+    Jv = np.asarray(J, dtype=np.int64)
+    perm = j_sort_permutation(Jv)
+    Gp = np.asfortranarray(G[:, perm].astype(np.complex128 if np.iscomplexobj(G) else np.float64))
+    Jp = Jv[perm]
+    nbl = 2 * ((n + 2 * block_width - 1) // (2 * block_width))
+    nbl = max(2, min(nbl, n - (n & 1)))
+    sizes = uniform_partition(n, nbl)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    status, sweeps, total = 2, 0, 0
+    for sweep in range(1, max_sweeps + 1):
+        sweeps = sweep
+        tab = schedule(nbl, strategy, sweep)
+        rot = 0
+        for step in range(tab.shape[0]):
+            for q in range(tab.shape[1]):
+                i, j = tab[step, q]
+                cols = np.concatenate([np.arange(offs[i], offs[i + 1]), np.arange(offs[j], offs[j + 1])])
+                GP = Gp[:, cols]
+                try:
+                    R = cholesky_upper(gram(GP))
+                except np.linalg.LinAlgError:
+                    return dict(Gt=None, status=3, sweeps=sweeps, rotations=total)
+                res = _inner_pass(R, Jp[cols],
+                                  block_oriented_pairs(sizes[i], sizes[j], whole_first and step == 0), tol)
+                if res["status"] == 3:
+                    return dict(Gt=None, status=3, sweeps=sweeps, rotations=total)
+                rot += res["rotations"]
+                Gp[:, cols] = update(GP, res["W"])
+        total += rot
+        if rot == 0:
+            status = 0
+            break
+    Gt = np.empty_like(Gp)
+    Gt[:, perm] = Gp
+    lam, U = eigenpairs(Gt, Jv)
+    return dict(Gt=Gt, lam=lam, U=U, status=status, sweeps=sweeps, rotations=total, nbl=nbl,
+                sizes=sizes)
+
+
+def _inner_blocks(ni: int, nj: int, ib: int) -> List[int]:
+    """Inner partition of a pivot that respects the boundary of its two blocks
+    (Sec. 5.2, Alg. 5.1): nb blocks of each, uniform partitions (3.3)."""
+    nb = max((ni + ib - 1) // ib, (nj + ib - 1) // ib)
+    nb = max(1, min(nb, ni, nj))
+    return uniform_partition(ni, nb) + uniform_partition(nj, nb)
+
+
+def _inner_blocked(R: np.ndarray, JP, ib: int, ni: int, nj: int, variant: str, first: bool,
+                   tol: float, inner_max_sweeps: int) -> Dict[str, object]:
+    """The inner problem of a three-level step on the Cholesky factor R of one
+    pivot: the blocked one-sided method on the columns of R (Alg. 3.3), with W
+    accumulated by applying every inner transformation to [R; W] too.
+    variant 'F': sweeps over all inner block pairs, each inner pivot solved to
+    convergence, until a sweep applies no rotation. variant 'B': one pass --
+    in the first outer step of a sweep over every inner block pair (each inner
+    pivot: its whole pass in the first inner step, its off-diagonal block in
+    the others), in the other outer steps over the pairs of an inner block of
+    block i with one of block j, each inner pivot's off-diagonal block once
+    (Alg. 5.1)."""
+    k = R.shape[1]
+    X = np.concatenate([R, np.eye(k, dtype=R.dtype)], axis=0)
+    isz = _inner_blocks(ni, nj, ib)
+    nb = len(isz) // 2
+    ioff = np.concatenate([[0], np.cumsum(isz)]).astype(np.int64)
+    total = 0
+
+    def pivot(a, b, whole_or_converge):
+        nonlocal total
+        cols = np.concatenate([np.arange(ioff[a], ioff[a + 1]), np.arange(ioff[b], ioff[b + 1])])
+        XP = X[:, cols]
+        Rin = cholesky_upper(gram(XP[:k]))
+        if variant == "F":
+            res = inner_solve(Rin, JP[cols], tol=tol, max_sweeps=inner_max_sweeps)
+        else:
+            res = _inner_pass(Rin, JP[cols], block_oriented_pairs(isz[a], isz[b], whole_or_converge), tol)
+        if res["status"] == 3:
+            raise np.linalg.LinAlgError("inner pivot not positive definite")
+        total += res["rotations"]
+        X[:, cols] = update(XP, res["W"])
+        return res["rotations"]
+
+    if variant == "F":
+        for sweep in range(1, inner_max_sweeps + 1):
+            tab = schedule(2 * nb, STRATEGY_ROUND_ROBIN, sweep)
+            rot = 0
+            for step in range(tab.shape[0]):
+                for a, b in tab[step]:
+                    rot += pivot(a, b, True)
+            if rot == 0:
+                break
+    elif first:
+        tab = schedule(2 * nb, STRATEGY_ROUND_ROBIN, 1)
+        for step in range(tab.shape[0]):
+            for a, b in tab[step]:
+                pivot(a, b, step == 0)
+    else:
+        for b in range(nb, 2 * nb):
+            for a in range(nb):
+                pivot(a, b, False)
+    return dict(W=X[k:], rotations=total)
+
+
+def solve_three_level(G: np.ndarray, J: Sequence[int], block_width: int, inner_width: int,
+                      variant: str = "F", strategy: int = STRATEGY_ROUND_ROBIN,
+                      tol: float = TOL_DEFAULT, max_sweeps: int = 60,
+                      inner_max_sweeps: int = 30) -> Dict[str, object]:
+    """Three-level algorithm (Sec. 5.1 case 3F, Sec. 5.2 case 3B): the two-level
+    step of Alg. 5.2 with the inner J-Jacobi on R itself blocked
+    (_inner_blocked), sequentially. A sweep with no rotation ends it."""
+    G = np.asarray(G)
+    m, n = G.shape
+    Jv = np.asarray(J, dtype=np.int64)
+    perm = j_sort_permutation(Jv)
+    Gp = np.asfortranarray(G[:, perm].astype(np.complex128 if np.iscomplexobj(G) else np.float64))
+    Jp = Jv[perm]
+    nbl = 2 * ((n + 2 * block_width - 1) // (2 * block_width))
+    nbl = max(2, min(nbl, n - (n & 1)))
+    sizes = uniform_partition(n, nbl)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    status, sweeps, total = 2, 0, 0
+    for sweep in range(1, max_sweeps + 1):
+        sweeps = sweep
+        tab = schedule(nbl, strategy, sweep)
+        rot = 0
+        for step in range(tab.shape[0]):
+            for q in range(tab.shape[1]):
+                i, j = tab[step, q]
+                cols = np.concatenate([np.arange(offs[i], offs[i + 1]), np.arange(offs[j], offs[j + 1])])
+                GP = Gp[:, cols]
+                try:
+                    R = cholesky_upper(gram(GP))
+                    res = _inner_blocked(R, Jp[cols], inner_width, sizes[i], sizes[j], variant,
+                                         step == 0, tol, inner_max_sweeps)
+                except np.linalg.LinAlgError:
+                    return dict(Gt=None, status=3, sweeps=sweeps, rotations=total)
+                rot += res["rotations"]
+                Gp[:, cols] = update(GP, res["W"])
+        total += rot
+        if rot == 0:
+            status = 0
+            break
+    Gt = np.empty_like(Gp)
+    Gt[:, perm] = Gp
+    lam, U = eigenpairs(Gt, Jv)
+    return dict(Gt=Gt, lam=lam, U=U, status=status, sweeps=sweeps, rotations=total, nbl=nbl,
+                sizes=sizes)
