@@ -1,0 +1,92 @@
+"""Host-side logic of bench.py (no GPU): the algorithmic flop conventions, the
+traffic lookup keyed to kernel sources, the clock sampler's parsing, and the
+reference arm's JSON line (the oracle on a bounded sample)."""
+import json
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_blocked_flop_convention():
+    # one pair (nbl = 2), one step, one sweep: Gram k(k+1)/2 m + update m k^2 MACs,
+    # plus 5 k MACs per inner rotation; complex MAC = 8 flops
+    info = {"nbl": 2, "sweeps": 1, "steps_per_sweep": 1, "rotations": 3}
+    n, m = 8, 10
+    k = 2.0 * n / 2
+    expect = 8.0 * (k * (k + 1) / 2 * m + m * k * k + 3 * 5.0 * k)
+    assert bench.blocked_flops(n, m, True, info) == pytest.approx(expect)
+    assert bench.blocked_flops(n, m, False, info) == pytest.approx(expect / 4.0)
+
+
+def test_plain_flop_convention():
+    # n(n-1)/2 pairs per sweep, 3 m MACs each (dot + two rotated columns)
+    assert bench.plain_flops(4, 10, True, 2) == pytest.approx(8.0 * 2 * 6 * 3 * 10)
+
+
+def test_captured_traffic_is_void_once_the_kernel_source_changes(tmp_path, monkeypatch):
+    fake = tmp_path / "repo"
+    (fake / "profiles").mkdir(parents=True)
+    csrc = fake / "paper_1008_4166_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("jj_update.cu", "jj_common.cuh"):
+        shutil.copy(os.path.join(ROOT, "paper_1008_4166_gb300", "csrc", f), csrc / f)
+    shutil.copy(os.path.join(ROOT, "profiles", "traffic.txt"), fake / "profiles" / "traffic.txt")
+    monkeypatch.setattr(bench, "ROOT", str(fake))
+    v = bench.captured_traffic("update_fp64_kernel")
+    assert isinstance(v, int) and v > 0
+    assert bench.captured_traffic("no_such_kernel") is None
+    with open(csrc / "jj_update.cu", "a") as fh:
+        fh.write("// edited\n")
+    assert bench.captured_traffic("update_fp64_kernel") is None
+
+
+def test_clock_sampler_parses_reasons():
+    s = bench.ClockSampler(0)
+
+    class _P:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    s.proc = _P()
+    s.lines = ["2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "2055, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "garbage line"]
+    out = s.stop()
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["sm_mhz"] == pytest.approx((2070 + 2055) / 2)
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 2
+
+
+def test_reference_arm_line_matches_the_measured_arm_config():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0", "--ref-budget", "1.5"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["unit"] == "GFLOP/s" and line["higher_is_better"] is True and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"] == {"value": line["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+    class _A:
+        workload = bench.WORKLOAD
+        block_width = 16
+        gemm = "hybrid"
+        strategy = "oriented"
+
+    class _P:
+        m = n = 4096
+
+    assert line["config"] == bench.bench_config(_A, _P)
+    assert line["metric"] == bench.METRIC
