@@ -180,7 +180,8 @@ int jjacobi_solve_host(jj_handle h, const void *G_host, int64_t ldg, const int8_
  * The handle's m and n bound the sizes (m[k] <= p->m, n[k] <= p->n); its
  * block_width is used for every problem (capped at ceil(n[k]/2)), or, when 0 or JJ_BLOCK_AUTO,
  * the widest block the contraction form takes (16 complex / 32 real columns for
- * the digit forms, 32 for FP64). Workspaces are (re)allocated on the first call
+ * the digit forms, 32 for FP64). Batched solves are two-level (inner_block_width
+ * is not used). Workspaces are (re)allocated on the first call
  * and kept while the shapes repeat. lambda_out (host or device, detected; sum of
  * n[k] doubles, problem k at offset sum_{l<k} n[l], each in its own column
  * order) receives lambda_i = J_ii ||g~_i||^2 if not NULL. A problem whose blocked
