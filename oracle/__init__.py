@@ -25,6 +25,9 @@ Contents
                        pass per pivot, Alg. 3.4 / Sec. 5.3).
   solve_three_level(...)     the three-level algorithms (3F, 3B: the inner
                        method on R blocked, Algs. 3.3 and 5.1).
+  cholesky_special, solve_blocked_special
+                       the Cholesky factor of a pivot with diagonal diagonal
+                       blocks (3.9)-(3.11), and 2F built on it (Sec. 3.3).
 
 Every function is pinned by tests/test_oracle_*.py against closed forms,
 invariants, constructions with known eigenvalues, LAPACK special cases and
@@ -639,6 +642,97 @@ def solve_three_level(G: np.ndarray, J: Sequence[int], block_width: int, inner_w
                     res = _inner_blocked(R, Jp[cols], inner_width, sizes[i], sizes[j], variant,
                                          step == 0, tol, inner_max_sweeps)
                 except np.linalg.LinAlgError:
+                    return dict(Gt=None, status=3, sweeps=sweeps, rotations=total)
+                rot += res["rotations"]
+                Gp[:, cols] = update(GP, res["W"])
+        total += rot
+        if rot == 0:
+            status = 0
+            break
+    Gt = np.empty_like(Gp)
+    Gt[:, perm] = Gp
+    lam, U = eigenpairs(Gt, Jv)
+    return dict(Gt=Gt, lam=lam, U=U, status=status, sweeps=sweeps, rotations=total, nbl=nbl,
+                sizes=sizes)
+
+
+# ---------------------------------------------------------------------------
+# Full block with diagonalized diagonal blocks: the special Cholesky (3.9)-(3.11)
+# ---------------------------------------------------------------------------
+
+def cholesky_special(lam_i: np.ndarray, lam_j: np.ndarray, Aij: np.ndarray,
+                     mutation: int = 0) -> np.ndarray:
+    """Cholesky factor R of a pivot with diagonal diagonal blocks (3.7):
+    R_ii = sqrt(Lambda_ii) (3.9), R_ij = R_ii^{-1} A_ij (3.10), and R_jj the
+    Cholesky factor of Lambda_jj - R_ij^* R_ij (3.11). Raises LinAlgError when
+    that block is not positive definite. mutation=1 plants a mistake for the
+    pins (A_ij scaled from the wrong side)."""
+    lam_i = np.asarray(lam_i, dtype=np.float64)
+    lam_j = np.asarray(lam_j, dtype=np.float64)
+    Aij = np.asarray(Aij)
+    ni, nj = len(lam_i), len(lam_j)
+    rii = np.sqrt(lam_i)
+    if mutation == 1:
+        Rij = Aij / rii[None, :nj] if nj <= ni else Aij / rii.mean()
+    else:
+        Rij = Aij / rii[:, None]
+    Rjj = cholesky_upper(np.diag(lam_j).astype(Aij.dtype) - Rij.conj().T @ Rij)
+    R = np.zeros((ni + nj, ni + nj), dtype=np.result_type(Aij.dtype, np.float64))
+    R[:ni, :ni] = np.diag(rii)
+    R[:ni, ni:] = Rij
+    R[ni:, ni:] = Rjj
+    return np.asfortranarray(R)
+
+
+def solve_blocked_special(G: np.ndarray, J: Sequence[int], block_width: int,
+                          strategy: int = STRATEGY_ROUND_ROBIN, tol: float = TOL_DEFAULT,
+                          max_sweeps: int = 60, inner_max_sweeps: int = 30) -> Dict[str, object]:
+    """Two-level full block (2F) with the structure of Sec. 3.3: at the start of
+    every sweep the diagonal block A_ii of every block is diagonalized (the
+    re-diagonalization of Sec. 5.3), so that each pivot has the form (3.7) and
+    its factor R comes from the special Cholesky (3.9)-(3.11) (the diagonal
+    blocks' off-diagonal entries, at most tol sqrt(a_rr a_ss) after a full
+    block solve, are taken as zero); then the inner J-Jacobi on R with W
+    accumulated (3.12) and the update (2.9), as in solve_blocked."""
+    G = np.asarray(G)
+    m, n = G.shape
+    Jv = np.asarray(J, dtype=np.int64)
+    perm = j_sort_permutation(Jv)
+    Gp = np.asfortranarray(G[:, perm].astype(np.complex128 if np.iscomplexobj(G) else np.float64))
+    Jp = Jv[perm]
+    nbl = 2 * ((n + 2 * block_width - 1) // (2 * block_width))
+    nbl = max(2, min(nbl, n - (n & 1)))
+    sizes = uniform_partition(n, nbl)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    status, sweeps, total = 2, 0, 0
+    for sweep in range(1, max_sweeps + 1):
+        sweeps = sweep
+        rot = 0
+        # diagonalize every diagonal block A_ii (one-sided, on the block's columns)
+        for i in range(nbl):
+            cols = np.arange(offs[i], offs[i + 1])
+            res = solve_plain(Gp[:, cols], Jp[cols], tol=tol, max_sweeps=inner_max_sweeps)
+            if res["status"] == 3:
+                return dict(Gt=None, status=3, sweeps=sweeps, rotations=total)
+            rot += res["rotations"]
+            Gp[:, cols] = res["Gt"]
+        tab = schedule(nbl, strategy, sweep)
+        for step in range(tab.shape[0]):
+            for q in range(tab.shape[1]):
+                i, j = tab[step, q]
+                ci = np.arange(offs[i], offs[i + 1])
+                cj = np.arange(offs[j], offs[j + 1])
+                cols = np.concatenate([ci, cj])
+                GP = Gp[:, cols]
+                lam_i = np.sum(np.abs(Gp[:, ci]) ** 2, axis=0)
+                lam_j = np.sum(np.abs(Gp[:, cj]) ** 2, axis=0)
+                Aij = Gp[:, ci].conj().T @ Gp[:, cj]
+                try:
+                    R = cholesky_special(lam_i, lam_j, Aij)
+                except np.linalg.LinAlgError:
+                    return dict(Gt=None, status=3, sweeps=sweeps, rotations=total)
+                res = inner_solve(R, Jp[cols], tol=tol, max_sweeps=inner_max_sweeps)
+                if res["status"] == 3:
                     return dict(Gt=None, status=3, sweeps=sweeps, rotations=total)
                 rot += res["rotations"]
                 Gp[:, cols] = update(GP, res["W"])

@@ -72,3 +72,49 @@ def test_mutation_no_whole_pivot_pass_breaks_block_oriented():
     ref = oracle.solve_plain(P.G, P.J)
     bad = oracle.solve_block_oriented(P.G, P.J, 5, whole_first=False, max_sweeps=30)
     assert bad["status"] != 0 or max_rel_err(bad["lam"], ref["lam"]) > 1e-6
+
+
+def _pivot_with_diagonal_blocks(rng, m, ni, nj, cplx):
+    """[G_i G_j] whose blocks have orthogonal columns: A_P has the form (3.7)."""
+    def block(w):
+        Z = rng.standard_normal((m, w)) + (1j * rng.standard_normal((m, w)) if cplx else 0)
+        Q, _ = np.linalg.qr(Z)
+        return Q * (10.0 ** rng.uniform(-2, 2, size=w))[None, :]
+    Gi, Gj = block(ni), block(nj)
+    # mix the two blocks (the pair is not yet orthogonal across blocks)
+    Gj = Gj + Gi @ (0.3 * rng.standard_normal((ni, nj)))
+    Q, Rr = np.linalg.qr(Gj)
+    Gj = Q * np.abs(np.diag(Rr))[None, :]  # re-orthogonalize within block j, keep the mixing
+    return Gi, Gj
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_special_cholesky_is_the_cholesky_factor(cplx):
+    rng = np.random.default_rng(21 + cplx)
+    for ni, nj in ((5, 5), (6, 4), (3, 7)):
+        Gi, Gj = _pivot_with_diagonal_blocks(rng, 30, ni, nj, cplx)
+        A = np.concatenate([Gi, Gj], axis=1)
+        A = A.conj().T @ A
+        lam_i = np.sum(np.abs(Gi) ** 2, axis=0)
+        lam_j = np.sum(np.abs(Gj) ** 2, axis=0)
+        R = oracle.cholesky_special(lam_i, lam_j, Gi.conj().T @ Gj)
+        scale = np.sqrt(np.outer(np.diag(A).real, np.diag(A).real))
+        assert np.max(np.abs(R.conj().T @ R - A) / scale) <= 1e-12
+        Rstd = oracle.cholesky_upper(A)  # unique with a positive diagonal
+        assert np.max(np.abs(R - Rstd)) <= 1e-10 * np.max(np.abs(Rstd))
+        try:  # the planted mistake: either the (3.11) block is no longer positive definite
+            bad = oracle.cholesky_special(lam_i, lam_j, Gi.conj().T @ Gj, mutation=1)
+        except np.linalg.LinAlgError:
+            continue
+        assert np.max(np.abs(bad.conj().T @ bad - A) / scale) > 1e-3  # or R^* R is not A
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_full_block_with_special_cholesky_matches_plain(cplx):
+    P = (synth.make_workload("plain_c128_n128", n=40) if cplx
+         else synth.make_workload("blocked_f64_n2048_b32", n=44))
+    ref = oracle.solve_plain(P.G, P.J)
+    got = oracle.solve_blocked_special(P.G, P.J, 5)
+    assert got["status"] == 0
+    assert max_rel_err(got["lam"], ref["lam"]) <= eig_rel_tol(P.G)
+    assert orth_residual(got["U"]) <= 8 * oracle.TOL_DEFAULT
