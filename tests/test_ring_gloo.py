@@ -109,6 +109,28 @@ def test_ring_two_ranks_matches_sequential_blocked(order):
     assert np.array_equal(Gt, ref["Gt"][:, perm])
 
 
+@pytest.mark.parametrize("order", [0, 1])
+def test_ring_three_ranks_matches_sequential_blocked(order):
+    """Three ranks for four processes (nbl = 8): processes 0 and 3 share rank 0,
+    so some exchanges are moves within a rank, the others messages."""
+    import oracle
+    from paper_1008_4166_gb300 import ring
+
+    n, b = 32, 4
+    res = _run(3, n, b, order, "ok")
+    P, perm, Gp, Jp, nbl, sizes, offs = _setup(n, b)
+    assert nbl == 8
+    blocks = {}
+    for rank, status, sweeps, _, blk in res:
+        assert status == ring.RING_OK
+        assert not (set(blocks) & set(blk))  # every block on exactly one rank
+        blocks.update(blk)
+    Gt = np.concatenate([blocks[k] for k in range(nbl)], axis=1)
+    ref = oracle.solve_blocked(P.G, P.J, b, strategy=order)
+    assert res[0][2] == ref["sweeps"]
+    assert np.array_equal(Gt, ref["Gt"][:, perm])
+
+
 def test_ring_rank_leaves_other_returns_error():
     from paper_1008_4166_gb300 import ring
 
