@@ -109,3 +109,49 @@ def test_product_does_not_import_oracle():
                 assert not pattern.search(txt), f
                 checked += 1
     assert checked >= 8
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "jjacobi.h"
+#include "jjacobi_kernels.h"
+
+int main(void) {
+    jj_params p;
+    jjacobi_default_params(&p, 100, 80, JJ_C128);
+    int32_t pairs[2 * 8 * 4];
+    int steps = jjacobi_schedule(8, JJ_ORDER_ROUND_ROBIN, 1, pairs);
+    jj_handle h = (jj_handle)0;
+    p.m = 10; p.n = 20;  /* m < n: refused before any device work */
+    int rc = jjacobi_create(&h, &p);
+    printf("%d %d %d %s %d %d %d\n", (int)jjacobi_version(), steps, pairs[0] * 100 + pairs[1],
+           jjacobi_status_string(JJ_NOT_POSDEF), rc, h == (jj_handle)0, p.max_sweeps);
+    jjacobi_destroy((jj_handle)0);
+    return 0;
+}
+"""
+
+
+def test_c_program_compiles_links_and_calls_the_abi(jj, tmp_path):
+    """The headers are valid C99 and the library links from C: host-only entry
+    points called from a C program (no GPU needed)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.join(ROOT, "paper_1008_4166_gb300")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-ljjacobi", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    ref = oracle.schedule(8, 0, 1)
+    assert out[0] == "10000" and out[1] == str(ref.shape[0])
+    assert int(out[2]) == int(ref[0, 0, 0]) * 100 + int(ref[0, 0, 1])
+    assert out[3] == "JJ_NOT_POSDEF" and int(out[4]) == jj.JJ_INVALID_ARG
+    assert out[5] == "1" and out[6] == "60"
