@@ -154,7 +154,9 @@ int jjacobi_create(jj_handle *h, const jj_params *p);
  * dtype of the handle) is overwritten by G~ = G W in the caller's column order
  * (the final re-permutation of Sec. 3.3). J (host, n entries of +-1) is copied.
  * Columns are permuted internally so that J = diag(I, -I) (Sec. 2.3).
- * info may be NULL. The handle keeps the G pointer for jjacobi_extract. */
+ * info may be NULL; otherwise it receives the status and the elapsed seconds on
+ * every return, errors included. The handle keeps the G pointer for
+ * jjacobi_extract. */
 int jjacobi_solve(jj_handle h, void *G, int64_t ldg, const int8_t *J, jj_info *info);
 
 /* Eigenpairs of the last solve (Alg. 5.2): lambda[i] = J_ii ||g~_i||^2
@@ -166,7 +168,9 @@ int jjacobi_extract(jj_handle h, double *lambda, void *U, int64_t ldu, int32_t s
 
 /* End-to-end call with host buffers: copies G_host (m x n, ldg) to the device,
  * solves, extracts lambda_host (n doubles) and, if U_host is not NULL, the
- * eigenvectors (m x n, ldu), and copies them back. G_host is not modified. */
+ * eigenvectors (m x n, ldu), and copies them back. G_host is not modified.
+ * info (may be NULL) is filled as by jjacobi_solve, with the seconds of the
+ * whole call. */
 int jjacobi_solve_host(jj_handle h, const void *G_host, int64_t ldg, const int8_t *J,
                        double *lambda_host, void *U_host, int64_t ldu, jj_info *info);
 
@@ -190,7 +194,9 @@ int jjacobi_solve_host(jj_handle h, const void *G_host, int64_t ldg, const int8_
  * finished by the plain method from its current columns; its jj_info then
  * reports block_width 0. infos (may be NULL) receives one jj_info per problem
  * (pairs_evaluated, pairs_rotated, kernel_launches, seconds and
- * last_max_offdiag are batch totals). A batch whose parallel step would hold
+ * last_max_offdiag are batch totals); on an error before the problems' own
+ * results exist (invalid arguments, a failed allocation or launch), every entry
+ * carries that status and zero counts. A batch whose parallel step would hold
  * more than 65535 block pairs is refused with JJ_INVALID_ARG (split it).
  * Returns the first non-OK problem status, else JJ_OK. jjacobi_extract does
  * not apply. */

@@ -129,16 +129,19 @@ namespace {
 
 __global__ void sweep_begin_kernel(int32_t *sweep) { *sweep += 1; }
 
-#define JJ_CUDA(call)                                                                   \
+// On a CUDA error: optional report, then `return ret` (JJ_CUDA: JJ_CUDA_ERROR;
+// entry points that fill a jj_info pass their own finishing expression)
+#define JJ_CUDA_RET(call, ret)                                                          \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \
         if (e_ != cudaSuccess) {                                                        \
             if (getenv("JJACOBI_DEBUG"))                                                \
                 fprintf(stderr, "jjacobi: %s failed: %s (%s:%d)\n", #call,             \
                         cudaGetErrorString(e_), __FILE__, __LINE__);                    \
-            return JJ_CUDA_ERROR;                                                       \
+            return ret;                                                                 \
         }                                                                               \
     } while (0)
+#define JJ_CUDA(call) JJ_CUDA_RET(call, JJ_CUDA_ERROR)
 
 template <typename T>
 cudaError_t dmalloc(T **p, size_t count) {
@@ -1309,11 +1312,17 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
     const int64_t ldw = plain ? c->ldp : c->P.ldw;
     int32_t *dperm = plain ? c->d_pperm : c->d_perm;
     if (order_after_legacy(c) != JJ_OK) return finish(JJ_CUDA_ERROR);
-    JJ_CUDA(cudaMemcpyAsync(dperm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    JJ_CUDA(cudaMemcpyAsync(plain ? c->d_pJw : c->d_Jw, Jw.data(), n, cudaMemcpyHostToDevice, st));
-    JJ_CUDA(cudaMemcpyAsync(c->d_Jorig, J, n, cudaMemcpyHostToDevice, st));
-    JJ_CUDA(launch_permute_columns(c->cplx, (const double *)G, ldg, W, ldw, c->m, n, dperm, false,
-                                   st));
+    JJ_CUDA_RET(cudaMemcpyAsync(dperm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                st),
+                finish(JJ_CUDA_ERROR));
+    JJ_CUDA_RET(cudaMemcpyAsync(plain ? c->d_pJw : c->d_Jw, Jw.data(), n, cudaMemcpyHostToDevice,
+                                st),
+                finish(JJ_CUDA_ERROR));
+    JJ_CUDA_RET(cudaMemcpyAsync(c->d_Jorig, J, n, cudaMemcpyHostToDevice, st),
+                finish(JJ_CUDA_ERROR));
+    JJ_CUDA_RET(launch_permute_columns(c->cplx, (const double *)G, ldg, W, ldw, c->m, n, dperm,
+                                       false, st),
+                finish(JJ_CUDA_ERROR));
     if (c->blocked && reset_skip_state(c) != JJ_OK) return finish(JJ_CUDA_ERROR);
     int launches = 1;
     int rc = JJ_NOT_CONVERGED;
@@ -1338,9 +1347,10 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
             break;
         }
     }
-    JJ_CUDA(launch_permute_columns(c->cplx, W, ldw, (double *)G, ldg, c->m, n, dperm, true, st));
+    JJ_CUDA_RET(launch_permute_columns(c->cplx, W, ldw, (double *)G, ldg, c->m, n, dperm, true, st),
+                finish(JJ_CUDA_ERROR));
     ++launches;
-    JJ_CUDA(cudaStreamSynchronize(st));
+    JJ_CUDA_RET(cudaStreamSynchronize(st), finish(JJ_CUDA_ERROR));
     inf.kernel_launches = launches;
     c->solved = (rc == JJ_OK || rc == JJ_NOT_CONVERGED);
     return finish(rc);
@@ -1385,50 +1395,69 @@ int jjacobi_extract(jj_handle c, double *lambda, void *U, int64_t ldu, int32_t s
 
 int jjacobi_solve_host(jj_handle c, const void *G_host, int64_t ldg, const int8_t *J,
                        double *lambda_host, void *U_host, int64_t ldu, jj_info *info) {
-    if (!c || !G_host || !J || !lambda_host || ldg < c->m || (U_host && ldu < c->m))
-        return JJ_INVALID_ARG;
     const auto t0 = std::chrono::steady_clock::now();
+    jj_info inf{};
+    auto finish = [&](int rc) {
+        inf.status = rc;
+        inf.seconds =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (info) *info = inf;
+        return rc;
+    };
+    if (!c || !G_host || !J || !lambda_host || ldg < c->m || (U_host && ldu < c->m))
+        return finish(JJ_INVALID_ARG);
     const size_t esz = (size_t)c->E * sizeof(double);
     const int64_t ldh = (c->m + 3) & ~int64_t(3);
     const size_t bytes = (size_t)ldh * c->n * esz;
-    if (!c->d_Ghost) JJ_CUDA(cudaMalloc(&c->d_Ghost, bytes));
-    if (U_host && !c->d_Uhost) JJ_CUDA(cudaMalloc(&c->d_Uhost, bytes));
+    if (!c->d_Ghost) JJ_CUDA_RET(cudaMalloc(&c->d_Ghost, bytes), finish(JJ_CUDA_ERROR));
+    if (U_host && !c->d_Uhost)
+        JJ_CUDA_RET(cudaMalloc(&c->d_Uhost, bytes), finish(JJ_CUDA_ERROR));
     cudaStream_t st = c->stream;
-    JJ_CUDA(cudaMemcpy2DAsync(c->d_Ghost, ldh * esz, G_host, ldg * esz, c->m * esz, c->n,
-                              cudaMemcpyHostToDevice, st));
-    jj_info inf{};
+    JJ_CUDA_RET(cudaMemcpy2DAsync(c->d_Ghost, ldh * esz, G_host, ldg * esz, c->m * esz, c->n,
+                                  cudaMemcpyHostToDevice, st),
+                finish(JJ_CUDA_ERROR));
     int rc = jjacobi_solve(c, c->d_Ghost, ldh, J, &inf);
     if (rc == JJ_OK || rc == JJ_NOT_CONVERGED) {
         const int rx = jjacobi_extract(c, c->d_lam, U_host ? c->d_Uhost : nullptr, ldh, 0);
         if (rx != JJ_OK) rc = rx;
     }
     if (rc == JJ_OK || rc == JJ_NOT_CONVERGED) {
-        JJ_CUDA(cudaMemcpyAsync(lambda_host, c->d_lam, c->n * sizeof(double),
-                                cudaMemcpyDeviceToHost, st));
+        JJ_CUDA_RET(cudaMemcpyAsync(lambda_host, c->d_lam, c->n * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st),
+                    finish(JJ_CUDA_ERROR));
         if (U_host)
-            JJ_CUDA(cudaMemcpy2DAsync(U_host, ldu * esz, c->d_Uhost, ldh * esz, c->m * esz,
-                                      c->n, cudaMemcpyDeviceToHost, st));
-        JJ_CUDA(cudaStreamSynchronize(st));
+            JJ_CUDA_RET(cudaMemcpy2DAsync(U_host, ldu * esz, c->d_Uhost, ldh * esz, c->m * esz,
+                                          c->n, cudaMemcpyDeviceToHost, st),
+                        finish(JJ_CUDA_ERROR));
+        JJ_CUDA_RET(cudaStreamSynchronize(st), finish(JJ_CUDA_ERROR));
     }
-    inf.status = rc;
-    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (info) *info = inf;
-    return rc;
+    return finish(rc);
 }
 
 int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int64_t *m,
                           const int64_t *n, const int64_t *ldg, const int8_t *const *J,
                           double *lambda_out, jj_info *infos) {
     const auto t0 = std::chrono::steady_clock::now();
-    if (!c || count < 1 || !G || !m || !n || !ldg || !J) return JJ_INVALID_ARG;
+    // an error before the per-problem results exist: every problem reports it
+    auto fail = [&](int r) {
+        if (infos)
+            for (int p = 0; p < count; ++p) {
+                infos[p] = jj_info{};
+                infos[p].status = r;
+                infos[p].seconds =
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            }
+        return r;
+    };
+    if (!c || count < 1 || !G || !m || !n || !ldg || !J) return fail(JJ_INVALID_ARG);
     int64_t ntot = 0;
     for (int p = 0; p < count; ++p) {
         if (!G[p] || !J[p] || n[p] < 1 || m[p] < n[p] || ldg[p] < m[p] || m[p] > c->m ||
             n[p] > c->n)
-            return JJ_INVALID_ARG;
+            return fail(JJ_INVALID_ARG);
         ntot += n[p];
     }
-    if (ntot > ((int64_t)1 << 31) - 1) return JJ_INVALID_ARG;
+    if (ntot > ((int64_t)1 << 31) - 1) return fail(JJ_INVALID_ARG);
     c->solved = false;  // jjacobi_extract refers to single solves
     // plan: reuse when the shapes repeat
     const Plan &P0 = c->P;
@@ -1438,11 +1467,11 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
     if (!same) {
         std::vector<int> bws(count);
         if (c->p.block_width == JJ_BLOCK_AUTO) {
-            if (order_after_legacy(c) != JJ_OK) return JJ_CUDA_ERROR;
+            if (order_after_legacy(c) != JJ_OK) return fail(JJ_CUDA_ERROR);
             const int r = batch_autotune(c, count, G, m, n, ldg, J, bws);
             if (r != JJ_OK) {
                 free_plan(c);
-                return r;
+                return fail(r);
             }
         } else {
             for (int p = 0; p < count; ++p) bws[p] = batch_block_width(c, n[p]);
@@ -1450,15 +1479,15 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
         const int r = build_plan(c, count, m, n, bws.data(), true);
         if (r != JJ_OK) {
             free_plan(c);
-            return r;
+            return fail(r);
         }
     }
     const Plan &P = c->P;
     cudaStream_t st = c->stream;
-    if (order_after_legacy(c) != JJ_OK) return JJ_CUDA_ERROR;
+    if (order_after_legacy(c) != JJ_OK) return fail(JJ_CUDA_ERROR);
     {
         const int r = batch_load(c, count, G, n, ldg, J);
-        if (r != JJ_OK) return r;
+        if (r != JJ_OK) return fail(r);
     }
     std::vector<jj_info> inf(count);
     std::vector<char> done(count, 0);
@@ -1474,7 +1503,7 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
     int64_t pairs_eval = 0, pairs_rot = 0;
     for (int sweep = 1; sweep <= c->max_sweeps && ndone < count; ++sweep) {
         const int r = run_sweep(c, false, &launches);
-        if (r != JJ_OK) return r;
+        if (r != JJ_OK) return fail(r);
         pairs_eval += (int64_t)c->h_cnt[kCntPairs];
         pairs_rot += (int64_t)c->h_cnt[kCntPairsRot];
         double mo;
@@ -1503,7 +1532,7 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
             if (inf[p].status == JJ_NOT_POSDEF) failed.push_back(p);
         if (!failed.empty()) {
             const int r = batch_plain_finish(c, failed, inf, &launches);
-            if (r != JJ_OK) return r;
+            if (r != JJ_OK) return fail(r);
         }
     }
     // scatter back, with the eigenvalues (lambda_out host or device)
@@ -1514,14 +1543,18 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
         if (cudaPointerGetAttributes(&at, lambda_out) == cudaSuccess)
             lam_dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
         cudaGetLastError();
-        if (!lam_dev && ensure_lam(c, P.ncols) != JJ_OK) return JJ_CUDA_ERROR;
+        if (!lam_dev && ensure_lam(c, P.ncols) != JJ_OK) return fail(JJ_CUDA_ERROR);
         lam = lam_dev ? lambda_out : c->d_lam;
     }
-    JJ_CUDA(launch_batch_scatter(c->cplx, c->Gw, P.ldw, c->d_bptr, c->d_bld, c->d_brows,
-                                 c->d_bcolprob, c->d_perm, c->d_blamoff, c->d_Jw, lam, P.ncols, st));
+    JJ_CUDA_RET(launch_batch_scatter(c->cplx, c->Gw, P.ldw, c->d_bptr, c->d_bld, c->d_brows,
+                                     c->d_bcolprob, c->d_perm, c->d_blamoff, c->d_Jw, lam, P.ncols,
+                                     st),
+                fail(JJ_CUDA_ERROR));
     if (lambda_out && !lam_dev)
-        JJ_CUDA(cudaMemcpyAsync(lambda_out, c->d_lam, P.ncols * sizeof(double), cudaMemcpyDeviceToHost, st));
-    JJ_CUDA(cudaStreamSynchronize(st));
+        JJ_CUDA_RET(cudaMemcpyAsync(lambda_out, c->d_lam, P.ncols * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st),
+                    fail(JJ_CUDA_ERROR));
+    JJ_CUDA_RET(cudaStreamSynchronize(st), fail(JJ_CUDA_ERROR));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int worst = rc;
     for (int p = 0; p < count; ++p) {

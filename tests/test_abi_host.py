@@ -96,6 +96,27 @@ def test_kernel_entry_points_validate_arguments(jj):
     assert lib.jjacobi_extract(None, None, None, 0, 0) == jj.JJ_INVALID_ARG
 
 
+def test_solve_entry_points_report_errors_through_info(jj):
+    """Every solve entry point fills its jj_info on an argument error (here a
+    null handle, rejected before any device work)."""
+    lib = jj.load()
+    info = jj.jj_info()
+    info.status = 12345
+    assert lib.jjacobi_solve(None, None, 1, None, ctypes.byref(info)) == jj.JJ_INVALID_ARG
+    assert info.status == jj.JJ_INVALID_ARG and info.seconds >= 0.0
+    info.status = 12345
+    assert lib.jjacobi_solve_host(None, None, 1, None, None, None, 0,
+                                  ctypes.byref(info)) == jj.JJ_INVALID_ARG
+    assert info.status == jj.JJ_INVALID_ARG
+    infos = (jj.jj_info * 3)()
+    for k in range(3):
+        infos[k].status = 12345
+        infos[k].sweeps = 7
+    rc = lib.jjacobi_solve_batched(None, 3, None, None, None, None, None, None, infos)
+    assert rc == jj.JJ_INVALID_ARG
+    assert all(infos[k].status == jj.JJ_INVALID_ARG and infos[k].sweeps == 0 for k in range(3))
+
+
 def test_product_does_not_import_oracle():
     """The product package (Python binding, CUDA sources, build script) never
     imports, loads or names the oracle: the two share no code."""
