@@ -127,6 +127,44 @@ def _ptr(x) -> Optional[int]:
     raise TypeError(type(x))
 
 
+def _avail_bytes(x) -> int:
+    """Bytes addressable from the first element of a tensor or array onward."""
+    if hasattr(x, "untyped_storage"):
+        return x.untyped_storage().nbytes() - x.storage_offset() * x.element_size()
+    if not x.flags["C_CONTIGUOUS"] and not x.flags["F_CONTIGUOUS"]:
+        raise ValueError("host arrays passed to the library must be contiguous")
+    return x.nbytes
+
+
+def _check_buffer(x, what: str, count: int, elem_bytes: int, device: bool,
+                  dtypes: Sequence[str] = ()) -> None:
+    """Argument checks the C entry points cannot make themselves: a tensor or
+    array must lie on the side the call reads it from, have the element type
+    and cover `count` elements. Raw integer addresses are passed unchecked."""
+    if x is None or isinstance(x, int):
+        return
+    is_cuda = bool(getattr(x, "is_cuda", False))
+    if device and not is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    name = str(x.dtype).replace("torch.", "")
+    if dtypes and name not in dtypes:
+        raise ValueError(f"{what} must have dtype {' or '.join(dtypes)}, not {name}")
+    if count > 0 and _avail_bytes(x) < count * elem_bytes:
+        raise ValueError(f"{what} holds fewer than the {count} elements the call reads")
+
+
+def _matrix_span(m: int, n: int, ld: int) -> int:
+    """Elements spanned by an m x n column-major matrix with leading dimension ld."""
+    return 0 if n < 1 else (n - 1) * ld + m
+
+
+def _signs(J, n: int, what: str = "J") -> np.ndarray:
+    Jc = np.ascontiguousarray(np.asarray(J, dtype=np.int8))
+    if Jc.ndim != 1 or Jc.shape[0] != n:
+        raise ValueError(f"{what} must hold exactly {n} signs, got shape {Jc.shape}")
+    return Jc
+
+
 def _stream_ptr(stream) -> Optional[int]:
     if stream is None:
         try:
@@ -204,8 +242,14 @@ class Handle:
     def __exit__(self, *a):
         self.close()
 
+    def _elem(self):
+        """(bytes, dtype names) of one matrix element of this handle."""
+        return (16, ("complex128",)) if self.dtype == JJ_C128 else (8, ("float64",))
+
     def jjacobi_solve(self, G, ldg: int, J: Sequence[int], allow=(JJ_OK,)) -> jj_info:
-        Jc = np.ascontiguousarray(np.asarray(J, dtype=np.int8))
+        esz, names = self._elem()
+        _check_buffer(G, "G", _matrix_span(self.m, self.n, int(ldg)), esz, True, names)
+        Jc = _signs(J, self.n)
         info = jj_info()
         rc = load().jjacobi_solve(self.h, _ptr(G), int(ldg), Jc.ctypes.data, ctypes.byref(info))
         _check(rc, "jjacobi_solve", allow)
@@ -221,6 +265,9 @@ class Handle:
         return {k: (float(t[i]), int(n[i])) for i, k in enumerate(names)}
 
     def jjacobi_extract(self, lam, U=None, ldu: int = 0, sort: int = 0) -> None:
+        esz, names = self._elem()
+        _check_buffer(lam, "lambda", self.n, 8, False, ("float64",))
+        _check_buffer(U, "U", _matrix_span(self.m, self.n, int(ldu)), esz, True, names)
         _check(load().jjacobi_extract(self.h, _ptr(lam), _ptr(U), int(ldu), int(sort)),
                "jjacobi_extract")
 
@@ -228,7 +275,10 @@ class Handle:
                            allow=(JJ_OK,)):
         """Host buffers in and out (column-major numpy array G)."""
         Gf = np.asfortranarray(G)
-        Jc = np.ascontiguousarray(np.asarray(J, dtype=np.int8))
+        if Gf.shape != (self.m, self.n):
+            raise ValueError(f"G must be {self.m} x {self.n}, got {Gf.shape}")
+        Gf = Gf.astype(np.complex128 if self.dtype == JJ_C128 else np.float64, copy=False)
+        Jc = _signs(J, self.n)
         lam = np.zeros(self.n, dtype=np.float64)
         U = np.zeros_like(Gf, order="F") if want_U else None
         info = jj_info()
@@ -249,7 +299,18 @@ class Handle:
         n = np.array([G.shape[1] for G in Gs], dtype=np.int64)
         ld = np.array([G.stride(1) if hasattr(G, "stride") else G.shape[0] for G in Gs],
                       dtype=np.int64)
-        Jcs = [np.ascontiguousarray(np.asarray(J, dtype=np.int8)) for J in Js]
+        if len(Js) != count:
+            raise ValueError(f"{count} matrices but {len(Js)} sign vectors")
+        esz, names = self._elem()
+        for k, G in enumerate(Gs):
+            if getattr(G, "ndim", 2) != 2:
+                raise ValueError(f"G[{k}] must be a matrix")
+            if hasattr(G, "stride") and G.shape[1] > 1 and G.stride(0) != 1:
+                raise ValueError(f"G[{k}] must be column-major (stride(0) == 1)")
+            _check_buffer(G, f"G[{k}]", _matrix_span(int(m[k]), int(n[k]), int(ld[k])), esz,
+                          True, names)
+        Jcs = [_signs(J, int(n[k]), f"J[{k}]") for k, J in enumerate(Js)]
+        _check_buffer(lam, "lambda", int(n.sum()), 8, False, ("float64",))
         jptrs = (ctypes.c_void_p * count)(*[J.ctypes.data for J in Jcs])
         infos = (jj_info * count)()
         rc = load().jjacobi_solve_batched(self.h, count, ptrs, m.ctypes.data, n.ctypes.data,

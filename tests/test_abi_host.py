@@ -176,3 +176,51 @@ def test_c_program_compiles_links_and_calls_the_abi(jj, tmp_path):
     assert int(out[2]) == int(ref[0, 0, 0]) * 100 + int(ref[0, 0, 1])
     assert out[3] == "JJ_NOT_POSDEF" and int(out[4]) == jj.JJ_INVALID_ARG
     assert out[5] == "1" and out[6] == "60"
+
+
+def _fake_handle(jj, m, n, dtype):
+    """A Handle object with a null jj_handle: enough to exercise the binding's
+    own argument checks, which run before any library call."""
+    h = jj.Handle.__new__(jj.Handle)
+    h.h = ctypes.c_void_p()
+    h.m, h.n, h.dtype = m, n, dtype
+    return h
+
+
+def test_binding_rejects_buffers_the_kernels_would_overrun(jj):
+    """Host tensors where device memory is read, wrong element types, short
+    buffers and sign vectors of the wrong length are refused in Python, before
+    a pointer reaches the library."""
+    import torch
+
+    h = _fake_handle(jj, 6, 4, jj.JJ_C128)
+    J = [1, 1, -1, -1]
+    G_host = torch.zeros((4, 6), dtype=torch.complex128).t()
+    with pytest.raises(ValueError, match="CUDA"):
+        h.jjacobi_solve(G_host, 6, J)
+    with pytest.raises(ValueError, match="CUDA"):
+        h.jjacobi_extract(np.zeros(4), G_host, 6)
+    with pytest.raises(ValueError, match="CUDA"):
+        h.jjacobi_solve_batched([G_host], [J])
+    with pytest.raises(ValueError, match="signs"):
+        h.jjacobi_solve_host(np.zeros((6, 4), complex), [1, -1])
+    with pytest.raises(ValueError, match="6 x 4"):
+        h.jjacobi_solve_host(np.zeros((4, 6), complex), [1, -1, 1, -1, 1, -1])
+    with pytest.raises(ValueError, match="fewer"):
+        h.jjacobi_extract(np.zeros(3), None)
+    with pytest.raises(ValueError, match="float64"):
+        h.jjacobi_extract(np.zeros(4, dtype=np.float32), None)
+    with pytest.raises(ValueError, match="sign vectors"):
+        h.jjacobi_solve_batched([G_host, G_host], [J])
+    # the checks themselves, on host tensors (device=False) where a call may read host memory
+    check = jj._check_buffer
+    check(torch.zeros(10, dtype=torch.float64), "x", 10, 8, False, ("float64",))
+    check(torch.zeros(12, dtype=torch.float64)[2:], "x", 10, 8, False, ("float64",))
+    with pytest.raises(ValueError, match="fewer"):
+        check(torch.zeros(12, dtype=torch.float64)[3:], "x", 10, 8, False, ("float64",))
+    with pytest.raises(ValueError, match="complex128"):
+        check(torch.zeros(10, dtype=torch.float64), "x", 5, 16, False, ("complex128",))
+    with pytest.raises(ValueError, match="contiguous"):
+        check(np.zeros((4, 4))[:, ::2], "x", 4, 8, False)
+    assert jj._matrix_span(6, 4, 8) == 3 * 8 + 6 and jj._matrix_span(6, 0, 8) == 0
+    check(12345, "raw address", 10 ** 9, 8, True)  # raw addresses are the caller's contract
