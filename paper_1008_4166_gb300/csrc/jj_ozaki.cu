@@ -84,8 +84,19 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
 }
 
-// Bounded wait on an mbarrier phase; false when the limit is reached.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase; false when the limit is reached. A failed
+// try_wait may itself suspend the thread for an unspecified time, so the bound
+// is wall-clock (2 s on the global nanosecond timer, far above any product or
+// copy of these kernels), with an iteration cap behind it.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    uint64_t t0 = 0;
     for (long i = 0; i < (1L << 28); ++i) {
         uint32_t ok;
         asm volatile(
@@ -95,6 +106,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        const uint64_t t = global_ns();
+        if (i == 0)
+            t0 = t;
+        else if (t - t0 > kWaitLimitNs)
+            return false;
     }
     return false;
 }
