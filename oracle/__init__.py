@@ -28,6 +28,10 @@ Contents
   cholesky_special, solve_blocked_special
                        the Cholesky factor of a pivot with diagonal diagonal
                        blocks (3.9)-(3.11), and 2F built on it (Sec. 3.3).
+  frontend             (module) H -> (G, J) by Bunch-Parlett factorization
+                       and block diagonalization (Sec. 2.2, (2.5)), the
+                       zero-eigenvalue completion by QR, and the whole method
+                       on a Hermitian H.
 
 Every function is pinned by tests/test_oracle_*.py against closed forms,
 invariants, constructions with known eigenvalues, LAPACK special cases and
