@@ -28,6 +28,9 @@ Contents
   cholesky_special, solve_blocked_special
                        the Cholesky factor of a pivot with diagonal diagonal
                        blocks (3.9)-(3.11), and 2F built on it (Sec. 3.3).
+  solve_plain_threads  the plain method in round-robin order on several host
+                       threads (jj_threads.c): the multithreaded CPU baseline,
+                       bit-equal to solve_plain in round-robin order.
   frontend             (module) H -> (G, J) by Bunch-Parlett factorization
                        and block diagonalization (Sec. 2.2, (2.5)), the
                        zero-eigenvalue completion by QR, and the whole method
@@ -63,16 +66,18 @@ STRATEGY_MODULUS = 1
 
 
 def build(outdir: Optional[str] = None, force: bool = False) -> str:
-    """Compile jj_oracle.c into a shared library with gcc (plain C11, -O2)."""
+    """Compile jj_oracle.c (the oracle) and jj_threads.c (the multithreaded CPU
+    baseline) into one shared library with gcc (plain C11, -O2, pthreads)."""
     outdir = outdir or _HERE
     out = os.path.join(outdir, _LIB_NAME)
-    src = os.path.join(_HERE, "jj_oracle.c")
+    srcs = [os.path.join(_HERE, f) for f in ("jj_oracle.c", "jj_threads.c")]
     body = os.path.join(_HERE, "jj_oracle_body.h")
     if (not force and os.path.exists(out)
-            and os.path.getmtime(out) >= max(os.path.getmtime(src), os.path.getmtime(body))):
+            and os.path.getmtime(out) >= max(os.path.getmtime(f) for f in srcs + [body])):
         return out
     tmp = out + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp]
+                          + srcs + ["-lm"])
     os.replace(tmp, out)
     return out
 
@@ -98,6 +103,9 @@ def _load():
         h.restype = ctypes.c_int
         h.argtypes = [R, R, R, R, ctypes.c_int, ctypes.c_int, vp]
     lib.jjo_long_double_mantissa_bits.restype = ctypes.c_int
+    lib.jjt_solve_rr.restype = ctypes.c_int
+    lib.jjt_solve_rr.argtypes = [ctypes.c_int, i64, i64, vp, i64, vp, ctypes.c_double,
+                                 ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -185,6 +193,29 @@ def solve_plain(G: np.ndarray, J: Sequence[int], tol: float = TOL_DEFAULT,
     lam, U = eigenpairs(Gw, Jc, precision=precision)
     return dict(Gt=Gw, lam=lam, U=U, W=W, sweeps=int(sweeps[0]), rotations=int(rots[0]),
                 status=int(st), maxoff=float(maxoff[0]))
+
+
+def solve_plain_threads(G: np.ndarray, J: Sequence[int], nthreads: int,
+                        tol: float = TOL_DEFAULT, max_sweeps: int = 60) -> Dict[str, object]:
+    """The plain method in round-robin order on nthreads host threads (the
+    multithreaded CPU baseline, jj_threads.c): the pairs of a parallel step are
+    disjoint, so it returns the bits of solve_plain(order=ORDER_ROUND_ROBIN)."""
+    lib = _load()
+    cplx = np.iscomplexobj(G)
+    Gw = _as_work(G, "f64")
+    m, n = Gw.shape
+    Jc = np.ascontiguousarray(np.asarray(J, dtype=np.int32))
+    tab = np.ascontiguousarray(column_rr_table(n).astype(np.int32))
+    sweeps = np.zeros(1, dtype=np.int32)
+    rots = np.zeros(1, dtype=np.int64)
+    maxoff = np.zeros(1, dtype=np.float64)
+    st = lib.jjt_solve_rr(int(cplx), m, n, _ptr(Gw), m, _ptr(Jc), tol, max_sweeps, _ptr(tab),
+                          int(tab.shape[0]), int(nthreads), _ptr(sweeps), _ptr(rots),
+                          _ptr(maxoff))
+    if st == 1:
+        raise ValueError("jjt_solve_rr: invalid argument or no resources")
+    return dict(Gt=Gw, sweeps=int(sweeps[0]), rotations=int(rots[0]), status=int(st),
+                maxoff=float(maxoff[0]))
 
 
 def eigenpairs(Gt: np.ndarray, J: Sequence[int], precision: Optional[str] = None

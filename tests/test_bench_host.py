@@ -1,6 +1,7 @@
 """Host-side logic of bench.py (no GPU): the algorithmic flop conventions, the
-traffic lookup keyed to kernel sources, the clock sampler's parsing, and the
-reference arm's JSON line (the oracle on a bounded sample)."""
+traffic lookup keyed to kernel sources, the clock sampler's parsing, the
+reference arm's JSON line (the oracle on a bounded sample) and the
+multithreaded CPU baseline's sampler."""
 import json
 import os
 import shutil
@@ -90,3 +91,13 @@ def test_reference_arm_line_matches_the_measured_arm_config():
 
     assert line["config"] == bench.bench_config(_A, _P)
     assert line["metric"] == bench.METRIC
+
+
+def test_threaded_cpu_baseline_sampler_grows_to_the_budget():
+    import synth
+
+    P = synth.make_workload("plain_c128_n128", precision="f64")
+    g, ncol, dt, nt = bench.cpu_baseline_threads(P, budget_s=0.01)
+    assert g > 0 and nt >= 1 and ncol == 64 and dt > 0  # the first sample already exceeds it
+    g, ncol, dt, nt = bench.cpu_baseline_threads(P, budget_s=1e9)
+    assert ncol == P.n  # grown to the whole input, then stopped
