@@ -37,6 +37,21 @@ def test_stored_oracle_eigenvalues_fit_the_input():
     assert abs(np.sum(lam) - tr) <= 1e-12 * scale
 
 
+def test_stored_values_come_from_the_oracle_alone():
+    """The script that wrote the stored values imports only the oracle, the
+    input generators and the standard library / numpy: no product code."""
+    import ast
+
+    src = os.path.join(os.path.dirname(GOLD), "make_graded_c128_n4096_oracle.py")
+    mods = set()
+    for node in ast.walk(ast.parse(open(src).read())):
+        if isinstance(node, ast.Import):
+            mods |= {a.name.split(".")[0] for a in node.names}
+        elif isinstance(node, ast.ImportFrom):
+            mods.add((node.module or "").split(".")[0])
+    assert mods <= {"os", "sys", "time", "numpy", "oracle", "synth"}, mods
+
+
 @pytest.mark.gpu
 def test_headline_eigenvalues_match_the_full_oracle_solve():
     from tests.gpu_util import require_gpu, to_dev
