@@ -77,6 +77,18 @@ def test_create_rejects_bad_params(jj):
     assert not h
     p = jj.jjacobi_default_params(10, 10, 7)
     assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(p)) == jj.JJ_INVALID_ARG
+    for m, n in ((0, 0), (5, 0), (-1, -1), (4, 5)):  # empty, negative, wide
+        p = jj.jjacobi_default_params(m, n, jj.JJ_F64)
+        assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(p)) == jj.JJ_INVALID_ARG
+        assert not h
+    for field, bad in (("order", 2), ("gemm", 4), ("gemm", -1), ("block_strategy", 2),
+                       ("inner_block_width", -1), ("ozaki_slices", -1)):
+        q = jj.jjacobi_default_params(8, 8, jj.JJ_F64)
+        setattr(q, field, bad)
+        assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(q)) == jj.JJ_INVALID_ARG, field
+    q = jj.jjacobi_default_params(8, (1 << 30) + 1, jj.JJ_F64)
+    q.m = q.n
+    assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(q)) == jj.JJ_INVALID_ARG
     assert lib.jjacobi_create(None, ctypes.byref(p)) == jj.JJ_INVALID_ARG
     lib.jjacobi_destroy(None)  # no-op
 
