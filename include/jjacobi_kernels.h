@@ -45,7 +45,12 @@ int jjk_plain_step(int32_t dtype, void *G, int64_t ld, int64_t m, int64_t n,
                    double tol, unsigned long long *counters, void *stream);
 
 /* Gram of every pivot pair (K-b, (3.6)): A_p = [G_i G_j]^* [G_i G_j], written as
- * the full Hermitian k x k block (both triangles). gemm: jj_gemm. */
+ * the full Hermitian k x k block (both triangles). gemm (jj_gemm) selects the
+ * Gram's form as the solver does: FP64 for JJ_GEMM_FP64; digit products for
+ * JJ_GEMM_OZAKI_FP16 and JJ_GEMM_OZAKI_GRAM (JJ_INVALID_ARG when the pivot
+ * width exceeds what they take: real width 2 kmax (complex) or kmax (real)
+ * above 64); JJ_GEMM_AUTO: digit products where they apply, else FP64. Other
+ * values: JJ_INVALID_ARG. */
 int jjk_gram(int32_t dtype, int32_t gemm, const void *G, int64_t ld, int64_t m,
              const int32_t *pairs, int32_t npairs, double *A, int32_t kmax, void *stream);
 
@@ -63,7 +68,9 @@ int jjk_inner(int32_t dtype, double *A, double *W, int32_t kmax, const int32_t *
 /* Block update (K-c, (2.9)): [Gd_i Gd_j] = [Gs_i Gs_j] W_p for every pair
  * (both use ld and the pair's column offsets). Gd may equal Gs (in place: each
  * block reads every row it writes before writing it); otherwise the two must
- * not overlap. */
+ * not overlap. gemm: digit products for JJ_GEMM_OZAKI_FP16 (the all-digit
+ * form), FP64 for JJ_GEMM_FP64, JJ_GEMM_OZAKI_GRAM and JJ_GEMM_AUTO (as in the
+ * solver); other values: JJ_INVALID_ARG. */
 int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld,
                int64_t m, const int32_t *pairs, int32_t npairs, const double *W,
                int32_t kmax, void *stream);

@@ -1594,12 +1594,19 @@ int jjk_plain_step(int32_t dtype, void *G, int64_t ld, int64_t m, int64_t n,
 
 int jjk_gram(int32_t dtype, int32_t gemm, const void *G, int64_t ld, int64_t m,
              const int32_t *pairs, int32_t npairs, double *A, int32_t kmax, void *stream) {
-    if (!dt_ok(dtype) || !G || !pairs || !A || ld < m || m < 1 || kmax < 1 || npairs < 0)
+    if (!dt_ok(dtype) || !G || !pairs || !A || ld < m || m < 1 || kmax < 1 || npairs < 0 ||
+        gemm < JJ_GEMM_FP64 || gemm > JJ_GEMM_AUTO)
         return JJ_INVALID_ARG;
     const bool cplx = dtype == JJ_C128;
     cudaStream_t st = (cudaStream_t)stream;
-    if (gemm == JJ_GEMM_OZAKI_FP16) {
-        if (!ozaki_supported(cplx, kmax)) return JJ_INVALID_ARG;
+    // the Gram's form in each solver mode: digit products unless FP64; AUTO
+    // takes them where the pivot width allows, FP64 otherwise
+    bool digits = gemm != JJ_GEMM_FP64;
+    if (digits && !ozaki_supported(cplx, kmax)) {
+        if (gemm != JJ_GEMM_AUTO) return JJ_INVALID_ARG;
+        digits = false;
+    }
+    if (digits) {
         // Scratch from the stream-ordered allocator: column exponents of every
         // column the pairs touch and the int128 accumulators.
         int64_t ncols = 0;
@@ -1615,7 +1622,11 @@ int jjk_gram(int32_t dtype, int32_t gemm, const void *G, int64_t ld, int64_t m,
         int32_t *cexp = nullptr;
         unsigned long long *acc = nullptr;
         JJ_CUDA(cudaMallocAsync((void **)&cexp, std::max<int64_t>(ncols, 1) * sizeof(int32_t), st));
-        JJ_CUDA(cudaMallocAsync((void **)&acc, ozaki_gram_workspace_bytes(npairs, kmax, cplx), st));
+        if (cudaMallocAsync((void **)&acc, ozaki_gram_workspace_bytes(npairs, kmax, cplx), st) !=
+            cudaSuccess) {
+            cudaFreeAsync(cexp, st);
+            return JJ_CUDA_ERROR;
+        }
         cudaError_t e = launch_colexp(cplx, (const double *)G, ld, m, ncols, cexp, st);
         if (e == cudaSuccess)
             e = launch_gram_ozaki(cplx, (const double *)G, ld, m, pairs, npairs, A, kmax, cexp, acc,
@@ -1643,9 +1654,12 @@ int jjk_inner(int32_t dtype, double *A, double *W, int32_t kmax, const int32_t *
 int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld, int64_t m,
                const int32_t *pairs, int32_t npairs, const double *W, int32_t kmax,
                void *stream) {
-    if (!dt_ok(dtype) || !Gs || !Gd || !pairs || !W || ld < m || m < 1 || kmax < 1 || npairs < 0)
+    if (!dt_ok(dtype) || !Gs || !Gd || !pairs || !W || ld < m || m < 1 || kmax < 1 ||
+        npairs < 0 || gemm < JJ_GEMM_FP64 || gemm > JJ_GEMM_AUTO)
         return JJ_INVALID_ARG;
     const bool cplx = dtype == JJ_C128;
+    // the update runs on digit products only in the all-digit form; the
+    // hybrid and AUTO forms keep it in FP64, as the solver does
     if (gemm == JJ_GEMM_OZAKI_FP16) {
         if (!ozaki_supported(cplx, kmax)) return JJ_INVALID_ARG;
         cudaStream_t st = (cudaStream_t)stream;
