@@ -1585,7 +1585,8 @@ int jjk_column_norms(int32_t dtype, const void *G, int64_t ld, int64_t m, int64_
 int jjk_plain_step(int32_t dtype, void *G, int64_t ld, int64_t m, int64_t n,
                    const int32_t *pairs, int32_t npairs, const int8_t *J, double *d, double tol,
                    unsigned long long *counters, void *stream) {
-    if (!dt_ok(dtype) || !G || !pairs || !J || !d || !counters || ld < m || m < 1 || npairs < 0)
+    if (!dt_ok(dtype) || !G || !pairs || !J || !d || !counters || ld < m || m < 1 || n < 0 ||
+        npairs < 0)
         return JJ_INVALID_ARG;
     JJ_CUDA(launch_plain_step(dtype == JJ_C128, (double *)G, ld, m, n, pairs, npairs, J, d,
                               tol > 0 ? tol : kDefaultTol, counters, (cudaStream_t)stream));
@@ -1643,7 +1644,8 @@ int jjk_gram(int32_t dtype, int32_t gemm, const void *G, int64_t ld, int64_t m,
 int jjk_inner(int32_t dtype, double *A, double *W, int32_t kmax, const int32_t *pairs,
               int32_t npairs, const int8_t *J, double tol, int32_t inner_max_sweeps,
               int32_t inner_block_width, unsigned long long *counters, void *stream) {
-    if (!dt_ok(dtype) || !A || !W || !pairs || !J || !counters || kmax < 1 || npairs < 0)
+    if (!dt_ok(dtype) || !A || !W || !pairs || !J || !counters || kmax < 1 || npairs < 0 ||
+        inner_block_width < 0)
         return JJ_INVALID_ARG;
     JJ_CUDA(launch_inner(dtype == JJ_C128, A, W, kmax, pairs, npairs, J,
                          tol > 0 ? tol : kDefaultTol, inner_max_sweeps > 0 ? inner_max_sweeps : 30,
@@ -1690,7 +1692,7 @@ int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld
 
 int jjk_extract(int32_t dtype, const void *G, int64_t ld, int64_t m, int64_t n, const int8_t *J,
                 double *lambda, void *U, int64_t ldu, void *stream) {
-    if (!dt_ok(dtype) || !G || !J || !lambda || ld < m || m < 1 || (U && ldu < m))
+    if (!dt_ok(dtype) || !G || !J || !lambda || ld < m || m < 1 || n < 0 || (U && ldu < m))
         return JJ_INVALID_ARG;
     JJ_CUDA(launch_extract(dtype == JJ_C128, (const double *)G, ld, m, n, J, nullptr, lambda,
                            (double *)U, ldu, (cudaStream_t)stream));

@@ -115,6 +115,12 @@ def test_kernel_entry_points_validate_arguments(jj):
         assert lib.jjk_update(0, g, x, x, 1, 1, x, 0, x, 1, None) == jj.JJ_INVALID_ARG
     for g in (jj.JJ_GEMM_OZAKI_FP16, jj.JJ_GEMM_OZAKI_GRAM):
         assert lib.jjk_gram(jj.JJ_C128, g, x, 1, 1, x, 0, x, 40, None) == jj.JJ_INVALID_ARG
+    # negative sizes
+    assert lib.jjk_plain_step(0, x, 1, 1, -1, x, 0, x, x, 0.0, x, None) == jj.JJ_INVALID_ARG
+    assert lib.jjk_plain_step(0, x, 1, 1, 1, x, -1, x, x, 0.0, x, None) == jj.JJ_INVALID_ARG
+    assert lib.jjk_inner(0, x, x, 8, x, 0, x, 0.0, 30, -1, x, None) == jj.JJ_INVALID_ARG
+    assert lib.jjk_extract(0, x, 1, 1, -1, x, x, None, 0, None) == jj.JJ_INVALID_ARG
+    assert lib.jjk_column_norms(0, x, 1, 1, -1, x, None) == jj.JJ_INVALID_ARG
 
 
 def test_solve_entry_points_report_errors_through_info(jj):
