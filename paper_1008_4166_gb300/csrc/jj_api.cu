@@ -8,6 +8,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "jj_common.cuh"
 
 using namespace jj;
@@ -126,6 +128,15 @@ struct jj_ctx {
 };
 
 namespace {
+
+// NVTX range for profilers (solve, sweep, extraction); header-only NVTX is a
+// no-op unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 __global__ void sweep_begin_kernel(int32_t *sweep) { *sweep += 1; }
 
@@ -1274,6 +1285,7 @@ void jjacobi_destroy(jj_handle h) {
 }
 
 int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *info) {
+    NvtxRange range("jjacobi_solve");
     const auto t0 = std::chrono::steady_clock::now();
     jj_info inf{};
     auto finish = [&](int rc) {
@@ -1327,6 +1339,7 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
     int launches = 1;
     int rc = JJ_NOT_CONVERGED;
     for (int sweep = 1; sweep <= c->max_sweeps; ++sweep) {
+        NvtxRange sweep_range("jj sweep");
         const int r = run_sweep(c, plain, &launches);
         if (r != JJ_OK) return finish(r);
         inf.sweeps = sweep;
@@ -1357,6 +1370,7 @@ int jjacobi_solve(jj_handle c, void *G, int64_t ldg, const int8_t *J, jj_info *i
 }
 
 int jjacobi_extract(jj_handle c, double *lambda, void *U, int64_t ldu, int32_t sort) {
+    NvtxRange range("jjacobi_extract");
     if (!c) return JJ_INVALID_ARG;
     if (!c->solved) return JJ_NOT_SOLVED;
     if (!lambda || (U && ldu < c->m)) return JJ_INVALID_ARG;
@@ -1437,6 +1451,7 @@ int jjacobi_solve_host(jj_handle c, const void *G_host, int64_t ldg, const int8_
 int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int64_t *m,
                           const int64_t *n, const int64_t *ldg, const int8_t *const *J,
                           double *lambda_out, jj_info *infos) {
+    NvtxRange range("jjacobi_solve_batched");
     const auto t0 = std::chrono::steady_clock::now();
     // an error before the per-problem results exist: every problem reports it
     auto fail = [&](int r) {
@@ -1502,6 +1517,7 @@ int jjacobi_solve_batched(jj_handle c, int32_t count, void *const *G, const int6
     int rc = JJ_OK;
     int64_t pairs_eval = 0, pairs_rot = 0;
     for (int sweep = 1; sweep <= c->max_sweeps && ndone < count; ++sweep) {
+        NvtxRange sweep_range("jj sweep");
         const int r = run_sweep(c, false, &launches);
         if (r != JJ_OK) return fail(r);
         pairs_eval += (int64_t)c->h_cnt[kCntPairs];
