@@ -220,3 +220,18 @@ def test_mutation_duplicated_column_write_breaks_eigenvalues():
     res = oracle.solve_plain(P.G, P.J, mutation=3, max_sweeps=10)
     bad = res["status"] != 0 or max_rel_err(res["lam"], P.lam_exact) > 1e-6
     assert bad
+
+
+@pytest.mark.parametrize("order", [oracle.ORDER_ROW_CYCLIC, oracle.ORDER_ROUND_ROBIN])
+def test_state_between_sweeps_is_g_alone(order):
+    """Alg. 3.2 recomputes the diagonal at the start of every sweep, so the
+    state between sweeps is the current G~ alone: a solve capped after k sweeps
+    and resumed from its G~ gives the bits of the uninterrupted solve. (This is
+    what makes a capped solve a checkpoint.)"""
+    P = synth.make_workload("plain_c128_n128", n=40)
+    full = oracle.solve_plain(P.G, P.J, order=order)
+    part = oracle.solve_plain(P.G, P.J, order=order, max_sweeps=3)
+    assert part["status"] == 2 and full["sweeps"] > 3
+    rest = oracle.solve_plain(part["Gt"], P.J, order=order)
+    assert rest["status"] == 0 and part["sweeps"] + rest["sweeps"] == full["sweeps"]
+    assert np.array_equal(rest["Gt"], full["Gt"])
