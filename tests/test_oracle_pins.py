@@ -235,3 +235,29 @@ def test_state_between_sweeps_is_g_alone(order):
     rest = oracle.solve_plain(part["Gt"], P.J, order=order)
     assert rest["status"] == 0 and part["sweeps"] + rest["sweeps"] == full["sweeps"]
     assert np.array_equal(rest["Gt"], full["Gt"])
+
+
+@pytest.mark.parametrize("hyp", [1, -1])
+def test_rotation_across_column_scales(hyp):
+    """Columns of very different lengths (the graded inputs' situation, here
+    up to 1e120 apart): the rotation stays finite and J-unitary, and the
+    rotated pair is orthogonal relative to its own column lengths. The method
+    works with squared norms, so the range is the one where products of two
+    squared column norms stay in FP64 (norms within about 1e+-75)."""
+    rng = np.random.default_rng(21 + hyp)
+    Jp = np.diag([1.0, float(hyp)])
+    for e1 in (-60, -30, -5, 0, 5, 30, 60):
+        for e2 in (-60, -8, 0, 8, 60):
+            G = _rand_pair(rng, 6, True)
+            G[:, 0] *= 10.0 ** e1
+            G[:, 1] *= 10.0 ** e2
+            A = G.conj().T @ G
+            par = oracle.rotation(A[0, 0].real, A[1, 1].real, A[0, 1], hyp)
+            assert par is not None
+            W = _rotation_matrix(par, hyp)
+            assert np.all(np.isfinite(W))
+            assert np.abs(W.conj().T @ Jp @ W - Jp).max() <= 8 * U64 * np.abs(W).max() ** 2
+            Gt = G @ W
+            n0, n1 = np.linalg.norm(Gt[:, 0]), np.linalg.norm(Gt[:, 1])
+            assert abs(np.vdot(Gt[:, 0], Gt[:, 1])) <= 64 * U64 * np.abs(W).max() ** 2 * max(
+                n0 * n1, abs(A[0, 1]))
