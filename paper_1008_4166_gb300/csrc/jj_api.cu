@@ -1,5 +1,8 @@
 // Host driver and C ABI of libjjacobi: handle life cycle, workspaces, the
-// sweep loop (one CUDA graph per sweep), convergence test, extraction.
+// sweep loop of Alg. 5.2 (parallel steps of the orderings of Sec. 4, one CUDA
+// graph per sweep; the three-level forms launched directly), the convergence
+// test (a sweep that applies no rotation, Sec. 5.3), extraction (the end of
+// Alg. 5.2), the batched solve and the building-block entry points.
 #include <algorithm>
 #include <chrono>
 #include <map>

@@ -1,5 +1,7 @@
-// Three-level form (Sec. 5.1, case 3F): the inner J-Jacobi of every outer
-// pivot pair is itself the blocked method (Alg. 3.3 on R). Outer pair q owns
+// Three-level forms (Sec. 5.1-5.2, cases 3F and 3B): the inner J-Jacobi of
+// every outer pivot pair is itself the blocked method (Alg. 3.3 on R; for 3B
+// one block-oriented pass, over every inner block pair in the first outer step
+// of a sweep and over the cross pairs of Alg. 5.1 in the others). Outer pair q owns
 // the slice X_q = [R_q; W_q] of an inner work matrix (columns
 // [q kmax, q kmax + k_q), leading dimension ldx >= 2 kmax): R_q (rows
 // [0, kmax)) is the Cholesky factor of the outer Gram block (3.8) and W_q
