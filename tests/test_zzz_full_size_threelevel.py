@@ -1,7 +1,7 @@
 """The three-level forms at the published full size, in the launch
-configuration bench.py times for the real workload of order 16384 (outer
-pivots of 256 columns, inner blocks of 16, digit Gram with FP64 update, one
-capped sweep).
+configuration bench.py timed for the real workload of order 16384 (outer
+pivots of 256 columns with FP64 contractions, inner blocks of 16 with digit
+products: --gemm ozaki, one capped sweep).
 
 The workload's own recipe takes minutes to generate on the host (a Haar QR of
 a 16384 x 16384 matrix), so this test takes a Gaussian G of the same shape and
@@ -30,7 +30,7 @@ def test_three_level_one_sweep_at_full_size_is_j_unitary(strategy):
     Gd = to_dev(G)
     strat = jj.JJ_BLOCK_ORIENTED if strategy == "oriented" else jj.JJ_FULL_BLOCK
     with jj.Handle(N, N, jj.JJ_F64, block_width=128, inner_block_width=16,
-                   gemm=jj.JJ_GEMM_OZAKI_GRAM, block_strategy=strat, max_sweeps=1) as h:
+                   gemm=jj.JJ_GEMM_OZAKI_FP16, block_strategy=strat, max_sweeps=1) as h:
         info = h.jjacobi_solve(Gd, Gd.stride(1), J, allow=(jj.JJ_OK, jj.JJ_NOT_CONVERGED)).as_dict()
     assert info["status"] == jj.JJ_NOT_CONVERGED and info["sweeps"] == 1
     assert info["nbl"] == 128 and info["rotations"] > 0
