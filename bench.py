@@ -280,11 +280,13 @@ def kernel_roofline(jj, P, times, info, gemm_gram_digits, gemm_upd_digits, peaks
             work = info["pairs_rotated"] * m * k * k * mac
             bound, peak, unit, name = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "update_fp64_kernel"
     achieved = work / (ms * 1e-3) / 1e12
+    if bound == "tensor":
+        src = ("measured bf16 burst of MEASURED_PEAKS.json (fp16 has the same dense rate)"
+               if "bf16_tflops" in peaks else "fallback bf16 burst figure, 1.9 PFLOP/s (no measured peaks)")
+    else:
+        src = "FP64: 152 SMs x 2 FMA/clk/SM x 2 flops x 2070 MHz (derived; 1.19 measured)"
     roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak,
-            "peak_source": ("measured bf16 burst of MEASURED_PEAKS.json (fp16 has the same dense rate)"
-                            if bound == "tensor" else
-                            "FP64: 152 SMs x 2 FMA/clk/SM x 2 flops x 2070 MHz (derived; 1.19 measured)"),
+            "frac": achieved / peak, "peak_source": src,
             "ms_per_launch": ms / max(launches, 1), "launches": launches,
             "family_ms": {f: fam[f][0] for f in fam}}
     return roof

@@ -101,3 +101,44 @@ def test_threaded_cpu_baseline_sampler_grows_to_the_budget():
     assert g > 0 and nt >= 1 and ncol == 64 and dt > 0  # the first sample already exceeds it
     g, ncol, dt, nt = bench.cpu_baseline_threads(P, budget_s=1e9)
     assert ncol == P.n  # grown to the whole input, then stopped
+
+
+def test_measured_arm_line_carries_every_contract_key():
+    """The JSON line of the default run (run_ours) is built from one dict
+    literal; it names every key the benchmark contract asks for. (Checked on the
+    source: the run itself needs a GPU.)"""
+    import ast
+
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    fn = next(n for n in tree.body if isinstance(n, ast.FunctionDef) and n.name == "run_ours")
+    keys = set()
+    for node in ast.walk(fn):
+        if (isinstance(node, ast.Assign) and any(getattr(t, "id", None) == "line"
+                                                 for t in node.targets)
+                and isinstance(node.value, ast.Dict)):
+            keys |= {k.value for k in node.value.keys if isinstance(k, ast.Constant)}
+    required = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches"}
+    assert required <= keys, required - keys
+
+
+def test_kernel_roofline_picks_the_dominant_family_and_its_peak():
+    class _P:
+        is_complex = True
+        m = n = 4096
+
+    info = {"nbl": 256, "pairs_evaluated": 1000, "pairs_rotated": 800, "rotations": 5000}
+    times = {"gram": (10.0, 5), "inner": (2.0, 5), "update": (50.0, 5)}
+    r = bench.kernel_roofline(None, _P, times, info, True, False, {"bf16_tflops": 1919.0})
+    k = 2.0 * 4096 / 256
+    assert r["kernel"] == "update_fp64_kernel" and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(800 * 4096 * k * k * 8.0 / 50e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"]) and r["unit"] == "TFLOP/s"
+    assert r["ms_per_launch"] == pytest.approx(10.0)
+    times = {"gram": (60.0, 5), "inner": (2.0, 5), "update": (50.0, 5)}
+    r = bench.kernel_roofline(None, _P, times, info, True, False, {"bf16_tflops": 1919.0})
+    assert r["kernel"] == "gram_ozaki_kernel" and r["bound"] == "tensor" and r["peak"] == 1919.0
+    assert "measured" in r["peak_source"]
+    r = bench.kernel_roofline(None, _P, times, info, True, False, {})
+    assert r["peak"] == 1900.0 and "fallback" in r["peak_source"]
