@@ -159,6 +159,22 @@ def cpu_baseline(P, budget_s: float = 15.0):
     return best
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), with the architecture."""
+    import platform
+
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return f"{name or 'unknown model'} ({platform.machine()})"
+
+
 def cpu_baseline_threads(P, budget_s: float = 10.0):
     """The multithreaded CPU baseline on a bounded sample: one round-robin sweep
     of the plain method on all host cores (oracle.solve_plain_threads), on the
@@ -209,6 +225,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": bench_config(args, P, world),
         "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "cpu": cpu_model(),
                          "sample": f"one row-cyclic plain sweep on the leading {vals[0][1]} "
                                    f"columns (all {P.m} rows) of the n={P.n} input"},
         "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -416,11 +433,11 @@ def run_ours(args):
     cpu = cpu_threads = None
     if rank == 0 and world == 1 and not args.no_cpu:
         g, ncol, dt = cpu_baseline(P, budget_s=15.0)
-        cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "cpu": cpu_model(),
                "sample": f"one row-cyclic plain sweep on the leading {ncol} columns (all {m} rows) "
                          f"of the n={n} input, {dt:.1f} s"}
         g, ncol, dt, nt = cpu_baseline_threads(P, budget_s=10.0)
-        cpu_threads = {"value": g, "unit": "GFLOP/s", "cores": nt,
+        cpu_threads = {"value": g, "unit": "GFLOP/s", "cores": nt, "cpu": cpu_model(),
                        "kind": "round-robin plain method on all host cores (pthreads)",
                        "sample": f"one round-robin plain sweep on the leading {ncol} columns "
                                  f"(all {m} rows) of the n={n} input, {dt:.1f} s"}
