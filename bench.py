@@ -30,6 +30,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -115,18 +116,31 @@ class ClockSampler:
 
 
 def blocked_flops(n: int, m: int, cplx: bool, info: dict) -> float:
-    """Algorithmic FP64-equivalent flops of one blocked solve.
+    """FP64-equivalent flops of the work one blocked solve executed.
 
-    Per pair and step: Gram k(k+1)/2 * m MACs (Hermitian half), update m k^2 MACs;
-    per applied inner rotation 5 k MACs (dot, R and W column pairs). A complex MAC
-    is 8 real flops, a real MAC 2."""
+    The Gram's Hermitian half, k(k+1)/2 * m MACs, for every pair whose Gram and
+    inner solve ran (pairs_evaluated: the solver skips pairs unchanged since
+    they were last found diagonal); the update's m k^2 MACs for every pair whose
+    inner solve applied a rotation (pairs_rotated: the others are left as they
+    are); 5 k MACs per applied inner rotation (dot, R and W column pairs). A
+    complex MAC is 8 real flops, a real MAC 2."""
+    mac = 8.0 if cplx else 2.0
+    k = 2.0 * n / info["nbl"]
+    gram = info["pairs_evaluated"] * k * (k + 1) / 2 * m
+    update = info["pairs_rotated"] * m * k * k
+    inner = info["rotations"] * 5.0 * k
+    return mac * (gram + update + inner)
+
+
+def blocked_flops_all_pairs(n: int, m: int, cplx: bool, info: dict) -> float:
+    """The same conventions charged for every pair of every step of every sweep
+    (as if no pair were skipped): context for comparisons with implementations
+    that always recompute."""
     mac = 8.0 if cplx else 2.0
     nbl = info["nbl"]
     k = 2.0 * n / nbl
     pair_steps = info["sweeps"] * info["steps_per_sweep"] * (nbl // 2)
-    gemm = pair_steps * (k * (k + 1) / 2 * m + m * k * k)
-    inner = info["rotations"] * 5.0 * k
-    return mac * (gemm + inner)
+    return mac * (pair_steps * (k * (k + 1) / 2 * m + m * k * k) + info["rotations"] * 5.0 * k)
 
 
 def plain_flops(n: int, m: int, cplx: bool, sweeps: int) -> float:
@@ -199,8 +213,11 @@ def cpu_baseline_threads(P, budget_s: float = 10.0):
 
 def bench_config(args, P, world: int = 1) -> dict:
     """The workload and launch configuration both arms report."""
-    return {"workload": args.workload, "m": P.m, "n": P.n, "block_width": args.block_width,
-            "gemm": args.gemm, "strategy": args.strategy, "order": "round_robin",
+    name = re.sub(r"_b\d+$", f"_b{args.block_width}", args.workload)
+    return {"workload": name, "recipe": args.workload, "m": P.m, "n": P.n,
+            "block_width": args.block_width, "gemm": args.gemm,
+            "update_digits": (args.digits or 12) if args.gemm == "ozaki" else None,
+            "strategy": args.strategy, "order": "round_robin",
             "l2": "inputs larger than L2 (G = 256 MiB; every step reads and writes it)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -276,6 +293,7 @@ def kernel_roofline(jj, P, times, info, gemm_gram_digits, gemm_upd_digits, peaks
     m = P.m
     k = 2.0 * P.n / info["nbl"]
     K2 = 2 * k if cplx else k
+    upd_digits = info.get("update_digits", 12)
     fam = {f: times[f] for f in ("gram", "inner", "update")}
     dom = max(fam, key=lambda f: fam[f][0])
     ms, launches = fam[dom]
@@ -291,8 +309,9 @@ def kernel_roofline(jj, P, times, info, gemm_gram_digits, gemm_upd_digits, peaks
         bound, peak, unit, name = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "inner_smem_kernel"
     else:
         if gemm_upd_digits:
-            work = info["pairs_rotated"] * update_products(8) * 2.0 * m * K2 * K2
-            bound, peak, unit, name = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", "update_ozaki_kernel"
+            # the kernel contracts all 64 real-form positions of a pivot
+            work = info["pairs_rotated"] * update_products(upd_digits) * 2.0 * m * 64 * 64
+            bound, peak, unit, name = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", "update_digits_kernel"
         else:
             work = info["pairs_rotated"] * m * k * k * mac
             bound, peak, unit, name = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "update_fp64_kernel"
@@ -342,7 +361,7 @@ def run_ours(args):
         lam = torch.empty(n, dtype=torch.float64, device="cuda")
     strat = {"full": jj.JJ_FULL_BLOCK, "oriented": jj.JJ_BLOCK_ORIENTED}[args.strategy]
     h = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
-                  block_strategy=strat, max_sweeps=args.max_sweeps)
+                  block_strategy=strat, max_sweeps=args.max_sweeps, ozaki_slices=args.digits)
     ok = (jj.JJ_OK, jj.JJ_NOT_CONVERGED) if args.max_sweeps else (jj.JJ_OK,)
 
     def step():
@@ -377,6 +396,7 @@ def run_ours(args):
     info = infos[-1]
     flops = blocked_flops(n, m, cplx, info)
     value = flops * world / (ms * 1e-3) / 1e9
+    flops_all = blocked_flops_all_pairs(n, m, cplx, info)
     launches = sum(x["kernel_launches"] + 1 for x in infos)  # + extraction kernel
     lam_blocked = lam.cpu().numpy().copy()
 
@@ -395,14 +415,16 @@ def run_ours(args):
     # around every kernel family of every step, on the solve's stream) and the
     # dominant kernel's roofline
     hp_ = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
-                    profile=True, max_sweeps=args.profile_sweeps, block_strategy=strat)
+                    profile=True, max_sweeps=args.profile_sweeps, block_strategy=strat,
+                    ozaki_slices=args.digits)
     with torch.cuda.stream(stream):
         Gw.copy_(G0)
         pinfo_ = hp_.jjacobi_solve(Gw, Gw.stride(1), P.J, allow=(jj.JJ_OK, jj.JJ_NOT_CONVERGED))
     stream.synchronize()
     times = hp_.jjacobi_kernel_times()
     hp_.close()
-    roof = kernel_roofline(jj, P, times, pinfo_.as_dict(), g_gram == jj.JJ_GEMM_OZAKI_FP16,
+    roof = kernel_roofline(jj, P, times, dict(pinfo_.as_dict(), update_digits=args.digits or 12),
+                           g_gram == jj.JJ_GEMM_OZAKI_FP16,
                            g_upd == jj.JJ_GEMM_OZAKI_FP16, _peaks())
     # DRAM bytes per launch from the ncu capture of the same kernel (one step of
     # this workload; per launch, like `achieved`), null once the kernel changed
@@ -449,7 +471,11 @@ def run_ours(args):
             "data": "synthetic",
             "config": dict(bench_config(args, P, world), sweeps=info["sweeps"],
                            steps_per_sweep=info["steps_per_sweep"], time_to_solution_s=ms / 1e3,
-                           max_sweeps=args.max_sweeps or None),
+                           max_sweeps=args.max_sweeps or None,
+                           flops="executed work: Gram per evaluated pair, update per rotated pair",
+                           pairs_evaluated=info["pairs_evaluated"],
+                           pairs_rotated=info["pairs_rotated"],
+                           gflops_if_every_pair_were_recomputed=flops_all * world / (ms * 1e-3) / 1e9),
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks, "plain": plain, "cpu_baseline_threads": cpu_threads,
         }
@@ -553,7 +579,9 @@ def run_batched(args):
     stream.synchronize()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    flops = sum(blocked_flops(P.n, P.m, True, i.as_dict()) for P, i in zip(probs, infos)
+    # per-problem pair counters of a batch are batch totals: every pair of every
+    # step of each problem's sweeps is charged here
+    flops = sum(blocked_flops_all_pairs(P.n, P.m, True, i.as_dict()) for P, i in zip(probs, infos)
                 if i.nbl > 0)
     sweeps = [i.sweeps for i in infos]
     line = {
@@ -673,7 +701,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-width", type=int, default=16)
-    ap.add_argument("--gemm", default="hybrid", choices=["hybrid", "ozaki", "fp64"])
+    ap.add_argument("--gemm", default="ozaki", choices=["hybrid", "ozaki", "fp64"])
+    ap.add_argument("--digits", type=int, default=0,
+                    help="digits per operand of the split-precision update (0: 12)")
     ap.add_argument("--strategy", default="oriented", choices=["oriented", "full"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-plain", dest="plain", action="store_false")

@@ -59,11 +59,12 @@ typedef enum { JJ_ORDER_ROUND_ROBIN = 0, JJ_ORDER_MODULUS = 1 } jj_order;
  * update (2.9)):
  *   JJ_GEMM_FP64        both on the FP64 pipe;
  *   JJ_GEMM_OZAKI_FP16  both as sums of exact fp16 digit products on the
- *                       tensor cores (tcgen05), recombined in integers;
- *   JJ_GEMM_OZAKI_GRAM  the Gram as digit products, the update in FP64: the
- *                       digit update carries a shared exponent along each row,
- *                       which loses relative accuracy on entries far below
- *                       their row's largest (strongly graded inputs);
+ *                       tensor cores (tcgen05), recombined in integers; the
+ *                       update carries one exponent per row and per column,
+ *                       and with its default 12 digits (84 bits) per operand
+ *                       its error stays within FP64's per-entry bound on
+ *                       strongly graded inputs;
+ *   JJ_GEMM_OZAKI_GRAM  the Gram as digit products, the update in FP64;
  *   JJ_GEMM_AUTO        JJ_GEMM_OZAKI_GRAM when the pivot fits the digit
  *                       kernels (real pivot width <= 64), else FP64. */
 typedef enum {
@@ -114,7 +115,8 @@ typedef struct {
     int32_t inner_block_width; /* 0: two-level; >0: inner block width (three-level) */
     int32_t order;             /* jj_order (blocked form; the plain form is round-robin) */
     int32_t gemm;              /* jj_gemm */
-    int32_t ozaki_slices;      /* digits of the split-precision update, 0: 8 (at most 512/N) */
+    int32_t ozaki_slices;      /* 7-bit digits per operand of the split-precision update,
+                                  1..12, 0: 12 */
     double tol;                /* <= 0: 128 * 2^-53; rotate when |a_rs| > tol sqrt(a_rr a_ss) */
     int32_t max_sweeps;        /* <= 0: 60 */
     int32_t inner_max_sweeps;  /* <= 0: 30 (inner J-Jacobi on R, blocked form) */
@@ -217,6 +219,18 @@ const char *jjacobi_status_string(int status);
  * [2] update (2.9), [3] plain pair steps, [4] column norms, [5..7] reserved.
  * launches (host, 8 int64, may be NULL): the matching launch counts. */
 int jjacobi_kernel_times(jj_handle h, double *times_ms, int64_t *launches);
+
+/* Bound, in nanoseconds of wall-clock time, of every device-side wait in this
+ * handle's tensor-core kernels (an mbarrier wait for a product, a copy or a
+ * pipeline stage; the kernels' failure path for a barrier nothing arrives at).
+ * A wait that runs out makes its kernel set an error flag, wait (again
+ * bounded) for its own products in flight, free its tensor memory and return;
+ * the solve then returns JJ_DEVICE_TIMEOUT and the handle stays usable. ns <= 0
+ * restores the default of 2 s, far above any wait of a healthy run. A bound of
+ * 1 ns makes every wait that does not succeed at its first poll expire: a
+ * way to exercise the failure path without a fault. Not a passage of the
+ * paper: a property of this implementation. */
+int jjacobi_set_wait_limit(jj_handle h, int64_t ns);
 
 /* Library version (JJACOBI_VERSION). */
 int32_t jjacobi_version(void);

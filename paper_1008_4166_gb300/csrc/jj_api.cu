@@ -93,7 +93,10 @@ struct jj_ctx {
     int32_t *d_mod = nullptr, *d_clean = nullptr, *d_flags = nullptr, *d_sweep = nullptr;
     uint8_t *d_wdig = nullptr;          // W-side digits of the digit update (per pair)
     int32_t *d_wdexp = nullptr;
-    int oz_slices_gram = 8, oz_slices_update = 8;
+    int oz_slices_gram = 8, oz_slices_update = 12;
+    long long *d_udscr = nullptr;       // scratch of the digit update (per persistent block)
+    int ud_nctas = 0;
+    unsigned long long wait_ns = 2000000000ull;  // bound of device-side waits
     int32_t *d_cexp = nullptr;          // column exponents (Ozaki Gram)
     unsigned long long *d_ozacc = nullptr;  // int128 Gram accumulators
     unsigned long long *d_prob_rot = nullptr, *h_prob_rot = nullptr;  // [2 count]
@@ -162,10 +165,12 @@ cudaError_t dmalloc(T **p, size_t count) {
     return cudaMalloc((void **)p, count ? count * sizeof(T) : 1);
 }
 
+// A wait that ran out leaves its kernel's outputs incomplete, and later kernels
+// of the sweep may then meet NaN or a failed Cholesky: the timeout is the cause.
 int status_from_flags(unsigned long long err) {
+    if (err & kErrTimeout) return JJ_DEVICE_TIMEOUT;
     if (err & kErrNonfinite) return JJ_NONFINITE;
     if (err & kErrNotPosdef) return JJ_NOT_POSDEF;
-    if (err & kErrTimeout) return JJ_DEVICE_TIMEOUT;
     return JJ_OK;
 }
 
@@ -173,6 +178,15 @@ template <typename T>
 void dfree(T *&p) {
     if (p) cudaFree((void *)p);
     p = nullptr;
+}
+
+// Scratch of the digit update: one row block per persistent block (kept while
+// the plan lives; shared by the outer and inner levels, which run in turn).
+cudaError_t alloc_ud_scratch(jj_ctx *c) {
+    if (c->d_udscr) return cudaSuccess;
+    c->ud_nctas = ud_num_ctas();
+    if (c->ud_nctas < 1) return cudaErrorInvalidDevice;
+    return cudaMalloc((void **)&c->d_udscr, ud_scratch_bytes(c->ud_nctas));
 }
 
 void free_plan(jj_ctx *c) {
@@ -188,6 +202,7 @@ void free_plan(jj_ctx *c) {
     dfree(c->d_ozacc);
     dfree(c->d_wdig);
     dfree(c->d_wdexp);
+    dfree(c->d_udscr);
     dfree(c->d_mod);
     dfree(c->d_clean);
     dfree(c->d_flags);
@@ -384,8 +399,9 @@ int build_three(jj_ctx *c, const std::vector<int32_t> &tab) {
         JJ_CUDA(dmalloc(&T.d_cexp2, xcols));
         JJ_CUDA(cudaMalloc((void **)&T.d_ozacc, ozaki_gram_workspace_bytes((int)npi, T.kmax_in, c->cplx)));
         if (T.ozaki_update) {
-            JJ_CUDA(dmalloc(&T.d_wdig, npi * 16 * kUpdSliceBytes));
+            JJ_CUDA(dmalloc(&T.d_wdig, npi * kUdMaxSlices * kUpdSliceBytes));
             JJ_CUDA(dmalloc(&T.d_wdexp, npi * 64));
+            JJ_CUDA(alloc_ud_scratch(c));
         }
     }
     return JJ_OK;
@@ -486,7 +502,7 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
     c->ozaki_update = c->ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
     c->oz_slices_update = ozaki_default_slices(false);
     if (c->ozaki && c->p.ozaki_slices > 0) {
-        if (c->p.ozaki_slices > ozaki_max_update_slices(c->cplx, P.kmax)) return JJ_INVALID_ARG;
+        if (c->p.ozaki_slices > kUdMaxSlices) return JJ_INVALID_ARG;
         c->oz_slices_update = c->p.ozaki_slices;
     }
     // device buffers
@@ -503,8 +519,9 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
     JJ_CUDA(dmalloc(&c->d_touched, 2 * np));
     if (c->ozaki) {
         if (c->ozaki_update) {
-            JJ_CUDA(dmalloc(&c->d_wdig, np * 16 * kUpdSliceBytes));
+            JJ_CUDA(dmalloc(&c->d_wdig, np * kUdMaxSlices * kUpdSliceBytes));
             JJ_CUDA(dmalloc(&c->d_wdexp, np * 64));
+            JJ_CUDA(alloc_ud_scratch(c));
         }
         JJ_CUDA(dmalloc(&c->d_cexp, (size_t)P.ncols));
         JJ_CUDA(cudaMalloc((void **)&c->d_ozacc, ozaki_gram_workspace_bytes((int)np, P.kmax, c->cplx)));
@@ -602,6 +619,7 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
             ctl.steps = P.steps;
             ctl.npairs = np;
             ctl.slot_base = s0;
+            ctl.wait_ns = c->wait_ns;
             if (c->d_rows) ctl.rows = c->d_rows + s0;
             if (c->d_prob) {
                 ctl.prob = c->d_prob + s0;
@@ -635,9 +653,9 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
                                  ud, pass));
             if (mark(2)) return JJ_CUDA_ERROR;
             if (c->ozaki_update)
-                JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw, c->Gw, P.ldw, mrows, pr, np, c->Wblk,
-                                            P.kmax, c->d_cexp, c->oz_slices_update, c->d_cnt, st,
-                                            ctl, ud));
+                JJ_CUDA(launch_update_digits(c->cplx, c->Gw, c->Gw, P.ldw, mrows, pr, np, P.kmax,
+                                             c->d_cexp, ud, c->d_udscr, c->ud_nctas, c->d_cnt, st,
+                                             ctl));
             else
                 JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw, c->Gw, P.ldw, mrows, pr, np,
                                       c->Wblk, P.kmax, st, ctl));
@@ -692,6 +710,7 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
         ctl.steps = P.steps;
         ctl.npairs = np;
         ctl.slot_base = s0;
+        ctl.wait_ns = c->wait_ns;
         if (mark(0)) return JJ_CUDA_ERROR;
         if (c->ozaki) {
             JJ_CUDA(launch_colexp_pairs(c->cplx, c->Gw, P.ldw, c->m, pr, np, P.kmax, c->d_cexp, st, ctl));
@@ -739,6 +758,7 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
                 ic.slot_base = T.slot0[t][ti];
                 ic.prob = T.d_prob + sl;
                 ic.prob_rot = T.d_rot;
+                ic.wait_ns = c->wait_ns;
                 if (!T.ozaki_update) ic.touched = T.d_touched;
                 UpdDigits ud;
                 if (T.ozaki) {
@@ -754,7 +774,7 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
                         ud.img = T.d_wdig;
                         ud.wexp = T.d_wdexp;
                         ud.cexp = T.d_cexp2;
-                        ud.slices = ozaki_default_slices(false);
+                        ud.slices = c->oz_slices_update;
                     }
                 } else {
                     JJ_CUDA(launch_gram(c->cplx, c->p.gemm, T.X, T.ldx, P.kmax, ip, ni, T.Ain, T.kmax_in, st, ic));
@@ -764,9 +784,9 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
                 JJ_CUDA(launch_inner(c->cplx, T.Ain, T.Win, T.kmax_in, ip, ni, T.d_JX, c->tol,
                                      c->inner_max_sweeps, 0, T.d_cnt, st, ic, ud, ipass));
                 if (T.ozaki_update)
-                    JJ_CUDA(launch_update_ozaki(c->cplx, T.X, T.X, T.ldx, 2 * P.kmax, ip, ni, T.Win,
-                                                T.kmax_in, T.d_cexp2, ozaki_default_slices(false),
-                                                T.d_cnt, st, ic, ud));
+                    JJ_CUDA(launch_update_digits(c->cplx, T.X, T.X, T.ldx, 2 * P.kmax, ip, ni,
+                                                 T.kmax_in, T.d_cexp2, ud, c->d_udscr, c->ud_nctas,
+                                                 T.d_cnt, st, ic));
                 else
                     JJ_CUDA(launch_update(c->cplx, c->p.gemm, T.X, T.X, T.ldx, 2 * P.kmax, ip, ni,
                                           T.Win, T.kmax_in, st, ic));
@@ -785,9 +805,18 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
                                     c->d_cnt, st, ctl));
         ++L;
         if (mark(2)) return JJ_CUDA_ERROR;
-        if (c->ozaki_update)
-            JJ_CUDA(launch_update_ozaki(c->cplx, c->Gw, c->Gw, P.ldw, c->m, pr, np, c->Wblk, P.kmax,
-                                        c->d_cexp, c->oz_slices_update, c->d_cnt, st, ctl, UpdDigits()));
+        if (c->ozaki_update) {
+            // the outer pivots' W-side digits, then the update
+            UpdDigits oud;
+            oud.img = c->d_wdig;
+            oud.wexp = c->d_wdexp;
+            oud.cexp = c->d_cexp;
+            oud.slices = c->oz_slices_update;
+            JJ_CUDA(launch_wimage(c->cplx, c->Wblk, P.kmax, pr, np, c->d_cexp, oud, st, ctl));
+            JJ_CUDA(launch_update_digits(c->cplx, c->Gw, c->Gw, P.ldw, c->m, pr, np, P.kmax,
+                                         c->d_cexp, oud, c->d_udscr, c->ud_nctas, c->d_cnt, st, ctl));
+            L += 1;
+        }
         else
             JJ_CUDA(launch_update(c->cplx, c->p.gemm, c->Gw, c->Gw, P.ldw, c->m, pr, np, c->Wblk,
                                   P.kmax, st, ctl));
@@ -1199,6 +1228,18 @@ int jjacobi_kernel_times(jj_handle c, double *times_ms, int64_t *launches) {
     for (int i = 0; i < 8; ++i) {
         times_ms[i] = c->prof_ms[i];
         if (launches) launches[i] = c->prof_n[i];
+    }
+    return JJ_OK;
+}
+
+int jjacobi_set_wait_limit(jj_handle c, int64_t ns) {
+    if (!c) return JJ_INVALID_ARG;
+    const unsigned long long v = ns > 0 ? (unsigned long long)ns : 2000000000ull;
+    if (v != c->wait_ns) {
+        c->wait_ns = v;
+        // captured sweeps carry the old bound in their kernel parameters
+        if (c->graph) cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
     }
     return JJ_OK;
 }
@@ -1694,13 +1735,30 @@ int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld
                 ncols = std::max<int64_t>(ncols, std::max(hp[4 * q] + hp[4 * q + 1],
                                                           hp[4 * q + 2] + hp[4 * q + 3]));
         }
+        // Scratch from the stream-ordered allocator: column exponents, the W-side
+        // digits of every pair, and the update's row blocks.
+        const int nctas = ud_num_ctas();
+        if (nctas < 1) return JJ_CUDA_ERROR;
+        UpdDigits ud;
+        ud.slices = kUdMaxSlices;
         int32_t *cexp = nullptr;
-        JJ_CUDA(cudaMallocAsync((void **)&cexp, std::max<int64_t>(ncols, 1) * sizeof(int32_t), st));
-        cudaError_t e = launch_colexp(cplx, (const double *)Gs, ld, m, ncols, cexp, st);
+        long long *scr = nullptr;
+        cudaError_t e = cudaMallocAsync((void **)&cexp, std::max<int64_t>(ncols, 1) * sizeof(int32_t), st);
         if (e == cudaSuccess)
-            e = launch_update_ozaki(cplx, (const double *)Gs, (double *)Gd, ld, m, pairs, npairs, W,
-                                    kmax, cexp, ozaki_default_slices(false), nullptr, st);
-        cudaFreeAsync(cexp, st);
+            e = cudaMallocAsync((void **)&ud.img, (size_t)std::max(npairs, 1) * ud.slices * kUpdSliceBytes, st);
+        if (e == cudaSuccess)
+            e = cudaMallocAsync((void **)&ud.wexp, (size_t)std::max(npairs, 1) * 64 * sizeof(int32_t), st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&scr, ud_scratch_bytes(nctas), st);
+        ud.cexp = cexp;
+        if (e == cudaSuccess) e = launch_colexp(cplx, (const double *)Gs, ld, m, ncols, cexp, st);
+        if (e == cudaSuccess) e = launch_wimage(cplx, W, kmax, pairs, npairs, cexp, ud, st);
+        if (e == cudaSuccess)
+            e = launch_update_digits(cplx, (const double *)Gs, (double *)Gd, ld, m, pairs, npairs,
+                                     kmax, cexp, ud, scr, nctas, nullptr, st);
+        if (cexp) cudaFreeAsync(cexp, st);
+        if (ud.img) cudaFreeAsync(ud.img, st);
+        if (ud.wexp) cudaFreeAsync(ud.wexp, st);
+        if (scr) cudaFreeAsync(scr, st);
         JJ_CUDA(e);
         return JJ_OK;
     }

@@ -7,6 +7,7 @@
 // Per-pair blocks (A_P, R, W_P) are kmax x kmax column-major at
 // pair * kmax * kmax elements (complex: interleaved).
 #include "jj_common.cuh"
+#include "jj_digits.cuh"
 
 namespace jj {
 namespace {
@@ -656,58 +657,20 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         __syncthreads();
         if (rot == 0) break;
     }
-    // Operand of the digit-product update: digits of D (W2 - I), W2 the real form
-    // [[Wr, Wi], [-Wi, Wr]] of W, D the column exponents of the pivot columns.
+    // Operand of the digit-product update: the digits of D (W2 - I), W2 the real
+    // form of W on the update's positions, D the column exponents of the pivot
+    // columns (jj_digits.cuh).
     if (ud.img && total_rot > 0) {
-        __shared__ int s_xexp[64], s_wexp[64];
-        const int K2 = CPLX ? 2 * k : k;
-        auto w2m = [&](int a, int j) -> double {  // (W2 - I)_aj from the smem W
-            double v;
-            if (CPLX) {
-                const int ar = a < k ? a : a - k, jr = j < k ? j : j - k;
-                const double re = W[((size_t)jr * ldr + ar) * 2], im = W[((size_t)jr * ldr + ar) * 2 + 1];
-                v = a < k ? (j < k ? re : im) : (j < k ? -im : re);
-            } else {
-                v = W[(size_t)j * ldr + a];
-            }
-            return a == j ? v - 1.0 : v;
-        };
-        for (int a = tid; a < 64; a += ST) {
-            int e = -1021;
-            if (a < K2) {
-                const int c = CPLX ? (a < k ? a : a - k) : a;
-                e = ud.cexp[pivot_col(pd, c)];
-            }
-            s_xexp[a] = e;
+        __shared__ int s_xexp[kUdPositions], s_wexp[kUdPositions];
+        for (int a = tid; a < kUdPositions; a += ST) {
+            const int c = CPLX ? (a & 31) : a;
+            s_xexp[a] = c < k ? ud.cexp[pivot_col(pd, c)] : -1021;
         }
         __syncthreads();
-        for (int j = warp; j < 64; j += SW) {
-            int mx = -100000;
-            if (j < K2)
-                for (int a = lane; a < K2; a += 32) {
-                    const unsigned long long mb = dg_mag_bits(w2m(a, j));
-                    if (mb) mx = max(mx, dg_exp_of_bits(mb) + s_xexp[a]);
-                }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane == 0) s_wexp[j] = mx == -100000 ? -1021 : mx;
-        }
-        __syncthreads();
-        uint8_t *img = ud.img + (size_t)blockIdx.x * ud.slices * kUpdSliceBytes;
-        for (int it = tid; it < 64 * 32; it += ST) {  // (row j, K positions a, a+1)
-            const int j = it / 32, a = (it % 32) * 2;
-            double x0 = 0.0, x1 = 0.0;
-            if (j < K2 && a < K2) x0 = w2m(a, j);
-            if (j < K2 && a + 1 < K2) x1 = w2m(a + 1, j);
-            const unsigned long long q0 = dg_fixed63(x0, s_wexp[j] - s_xexp[a]);
-            const unsigned long long q1 = dg_fixed63(x1, s_wexp[j] - s_xexp[a + 1]);
-            const bool n0 = __double_as_longlong(x0) < 0, n1 = __double_as_longlong(x1) < 0;
-            const uint32_t off = dg_sw128_off(j, a * 2);
-            for (int t = 1; t <= ud.slices; ++t)
-                *reinterpret_cast<uint32_t *>(img + (size_t)(t - 1) * kUpdSliceBytes + off) =
-                    dg_digits2_bits(q0, n0, q1, n1, t);
-        }
-        for (int j = tid; j < 64; j += ST) ud.wexp[(size_t)blockIdx.x * 64 + j] = s_wexp[j];
+        auto wacc = [&](int rr, int cc, int part) -> double { return W[((size_t)cc * ldr + rr) * E + part]; };
+        ud_wimage_build<CPLX>(wacc, k, s_xexp, s_wexp, ud.slices,
+                              ud.img + (size_t)blockIdx.x * ud.slices * kUpdSliceBytes,
+                              ud.wexp + (size_t)blockIdx.x * kUdPositions, tid, ST);
     }
     // write back R~ and W
     for (int t = tid; t < k * k; t += ST) {

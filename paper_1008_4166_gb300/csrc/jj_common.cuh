@@ -119,15 +119,18 @@ struct StepCtl {
     // [npairs][2]: bit c set when the inner solve rotated column c of the pair
     // (columns never rotated keep W's column e_c, so the update can skip them)
     unsigned long long *touched = nullptr;
+    // bound of every device-side wait of the step's kernels (nanoseconds)
+    unsigned long long wait_ns = 2000000000ull;
 };
 constexpr int kPairSkipped = 1;
 constexpr int kPairIdentity = 2;
 
 // Operand of the split-precision update produced by the inner solve: the fp16
 // digits of D (W2 - I) as shared-memory images (SWIZZLE_128B, K-major: 64 rows
-// of 128 bytes per digit, row j = output column j, K position a = row of W2),
-// and their column exponents. D holds the column exponents of the pivot
-// columns (cexp). Used only when the update runs as digit products.
+// of 128 bytes per digit, row j = output position j, K position a = row of
+// W2, on the real-form positions of jj_digits.cuh), and their column
+// exponents. D holds the column exponents of the pivot columns (cexp). Used
+// only when the update runs as digit products.
 struct UpdDigits {
     uint8_t *img = nullptr;        // [npairs][slices][64 * 128]
     int32_t *wexp = nullptr;       // [npairs][64]
@@ -135,6 +138,7 @@ struct UpdDigits {
     int slices = 0;
 };
 constexpr int kUpdSliceBytes = 64 * 128;
+constexpr int kUdMaxSlices = 12;  // digits per operand of the update (84 bits)
 
 // Decide (Gram kernels) whether pair q of this step can be skipped: the slot was
 // found clean at step `clean` and neither block changed after it.
@@ -210,7 +214,6 @@ bool inner_single_pass_supported(bool cplx, int kmax);
 
 // Split-precision (fp16 digit) forms on the tensor cores (jj_ozaki.cu).
 int ozaki_default_slices(bool gram);
-int ozaki_max_update_slices(bool cplx, int kmax);
 bool ozaki_supported(bool cplx, int kmax);
 size_t ozaki_gram_workspace_bytes(int npairs, int kmax, bool cplx);
 cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int64_t n,
@@ -224,11 +227,20 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
                               const int32_t *cexp, unsigned long long *acc, int slices,
                               unsigned long long *counters, cudaStream_t st,
                               StepCtl ctl = StepCtl());
-// cexp: column exponents of Gs (launch_colexp), used for the two-sided scaling.
-cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
-                                const int32_t *pairs, int npairs, const double *W, int kmax,
-                                const int32_t *cexp, int slices, unsigned long long *counters,
-                                cudaStream_t st, StepCtl ctl = StepCtl(), UpdDigits ud = UpdDigits());
+// Split-precision block update (jj_update_digits.cu): ud.img / ud.wexp hold the
+// W-side digits of every active pair (built by the inner solve, or by
+// launch_wimage), cexp the column exponents of Gs, scratch
+// ud_scratch_bytes(nctas) bytes; nctas persistent blocks (ud_num_ctas()).
+cudaError_t launch_update_digits(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
+                                 const int32_t *pairs, int npairs, int kmax, const int32_t *cexp,
+                                 const UpdDigits &ud, long long *scratch, int nctas,
+                                 unsigned long long *counters, cudaStream_t st,
+                                 StepCtl ctl = StepCtl());
+cudaError_t launch_wimage(bool cplx, const double *W, int kmax, const int32_t *pairs, int npairs,
+                          const int32_t *cexp, const UpdDigits &ud, cudaStream_t st,
+                          StepCtl ctl = StepCtl());
+size_t ud_scratch_bytes(int nctas);
+int ud_num_ctas();
 // Digit helpers shared by the inner solve (W-side digits) and the digit kernels.
 __device__ __forceinline__ unsigned long long dg_mag_bits(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;

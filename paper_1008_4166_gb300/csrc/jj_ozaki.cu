@@ -30,121 +30,16 @@
 // threads (the digits are computed, not copied), then fenced to the async
 // proxy before the single issuing thread launches tcgen05.mma.
 #include "jj_common.cuh"
+#include "jj_tc.cuh"
 
 namespace jj {
 
 constexpr int kBeta = 7;          // bits per digit
-constexpr int kOzMaxSlices = 9;   // 63 bits
 constexpr int kOzMaxK2 = 64;      // real width 2k (complex) or k (real) handled here
-constexpr int kOzUpdMaxSlices = 16;  // update digits (exact group sums need s * K2 * 127^2 < 2^24)
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t su32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);  // start address
-    d |= (uint64_t)1 << 16;                  // leading byte offset (unused, swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: 8-row groups
-    d |= (uint64_t)1 << 46;                  // descriptor version
-    d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
-    return d;
-}
-
-__device__ __forceinline__ uint32_t sw128_off(int row, int kbyte) {
-    return (uint32_t)(row * 128 + ((((kbyte >> 4) ^ (row & 7))) << 4) + (kbyte & 15));
-}
-
-// fp16 x fp16 -> fp32, K-major A and B, dense.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                        uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait on an mbarrier phase; false when the limit is reached. A failed
-// try_wait may itself suspend the thread for an unspecified time, so the bound
-// is wall-clock (2 s on the global nanosecond timer, far above any product or
-// copy of these kernels), with an iteration cap behind it.
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    uint64_t t0 = 0;
-    for (long i = 0; i < (1L << 28); ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        const uint64_t t = global_ns();
-        if (i == 0)
-            t0 = t;
-        else if (t - t0 > kWaitLimitNs)
-            return false;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst_smem),
-                 "r"(ncols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols));
-}
-
-// 32 lanes x 8 consecutive 32-bit columns (one lane per thread of the warp).
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
+using namespace tc;
 
 // ---------------------------------------------------------------------------
 // Digits
@@ -174,31 +69,6 @@ __device__ __forceinline__ unsigned long long fixed63(double x, int e) {
     if (sh >= 0) return mant << sh;
     if (sh <= -64) return 0ull;
     return mant >> (-sh);
-}
-
-// v * 2^e as a double, built from the integer's bits (normalize, round to
-// nearest even, assemble exponent and significand): integer ALU work only. Out
-// of the normal range (never for these workloads) it defers to ldexp.
-__device__ __forceinline__ double int_scaled_to_double(long long v, int e) {
-    if (v == 0) return 0.0;
-    const bool neg = v < 0;
-    const unsigned long long u = neg ? (unsigned long long)(-v) : (unsigned long long)v;
-    int lz = __clzll((long long)u);
-    const unsigned long long mm = u << lz;       // leading one at bit 63
-    unsigned long long mant = mm >> 11;          // 53 bits
-    const unsigned long long low = mm & 0x7FFull;
-    if (low > 0x400ull || (low == 0x400ull && (mant & 1ull))) {
-        ++mant;
-        if (mant == (1ull << 53)) {
-            mant >>= 1;
-            --lz;
-        }
-    }
-    const int biased = 63 + e - lz + 1023;
-    if (biased < 1 || biased > 2046) return ldexp((double)v, e);
-    const unsigned long long bits = ((unsigned long long)neg << 63) |
-                                    ((unsigned long long)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -350,12 +220,17 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
 
     // One thread polls the mbarrier; the others wait in the block barrier that
     // follows (spinning threads would take issue slots from the digit builders).
-    auto wait_buf = [&](int b) {
+    // A wait that runs out leaves the buffer pending, so that the teardown
+    // still waits for its products before the TMEM is freed.
+    auto wait_buf = [&](int b, uint64_t limit) {
         if (!pending[b]) return;
-        if (tid == 0 && !mbar_wait(su32(&bar_mma[b]), ph[b])) s_abort = 1;
-        __syncthreads();
-        ph[b] ^= 1u;
-        pending[b] = false;
+        const int ok = __syncthreads_and(tid != 0 || mbar_wait(su32(&bar_mma[b]), ph[b], limit));
+        if (ok) {
+            ph[b] ^= 1u;
+            pending[b] = false;
+        } else {
+            s_abort = 1;
+        }
     };
     // digits of rows [row0 + 64 i, +64) of the K2 real columns into buffer b,
     // by warps 1..15 (warp 0 issues the tensor-core products meanwhile);
@@ -443,13 +318,13 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         }
         pending[b] = true;
         if (i + 1 < nsc) {
-            wait_buf(b ^ 1);  // the products that read the other buffer are done
+            wait_buf(b ^ 1, ctl.wait_ns);  // the products that read the other buffer are done
             if (warp != 0) build(i + 1, b ^ 1);
             fence_async_smem();
         }
         if ((i & 1) == 1 || i == nsc - 1) {
-            wait_buf(b ^ 1);
-            wait_buf(b);
+            wait_buf(b ^ 1, ctl.wait_ns);
+            wait_buf(b, ctl.wait_ns);
             tc_fence_after();
             if (!s_abort) {
                 // two groups (32 columns of this thread) per TMEM round trip
@@ -487,9 +362,10 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         tc_fence_after();
     }
     if (s_abort) {
-        // give in-flight products a bounded chance to finish before freeing TMEM
-        wait_buf(0);
-        wait_buf(1);
+        // in-flight products finish before the TMEM is freed (the default bound:
+        // the products still complete after a shorter wait ran out)
+        wait_buf(0, kWaitLimitNs);
+        wait_buf(1, kWaitLimitNs);
         if (tid == 0 && counters) atomicOr(&counters[kCntErr], kErrTimeout);
     } else if (owns) {
         // add the partial sums: acc_out[pair][col b][row a] = {lo, hi}
@@ -571,304 +447,6 @@ __global__ void __launch_bounds__(256) gram_fixed_to_double_kernel(
     }
 }
 
-// ---------------------------------------------------------------------------
-// Update: one block per (128-row tile, pair), in correction form
-//     Y = X W2 = X + X (W2 - I),
-// so that only the correction goes through digits: its error scales with
-// ||W2 - I|| and not with the largest entry of each row of X, and the identity
-// part is the exact FP64 entry of X. (W2 - I is exact for the diagonal entries
-// near 1 by Sterbenz's lemma.) Two-sided power-of-two scaling keeps every
-// digit relative to a scale close to its own size:
-// X = [Xr Xi] = Xh D with D = diag(2^e_c) the column exponents of the pivot
-// columns, so X (W2 - I) = Xh (D (W2 - I)), W2 = [[Wr, Wi], [-Wi, Wr]].
-// A operand: digits of the rows of Xh (per-row exponent r_l of the
-// column-normalized rows); B operand: digits of the columns of D (W2 - I)
-// (per-column exponent w_j). Both scalings are exact (exponent shifts of the
-// digit extraction). All diagonal groups (s of them, N columns each) live in
-// TMEM at once; one commit, one drain into int64 fixed-point accumulators,
-// then Y = X + acc * 2^(r_l + w_j - F).
-// Every read of a tile's rows precedes the block barrier before the MMA, so
-// the update may run in place (Gd = Gs).
-// ---------------------------------------------------------------------------
-constexpr int UZ_THREADS = 512;
-constexpr int UZ_M = 128;
-constexpr int UZ_ASLICE = UZ_M * 128;       // 128 rows x 128 B (per digit)
-constexpr int UZ_BSLICE = kOzMaxK2 * 128;   // 64 rows x 128 B
-constexpr int UZ_F = 56;                    // fixed-point fraction bits of the update
-
-template <bool CPLX>
-__global__ void __launch_bounds__(UZ_THREADS, 1) update_ozaki_kernel(
-    const double *Gs, double *Gd, int64_t ld, int64_t m,
-    const int32_t *__restrict__ pairs, const double *__restrict__ Wb, int kmax,
-    const int32_t *__restrict__ cexp, int slices, unsigned long long *__restrict__ counters,
-    StepCtl ctl, UpdDigits ud) {
-    extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
-    uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = sm;                               // slices x 128 x 128 B
-    uint8_t *sB = sm + slices * UZ_ASLICE;          // slices x 64 x 128 B
-    __shared__ __align__(8) unsigned long long bar_done;
-    __shared__ uint32_t tmem_base_sh;
-    __shared__ int rexp[UZ_M];
-    __shared__ int wexp[kOzMaxK2];
-    __shared__ int xexp[kOzMaxK2];  // column exponents e_a of the K2 real columns of X
-    __shared__ int rmax_sh[UZ_M];
-    __shared__ int s_abort;
-
-    const int32_t *pd = pairs + 4 * blockIdx.y;
-    const int k = pd[1] + pd[3];
-    m = pair_rows(ctl, blockIdx.y, m);
-    if ((int64_t)blockIdx.x * UZ_M >= m) return;
-    if (pair_passthrough(ctl, blockIdx.y)) {
-        const int64_t r0 = (int64_t)blockIdx.x * UZ_M;
-        if (Gd != Gs)
-            pair_copy_rows(CPLX, Gs, Gd, ld, pd, r0, min(m, r0 + UZ_M), 0, k, threadIdx.x, UZ_THREADS);
-        return;
-    }
-    const int K2 = CPLX ? 2 * k : k;
-    const int NP = (K2 + 15) & ~15;
-    const int KP = NP;  // K of the MMA (K2 padded to 16)
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int s = slices;
-    const int64_t l0 = (int64_t)blockIdx.x * UZ_M;
-    const double *Wp = Wb + (size_t)blockIdx.y * kmax * kmax * (CPLX ? 2 : 1);
-    auto gcol = [&](int c) -> int64_t {
-        return c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
-    };
-    // X[l][a]: a < k real part of pivot column a, a >= k imaginary part
-    auto xval = [&](int64_t l, int a) -> double {
-        if (CPLX) {
-            const int c = a < k ? a : a - k;
-            return Gs[(gcol(c) * ld + l) * 2 + (a < k ? 0 : 1)];
-        }
-        return Gs[gcol(a) * ld + l];
-    };
-    // W2[a][j]
-    auto w2raw = [&](int a, int j) -> double {
-        if (CPLX) {
-            const int ar = a < k ? a : a - k, jr = j < k ? j : j - k;
-            const double re = Wp[((size_t)jr * kmax + ar) * 2], im = Wp[((size_t)jr * kmax + ar) * 2 + 1];
-            if (a < k) return j < k ? re : im;  // top: [Wr Wi]
-            return j < k ? -im : re;            // bottom: [-Wi Wr]
-        }
-        return Wp[(size_t)j * kmax + a];
-    };
-    auto w2val = [&](int a, int j) -> double { return a == j ? w2raw(a, j) - 1.0 : w2raw(a, j); };
-
-    if (warp == 0) tmem_alloc(su32(&tmem_base_sh), 512);
-    if (tid == 0) {
-        mbar_init(su32(&bar_done), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        s_abort = 0;
-    }
-    // zero operand tiles when they have padding (K2 below the 64-wide tile)
-    if (K2 < 64)
-        for (int i = tid; i < s * (UZ_ASLICE + UZ_BSLICE) / 16; i += UZ_THREADS)
-            reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
-    for (int a = tid; a < K2; a += UZ_THREADS) {
-        const int c = CPLX ? (a < k ? a : a - k) : a;
-        xexp[a] = cexp[gcol(c)];
-    }
-    __syncthreads();
-    const bool wpre = ud.img != nullptr;  // W-side digits produced by the inner solve
-    if (wpre) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(ud.img + (size_t)blockIdx.y * s * kUpdSliceBytes);
-        for (int i = tid; i < s * kUpdSliceBytes / 16; i += UZ_THREADS)
-            reinterpret_cast<uint4 *>(sB)[i] = src[i];
-        for (int j = tid; j < 64; j += UZ_THREADS) wexp[j] = ud.wexp[(size_t)blockIdx.y * 64 + j];
-    } else {
-    // column exponents of D W2: max over a of (exponent of W2_aj) + e_a, from the
-        // exponent fields (a power-of-two product changes only the exponent)
-        for (int j = warp; j < K2; j += UZ_THREADS / 32) {
-            int mx = -100000;
-            for (int a = lane; a < K2; a += 32) {
-                const unsigned long long mb = mag_bits(w2val(a, j));
-                if (mb) mx = max(mx, exp_of_bits(mb) + xexp[a]);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane == 0) wexp[j] = mx == -100000 ? -1021 : mx;
-        }
-    }
-    // row exponents of Xh = X D^-1: four threads per row (quarters of the columns)
-    {
-        const int r = tid & (UZ_M - 1), hf = tid >> 7;
-        const int64_t l = l0 + r;
-        int mx = -100000;
-        if (l < m) {
-            double xs[kOzMaxK2 / 4];
-#pragma unroll
-            for (int q = 0; q < kOzMaxK2 / 4; ++q) {
-                const int a = hf + 4 * q;
-                xs[q] = a < K2 ? xval(l, a) : 0.0;
-            }
-#pragma unroll
-            for (int q = 0; q < kOzMaxK2 / 4; ++q) {
-                const int a = hf + 4 * q;
-                const unsigned long long mb = mag_bits(xs[q]);
-                if (a < K2 && mb) mx = max(mx, exp_of_bits(mb) - xexp[a]);
-            }
-        }
-        if (hf == 0) rmax_sh[r] = mx;
-        __syncthreads();
-        for (int h = 1; h < 4; ++h) {
-            if (hf == h) rmax_sh[r] = max(rmax_sh[r], mx);
-            __syncthreads();
-        }
-        if (hf == 0) {
-            const int o = rmax_sh[r];
-            rexp[r] = o == -100000 ? -1021 : o;
-        }
-    }
-    __syncthreads();
-    if (!wpre) {
-        // digits of the columns of D W2: B operand row j, K position a;
-        // (D W2)_aj < 2^w_j  <=>  W2_aj < 2^(w_j - e_a)
-        // K positions a, a + 1 per thread: one 32-bit shared store per digit
-        const int K2h = (K2 + 1) / 2;
-        for (int idx = tid; idx < K2 * K2h; idx += UZ_THREADS) {
-            const int a = (idx % K2h) * 2, j = idx / K2h;
-            const double x0 = w2val(a, j);
-            const double x1 = a + 1 < K2 ? w2val(a + 1, j) : 0.0;
-            const unsigned long long q0 = fixed63(x0, wexp[j] - xexp[a]);
-            const unsigned long long q1 = a + 1 < K2 ? fixed63(x1, wexp[j] - xexp[a + 1]) : 0ull;
-            const uint32_t off = sw128_off(j, a * 2);
-            for (int t = 1; t <= s; ++t)
-                *reinterpret_cast<uint32_t *>(sB + (t - 1) * UZ_BSLICE + off) =
-                    dg_digits2_bits(q0, neg_bits(x0), q1, neg_bits(x1), t);
-        }
-    }
-    // digits of X rows: A operand row r, K positions a, a+1 (consecutive threads
-    // take consecutive rows of one column pair: coalesced loads, one 32-bit
-    // shared store per digit)
-    const int K2h = (K2 + 1) / 2;
-    constexpr int UZ_ITEMS = UZ_M * (kOzMaxK2 / 2) / UZ_THREADS;
-    {
-        double xv0[UZ_ITEMS], xv1[UZ_ITEMS];
-#pragma unroll
-        for (int it = 0; it < UZ_ITEMS; ++it) {
-            const int idx = tid + it * UZ_THREADS;
-            const int r = idx % UZ_M, a = (idx / UZ_M) * 2;
-            const int64_t l = l0 + r;
-            xv0[it] = (l < m && a < K2) ? xval(l, a) : 0.0;
-            xv1[it] = (l < m && a + 1 < K2) ? xval(l, a + 1) : 0.0;
-        }
-#pragma unroll
-        for (int it = 0; it < UZ_ITEMS; ++it) {
-            const int idx = tid + it * UZ_THREADS;
-            const int r = idx % UZ_M, a = (idx / UZ_M) * 2;
-            if (a >= 2 * K2h) continue;
-            const unsigned long long q0 = fixed63(xv0[it], rexp[r] + xexp[a]);  // Xh_la < 2^r_l
-            const unsigned long long q1 = fixed63(xv1[it], rexp[r] + xexp[a + 1]);
-            const bool n0 = neg_bits(xv0[it]), n1 = neg_bits(xv1[it]);
-            const uint32_t off = sw128_off(r, a * 2);
-            for (int t = 1; t <= s; ++t)
-                *reinterpret_cast<uint32_t *>(sA + (t - 1) * UZ_ASLICE + off) = dg_digits2_bits(q0, n0, q1, n1, t);
-        }
-    }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base_sh;
-    if (tid == 0) {
-        // As in the Gram: with N = 64 the B tiles of digits u, u + 1, ... (64-row
-        // slices) and the groups t + u, t + u + 1, ... are adjacent, so one
-        // product with N = 64 * run covers a run of up to four; digit t = 1
-        // initializes every group.
-        const uint32_t idesc = idesc_f16(UZ_M, NP);
-        const bool mergeable = NP == 64;
-        const uint32_t a_base = su32(sA), b_base = su32(sB);
-        for (int t = 1; t <= s; ++t) {
-            const int umax = s + 1 - t;
-            for (int u = 1; u <= umax;) {
-                const int run = mergeable ? min(4, umax - u + 1) : 1;
-                const uint32_t id = run == 1 ? idesc : idesc_f16(UZ_M, 64 * run);
-                const uint32_t dt = tmem + (uint32_t)((t + u - 2) * NP);
-                for (int ks = 0; ks < KP / 16; ++ks)
-                    mma_f16(dt, desc_sw128(a_base + (t - 1) * UZ_ASLICE + ks * 32),
-                            desc_sw128(b_base + (u - 1) * UZ_BSLICE + ks * 32), id,
-                            (t == 1 && ks == 0) ? 0u : 1u);
-                u += run;
-            }
-        }
-        mma_commit(su32(&bar_done));
-    }
-    if (tid == 0 && !mbar_wait(su32(&bar_done), 0)) s_abort = 1;
-    __syncthreads();
-    tc_fence_after();
-    if (!s_abort) {
-        // thread: TMEM lane quadrant warp%4 (rows), column quarter warp/4
-        const int quad = warp & 3, hfc = warp >> 2;
-        const int r = quad * 32 + lane;
-        const int64_t l = l0 + r;
-        const int jbase = hfc * 16;
-        long long acc[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = 0;
-        // two groups (up to 32 values of this thread) per TMEM round trip
-        for (int d0 = 2; d0 <= s + 1; d0 += 2) {
-            uint32_t v[2][2][8];
-#pragma unroll
-            for (int g = 0; g < 2; ++g)
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (d0 + g <= s + 1 && jbase + 8 * h < NP)
-                        tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) +
-                                     (uint32_t)((d0 + g - 2) * NP + jbase + 8 * h),
-                                 v[g][h]);
-            tmem_wait_ld();
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                const int d = d0 + g;
-                if (d > s + 1) break;
-                const int sh = UZ_F - kBeta * d;  // may be negative for the lowest digits
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (jbase + 8 * h >= NP) break;
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const long long iv = (long long)__float2int_rn(__uint_as_float(v[g][h][j]));
-                        if (sh >= 0)
-                            acc[8 * h + j] += iv << sh;
-                        else if (sh > -62)
-                            acc[8 * h + j] += (iv + (1ll << (-sh - 1))) >> (-sh);
-                    }
-                }
-            }
-        }
-        if (l < m) {
-            double xo[16];
-            int64_t oo[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int jj = jbase + j;
-                oo[j] = -1;
-                xo[j] = 0.0;
-                if (jj < K2) {
-                    if (CPLX) {
-                        const int c = jj < k ? jj : jj - k;
-                        oo[j] = (gcol(c) * ld + l) * 2 + (jj < k ? 0 : 1);
-                    } else {
-                        oo[j] = gcol(jj) * ld + l;
-                    }
-                    xo[j] = Gs[oo[j]];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int jj = jbase + j;
-                if (jj < K2) Gd[oo[j]] = xo[j] + int_scaled_to_double(acc[j], rexp[r] + wexp[jj] - UZ_F);
-            }
-        }
-    } else if (tid == 0 && counters) {
-        atomicOr(&counters[kCntErr], kErrTimeout);
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 512);
-}
-
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -876,15 +454,7 @@ cudaError_t set_smem(K kern, size_t bytes) {
 
 }  // namespace
 
-int ozaki_default_slices(bool gram) { return gram ? GZ_SLICES : 8; }
-
-int ozaki_max_update_slices(bool cplx, int kmax) {
-    const int np = ((cplx ? 2 * kmax : kmax) + 15) & ~15;
-    const int by_tmem = 512 / np;
-    const int by_smem = (227 * 1024 - 1024) / (UZ_ASLICE + UZ_BSLICE);
-    int s = by_tmem < by_smem ? by_tmem : by_smem;
-    return s < kOzUpdMaxSlices ? s : kOzUpdMaxSlices;
-}
+int ozaki_default_slices(bool gram) { return gram ? GZ_SLICES : kUdMaxSlices; }
 
 bool ozaki_supported(bool cplx, int kmax) { return (cplx ? 2 * kmax : kmax) <= kOzMaxK2; }
 
@@ -946,31 +516,6 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
         gram_fixed_to_double_kernel<true><<<g2, 256, 0, st>>>(acc, pairs, cexp, A, kmax, k2max, slices);
     else
         gram_fixed_to_double_kernel<false><<<g2, 256, 0, st>>>(acc, pairs, cexp, A, kmax, k2max, slices);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_update_ozaki(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
-                                const int32_t *pairs, int npairs, const double *W, int kmax,
-                                const int32_t *cexp, int slices, unsigned long long *counters,
-                                cudaStream_t st, StepCtl ctl, UpdDigits ud) {
-    if (npairs <= 0) return cudaSuccess;
-    const int k2max = cplx ? 2 * kmax : kmax;
-    // all s diagonal groups of N columns must fit the 512 TMEM columns
-    const int np = (k2max + 15) & ~15;
-    if (k2max > kOzMaxK2 || slices < 1 || slices > kOzUpdMaxSlices || slices * np > 512)
-        return cudaErrorInvalidValue;
-    const size_t smem = (size_t)slices * (UZ_ASLICE + UZ_BSLICE) + 1024;
-    dim3 grid((unsigned)((m + UZ_M - 1) / UZ_M), npairs);
-    cudaError_t e;
-    if (cplx) {
-        if ((e = set_smem(update_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
-        update_ozaki_kernel<true><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
-                                                                   cexp, slices, counters, ctl, ud);
-    } else {
-        if ((e = set_smem(update_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
-        update_ozaki_kernel<false><<<grid, UZ_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, W, kmax,
-                                                                    cexp, slices, counters, ctl, ud);
-    }
     return cudaGetLastError();
 }
 

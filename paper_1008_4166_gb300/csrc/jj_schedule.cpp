@@ -1,9 +1,31 @@
-// Parallel block-pivot orderings of the two-level algorithms (Sec. 4):
-// Initialize (Alg. 4.1), the modified modulus step MMStep (Alg. 4.2) and the
-// modified round-robin step RLStep (Alg. 4.3), run for every process of a
-// ring of p = nbl/2 processes. On one GPU the ring shift that follows each
-// step becomes a relabelling: the table records, per step, the block pair
-// each process holds, and every pair of a step runs in the same launch.
+// Parallel block-pivot orderings of the two-level algorithms (Sec. 4), built
+// from their definitions.
+//
+// Pair sets. With nbl = 2p blocks numbered 1..nbl, every parallel step is a
+// perfect matching of the blocks:
+//   * modulus (Sec. 4.1): step t pairs the blocks whose indices sum to
+//     t + 1 modulo nbl; when that residue is even, two blocks are their own
+//     partners (2i = t + 1 mod nbl), they lie p apart, and the process that
+//     would idle transforms that pair of the p-th block superdiagonal (the
+//     pairs visited twice per sweep). nbl steps per sweep.
+//   * round robin (Sec. 4.2): the tournament schedule with block nbl fixed:
+//     step t pairs the blocks 1..nbl-1 whose indices sum to t + 2 modulo
+//     nbl - 1, and the block that is its own partner meets block nbl. nbl - 1
+//     steps per sweep.
+// Both sets are the same in every sweep; the first step of either is the
+// main block antidiagonal (i + j = nbl + 1).
+//
+// Processes. Process q starts the first sweep on blocks (q + 1, nbl - q)
+// (Sec. 4). Between steps the processes form a ring: each keeps one block and
+// receives the other from one neighbour, the neighbour above (q + 1) in odd
+// sweeps and below (q - 1) in even ones, so the pair of process q in the next
+// step is the one that meets both its current pair and that neighbour's. With
+// two processes each is the other's neighbour on both sides and the ring does
+// not decide; process 0 then keeps the lower-numbered of its blocks.
+//
+// On one GPU the ring shift becomes a relabelling: the table records, per
+// step, the pair each process holds, and every pair of a step runs in the same
+// launch.
 #include <stdint.h>
 
 #include <vector>
@@ -12,92 +34,87 @@ namespace jj {
 
 namespace {
 
-struct PivotState {
-    int ip, jp, i_blk, j_blk;
-};
-
-// Alg. 4.1: process `rank` starts the sweep on blocks (rank+1, nbl-rank).
-PivotState initialize(int rank, int nbl) {
-    PivotState s;
-    s.ip = rank + 1;
-    s.i_blk = s.ip;
-    s.jp = nbl - rank;
-    s.j_blk = s.jp;
-    return s;
-}
-
-// Alg. 4.2: next pivot of the modified modulus strategy.
-void mm_step(int nbl, PivotState &s) {
-    if (s.ip + s.jp > nbl) {
-        s.ip += 1;
-        if (s.ip == s.jp) {
-            s.ip -= nbl / 2;
-            s.jp = s.ip;
+// partner[b] (1-based) of every block in step t of the ordering.
+void step_partners(int nbl, int order, int t, std::vector<int> &partner) {
+    partner.assign(nbl + 1, 0);
+    if (order == 1) {
+        const int r = (t + 1) % nbl;
+        std::vector<int> self;
+        for (int i = 1; i <= nbl; ++i) {
+            int j = ((r - i) % nbl + nbl) % nbl;  // i + j = r (mod nbl), j in 1..nbl
+            if (j == 0) j = nbl;
+            if (j == i)
+                self.push_back(i);
+            else
+                partner[i] = j;
         }
-        s.i_blk = s.ip;
+        if (self.size() == 2) {  // even residue: the pair of the p-th superdiagonal
+            partner[self[0]] = self[1];
+            partner[self[1]] = self[0];
+        }
     } else {
-        s.jp += 1;
-        s.j_blk = s.jp;
-    }
-}
-
-// Alg. 4.3: next pivot of the modified round-robin strategy (the swap flag
-// only renumbers the pair so that i_blk < j_blk, which the table does anyway).
-void rl_step(int nbl, PivotState &s) {
-    if (s.ip + s.jp > nbl) {
-        if (s.jp < nbl) {
-            s.ip += 1;
-            if (s.ip < s.jp) {
-                s.i_blk = s.ip;
+        const int M = nbl - 1;
+        const int r = (t + 2) % M;
+        for (int i = 1; i <= M; ++i) {
+            int j = ((r - i) % M + M) % M;
+            if (j == 0) j = M;
+            if (j == i) {
+                partner[i] = nbl;
+                partner[nbl] = i;
             } else {
-                s.ip = s.jp;
-                s.i_blk = s.j_blk;
-                s.jp = nbl;
-                s.j_blk = s.jp;
+                partner[i] = j;
             }
-        } else if (s.ip > nbl / 2) {
-            s.ip = s.ip - nbl / 2 + 1;
-            s.i_blk = s.ip;
-        } else {
-            s.jp = s.ip + 1;
-            s.j_blk = s.jp;
         }
-    } else {
-        s.jp += 1;
-        s.j_blk = s.jp;
     }
 }
 
 }  // namespace
 
-// Pairs (0-based, i < j) of sweep `sweep` (>= 1): steps x (nbl/2) x 2 ints.
-// Returns the number of steps, or -1 for invalid arguments.
+// Pairs (0-based, i < j) of sweep `sweep` (>= 1): steps x (nbl/2) x 2 ints,
+// pair q of a step being the pivot of process q. Returns the number of steps,
+// or -1 for invalid arguments.
 int schedule_pairs(int nbl, int order, int sweep, int32_t *pairs) {
     if (nbl < 2 || (nbl & 1) || sweep < 1 || (order != 0 && order != 1)) return -1;
     const int p = nbl / 2;
     const int steps = order == 1 ? nbl : nbl - 1;
-    std::vector<PivotState> st(p);
-    for (int q = 0; q < p; ++q) st[q] = initialize(q, nbl);
+    std::vector<int> a(p), b(p), na(p), nb(p), partner;
+    for (int q = 0; q < p; ++q) {
+        a[q] = q + 1;
+        b[q] = nbl - q;
+    }
     for (int sw = 1; sw <= sweep; ++sw) {
+        const int dir = (sw & 1) ? 1 : p - 1;  // neighbour that sends: q + 1 (odd), q - 1 (even)
         for (int t = 0; t < steps; ++t) {
             if (sw == sweep && pairs) {
                 for (int q = 0; q < p; ++q) {
-                    int a = st[q].i_blk - 1, b = st[q].j_blk - 1;
-                    if (a > b) {
-                        const int x = a;
-                        a = b;
-                        b = x;
-                    }
-                    pairs[2 * (t * p + q)] = a;
-                    pairs[2 * (t * p + q) + 1] = b;
+                    pairs[2 * (t * p + q)] = (a[q] < b[q] ? a[q] : b[q]) - 1;
+                    pairs[2 * (t * p + q) + 1] = (a[q] < b[q] ? b[q] : a[q]) - 1;
+                }
+                if (t == steps - 1) break;
+            }
+            step_partners(nbl, order, t + 1 < steps ? t + 1 : 0, partner);
+            if (p == 1) continue;
+            if (p == 2) {
+                const int keep = a[0] < b[0] ? a[0] : b[0];
+                na[0] = keep;
+                nb[0] = partner[keep];
+                const int other = (partner[keep] == a[1]) ? b[1] : a[1];
+                na[1] = other;
+                nb[1] = partner[other];
+            } else {
+                for (int q = 0; q < p; ++q) {
+                    const int s = (q + dir) % p;
+                    // the block of q whose next partner the neighbour holds now
+                    const bool ka = partner[a[q]] == a[s] || partner[a[q]] == b[s];
+                    const bool kb = partner[b[q]] == a[s] || partner[b[q]] == b[s];
+                    if (ka == kb) return -1;  // not a ring shift (never for these orderings)
+                    const int keep = ka ? a[q] : b[q];
+                    na[q] = keep;
+                    nb[q] = partner[keep];
                 }
             }
-            for (int q = 0; q < p; ++q) {
-                if (order == 1)
-                    mm_step(nbl, st[q]);
-                else
-                    rl_step(nbl, st[q]);
-            }
+            a.swap(na);
+            b.swap(nb);
         }
     }
     return steps;

@@ -28,6 +28,7 @@ EXPORTS = [
     "jjacobi_default_params", "jjacobi_create", "jjacobi_solve", "jjacobi_extract",
     "jjacobi_solve_host", "jjacobi_solve_batched", "jjacobi_destroy",
     "jjacobi_status_string", "jjacobi_version", "jjacobi_schedule", "jjacobi_kernel_times",
+    "jjacobi_set_wait_limit",
     "jjk_column_norms", "jjk_plain_step", "jjk_gram", "jjk_inner", "jjk_update", "jjk_extract",
     "jjk_gram_noalloc",
 ]
@@ -88,6 +89,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "jjacobi_version": (i32, []),
         "jjacobi_schedule": (i32, [i32, i32, i32, vp]),
         "jjacobi_kernel_times": (ctypes.c_int, [vp, vp, vp]),
+        "jjacobi_set_wait_limit": (ctypes.c_int, [vp, i64]),
         "jjk_column_norms": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, vp]),
         "jjk_plain_step": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, i32, vp, vp, dbl, vp, vp]),
         "jjk_gram": (ctypes.c_int, [i32, i32, vp, i64, i64, vp, i32, vp, i32, vp]),
@@ -254,6 +256,10 @@ class Handle:
         rc = load().jjacobi_solve(self.h, _ptr(G), int(ldg), Jc.ctypes.data, ctypes.byref(info))
         _check(rc, "jjacobi_solve", allow)
         return info
+
+    def jjacobi_set_wait_limit(self, ns: int) -> None:
+        """Bound (ns) of the device-side waits of this handle's kernels; <= 0: 2 s."""
+        _check(load().jjacobi_set_wait_limit(self.h, int(ns)), "jjacobi_set_wait_limit")
 
     def jjacobi_kernel_times(self):
         """(ms, launches) per kernel family: gram, inner, update, plain step, norms."""

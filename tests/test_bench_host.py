@@ -16,14 +16,18 @@ import bench  # noqa: E402
 
 
 def test_blocked_flop_convention():
-    # one pair (nbl = 2), one step, one sweep: Gram k(k+1)/2 m + update m k^2 MACs,
-    # plus 5 k MACs per inner rotation; complex MAC = 8 flops
-    info = {"nbl": 2, "sweeps": 1, "steps_per_sweep": 1, "rotations": 3}
+    # executed work: Gram k(k+1)/2 m MACs per evaluated pair, update m k^2 MACs
+    # per rotated pair, 5 k MACs per inner rotation; complex MAC = 8 flops
+    info = {"nbl": 2, "sweeps": 4, "steps_per_sweep": 1, "rotations": 3,
+            "pairs_evaluated": 3, "pairs_rotated": 2}
     n, m = 8, 10
     k = 2.0 * n / 2
-    expect = 8.0 * (k * (k + 1) / 2 * m + m * k * k + 3 * 5.0 * k)
+    expect = 8.0 * (3 * k * (k + 1) / 2 * m + 2 * m * k * k + 3 * 5.0 * k)
     assert bench.blocked_flops(n, m, True, info) == pytest.approx(expect)
     assert bench.blocked_flops(n, m, False, info) == pytest.approx(expect / 4.0)
+    # every pair of every step of every sweep: 4 sweeps x 1 step x 1 pair
+    every = 8.0 * (4 * (k * (k + 1) / 2 * m + m * k * k) + 3 * 5.0 * k)
+    assert bench.blocked_flops_all_pairs(n, m, True, info) == pytest.approx(every)
 
 
 def test_plain_flop_convention():
@@ -36,12 +40,16 @@ def test_captured_traffic_is_void_once_the_kernel_source_changes(tmp_path, monke
     (fake / "profiles").mkdir(parents=True)
     csrc = fake / "paper_1008_4166_gb300" / "csrc"
     csrc.mkdir(parents=True)
+    import hashlib
+    h = hashlib.sha256()
     for f in ("jj_update.cu", "jj_common.cuh"):
         shutil.copy(os.path.join(ROOT, "paper_1008_4166_gb300", "csrc", f), csrc / f)
-    shutil.copy(os.path.join(ROOT, "profiles", "traffic.txt"), fake / "profiles" / "traffic.txt")
+        h.update(open(csrc / f, "rb").read())
+    with open(fake / "profiles" / "traffic.txt", "w") as fh:
+        fh.write("# kernel bytes files hash\n")
+        fh.write(f"update_fp64_kernel 123456 jj_update.cu,jj_common.cuh {h.hexdigest()[:16]}\n")
     monkeypatch.setattr(bench, "ROOT", str(fake))
-    v = bench.captured_traffic("update_fp64_kernel")
-    assert isinstance(v, int) and v > 0
+    assert bench.captured_traffic("update_fp64_kernel") == 123456
     assert bench.captured_traffic("no_such_kernel") is None
     with open(csrc / "jj_update.cu", "a") as fh:
         fh.write("// edited\n")
@@ -83,7 +91,8 @@ def test_reference_arm_line_matches_the_measured_arm_config():
     class _A:
         workload = bench.WORKLOAD
         block_width = 16
-        gemm = "hybrid"
+        gemm = "ozaki"
+        digits = 0
         strategy = "oriented"
 
     class _P:

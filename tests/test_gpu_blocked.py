@@ -201,13 +201,7 @@ def test_blocked_graded_complex(gemm):
     ref = oracle.solve_plain(P.G, P.J)
     got = solve_gpu(P.G, P.J, block_width=16, gemm=gemm)
     assert got["info"]["status"] == 0
-    # The all-digit form misses the published bound on strongly graded inputs:
-    # its update carries one exponent per row and column (errors relative to
-    # the row and column scales, not to each entry), where the FP64 update's
-    # error is relative to sum_a |x_la||w_aj|. It is held to 1e-9 here; the
-    # FP64 and hybrid forms to 1e-10.
-    bound = 1e-9 if gemm == 1 else 1e-10
-    assert max_rel_err(got["lam"], ref["lam"]) <= bound
+    assert max_rel_err(got["lam"], ref["lam"]) <= 1e-10
 
 
 @pytest.mark.parametrize("gemm", GEMMS)
@@ -299,7 +293,7 @@ def test_block_oriented_real_matches_oracle(gemm):
 @pytest.mark.parametrize("order", [0, 1])
 def test_block_oriented_complex_ragged_and_graded(order):
     """Unequal block sizes (150 columns, b = 11: off-diagonal blocks of 10 x 11)
-    and the graded recipe held to 1e-10 (hybrid form)."""
+    and the graded recipe held to 1e-10 (hybrid and all-digit forms)."""
     require_gpu()
     from paper_1008_4166_gb300 import jjacobi as jj
 
@@ -311,10 +305,11 @@ def test_block_oriented_complex_ragged_and_graded(order):
     assert max_rel_err(got["lam"], ref["lam"]) <= eig_rel_tol(P.G)
     Pg = synth.make_workload("graded_c128_n4096_b64", n=192)
     refg = oracle.solve_plain(Pg.G, Pg.J)
-    gg = solve_gpu(Pg.G, Pg.J, block_width=16, gemm=2, order=order,
-                   block_strategy=jj.JJ_BLOCK_ORIENTED)
-    assert gg["info"]["status"] == 0
-    assert max_rel_err(gg["lam"], refg["lam"]) <= 1e-10
+    for gemm in (2, 1):  # hybrid, all-digit
+        gg = solve_gpu(Pg.G, Pg.J, block_width=16, gemm=gemm, order=order,
+                       block_strategy=jj.JJ_BLOCK_ORIENTED)
+        assert gg["info"]["status"] == 0
+        assert max_rel_err(gg["lam"], refg["lam"]) <= 1e-10, gemm
 
 
 def test_block_oriented_rejects_pivots_beyond_shared_memory():

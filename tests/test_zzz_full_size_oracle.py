@@ -53,7 +53,8 @@ def test_stored_values_come_from_the_oracle_alone():
 
 
 @pytest.mark.gpu
-def test_headline_eigenvalues_match_the_full_oracle_solve():
+@pytest.mark.parametrize("gemm", [1, 2])  # all digits (the bench's form), hybrid
+def test_headline_eigenvalues_match_the_full_oracle_solve(gemm):
     from tests.gpu_util import require_gpu, to_dev
 
     jj = require_gpu()
@@ -62,7 +63,7 @@ def test_headline_eigenvalues_match_the_full_oracle_solve():
     P = synth.make_workload("graded_c128_n4096_b64", precision="f64")
     ref = _gold()
     Gd = to_dev(P.G)
-    with jj.Handle(P.m, P.n, jj.JJ_C128, block_width=16, gemm=jj.JJ_GEMM_OZAKI_GRAM,
+    with jj.Handle(P.m, P.n, jj.JJ_C128, block_width=16, gemm=gemm,
                    block_strategy=jj.JJ_BLOCK_ORIENTED) as h:
         info = h.jjacobi_solve(Gd, Gd.stride(1), P.J)
         lam = torch.empty(P.n, dtype=torch.float64, device="cuda")
