@@ -48,6 +48,23 @@ __device__ __forceinline__ uint32_t dg_digit84(const Fx84 &f, int t) {
     return t <= 9 ? (uint32_t)(f.hi >> (64 - 7 * t)) & 127u : (f.lo >> (84 - 7 * t)) & 127u;
 }
 
+// The 21-bit window of V = floor(|x| 2^(84 - e)) (|x| < 2^e) that holds the
+// digits 3p + 1, 3p + 2, 3p + 3: bits [63 - 21p, 84 - 21p) of V, so that digit
+// 3p + 1 + i is (window >> (14 - 7i)) & 127. Integer shifts only.
+__device__ __forceinline__ uint32_t dg_window21(double x, int e, int p) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return 0u;
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E - 1054 - e + 21 * p;  // V >> (63 - 21p) = mant 2^sh, sh <= 31
+    unsigned long long w = 0ull;
+    if (sh >= 0)
+        w = mant << sh;  // only the low 21 bits are kept
+    else if (sh > -64)
+        w = mant >> (-sh);
+    return (uint32_t)w & 0x1FFFFFu;
+}
+
 // Two signed digits as packed fp16 bits: +-d is (1024 + d) - 1024 in fp16 (the
 // bit pattern of +-(1024 + d) is (0x6400 or 0xE400) | d; adding -+1024 leaves
 // +-d exactly).

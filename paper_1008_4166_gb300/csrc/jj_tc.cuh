@@ -76,20 +76,22 @@ __device__ __forceinline__ uint64_t global_ns() {
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // Bounded wait for the completion of the mbarrier phase with the given parity;
-// false when the limit is reached. A failed try_wait may itself suspend the
-// thread for an unspecified time, so the bound is wall-clock time (the global
-// nanosecond timer, read only after a failed poll), with an iteration cap
-// behind it.
+// false when the limit is reached. Each try_wait suspends the thread until the
+// phase completes or a hint of 1 ms passes (a suspended thread issues no
+// instructions, so a waiting role leaves the issue slots to the working ones).
+// The bound is wall-clock time (the global nanosecond timer, read only after a
+// failed poll), with an iteration cap behind it.
+constexpr uint32_t kSuspendHintNs = 1000000u;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
                                           uint64_t limit_ns = kWaitLimitNs) {
     uint64_t t0 = 0;
     for (long i = 0; i < (1L << 28); ++i) {
         uint32_t ok;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
             " selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
             : "memory");
         if (ok) return true;
         const uint64_t t = global_ns();

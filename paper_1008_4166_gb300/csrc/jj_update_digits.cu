@@ -227,30 +227,54 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
         long long *scr = scratch + (size_t)blockIdx.x * kUdPositions * UD_M;
         int q = S.q0, r = S.r0;
         long long acc[32];
-        // drain group g into the Horner sums; false when a wait ran out
-        auto drain = [&](long long g, bool first) -> bool {
-            const int slot = (int)(g & (UD_TSLOTS - 1));
-            const uint32_t par = (uint32_t)((g >> 3) & 1);
-            const bool ok = __all_sync(0xffffffffu, !*abort_flag && mbar_wait(su32(&S.t_full[slot]), par, wait_ns));
-            if (!ok) {
-                *abort_flag = 1;
-                return false;
+        // Drain n = 1 or 2 consecutive groups g (and g + 1) into the Horner sums.
+        // Two groups fold exactly in int32 first (|S_d| < 2^23.6, so
+        // S_d 128 + S_(d+1) < 2^31), then into int64 with one shift; both TMEM
+        // slots are released after the pair. False when a wait ran out.
+        auto drain = [&](long long g, int n, bool first) -> bool {
+            for (int i = 0; i < n; ++i) {
+                const int slot = (int)((g + i) & (UD_TSLOTS - 1));
+                const uint32_t par = (uint32_t)(((g + i) >> 3) & 1);
+                const bool ok = __all_sync(0xffffffffu,
+                                           !*abort_flag && mbar_wait(su32(&S.t_full[slot]), par, wait_ns));
+                if (!ok) {
+                    *abort_flag = 1;
+                    return false;
+                }
             }
             tc_fence_after();
-            uint32_t v[16];
+            const int s0 = (int)(g & (UD_TSLOTS - 1)), s1 = (int)((g + 1) & (UD_TSLOTS - 1));
+            const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(hh * 32);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(slot * 64 + hh * 32 + h * 16), v);
+            for (int h = 0; h < 4; ++h) {
+                uint32_t v0[8], v1[8];
+                tmem_ld8(lane_base + (uint32_t)(s0 * 64 + h * 8), v0);
+                if (n == 2) tmem_ld8(lane_base + (uint32_t)(s1 * 64 + h * 8), v1);
                 tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const long long iv = (long long)__float2int_rn(__uint_as_float(v[c]));  // exact
-                    acc[h * 16 + c] = first ? iv : acc[h * 16 + c] * 128 + iv;
+                for (int c = 0; c < 8; ++c) {
+                    const int i0 = __float2int_rn(__uint_as_float(v0[c]));  // exact integers
+                    long long& a = acc[h * 8 + c];
+                    if (n == 2) {
+                        const int pr = i0 * 128 + __float2int_rn(__uint_as_float(v1[c]));
+                        a = first ? (long long)pr : a * 16384 + pr;
+                    } else {
+                        a = first ? (long long)i0 : a * 128 + i0;
+                    }
                 }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(su32(&S.t_empty[slot]));
+            if (lane == 0) {
+                mbar_arrive(su32(&S.t_empty[s0]));
+                if (n == 2) mbar_arrive(su32(&S.t_empty[s1]));
+            }
+            return true;
+        };
+        // groups [d_lo, d_hi] of item j, in pairs
+        auto drain_range = [&](long long g0, int d_lo, int d_hi) -> bool {
+            for (int d = d_lo; d <= d_hi; d += 2)
+                if (!drain(g0 + d - 2, d + 1 <= d_hi ? 2 : 1, d == d_lo)) return false;
             return true;
         };
         for (int j = 0; j < count; ++j) {
@@ -261,12 +285,12 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
             const int64_t l = (int64_t)r * UD_M + rl;
             const long long g0 = (long long)j * s;
             bool ok = true;
-            for (int d = 2; d <= hA + 1 && ok; ++d) ok = drain(g0 + d - 2, d == 2);
+            ok = drain_range(g0, 2, hA + 1);
             if (!ok) break;
             if (phaseB) {
 #pragma unroll
                 for (int c = 0; c < 32; ++c) scr[(size_t)(hh * 32 + c) * UD_M + rl] = acc[c];
-                for (int d = UD_PA + 2; d <= s + 1 && ok; ++d) ok = drain(g0 + d - 2, d == UD_PA + 2);
+                ok = drain_range(g0, UD_PA + 2, s + 1);
                 if (!ok) break;
             }
             const int rho = j % UD_RING;
@@ -275,29 +299,47 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                 break;
             }
             const int re = S.rexp[rho][rl];
-            const int32_t *wx = wexp + (size_t)q * kUdPositions;
+            const int32_t *wx = wexp + (size_t)q * kUdPositions + hh * 32;
+            // Y = X + corr, 4 outputs at a time: all loads of a batch are issued
+            // before its stores (Gd may be Gs, so a load cannot move above a store)
             if (l < rows) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int cc = CPLX ? c : hh * 32 + c;  // pivot column of position hh * 32 + c
-                    if (cc >= k) continue;
-                    const int64_t idx = CPLX ? (ud_gcol(pd, cc) * ld + l) * 2 + hh : ud_gcol(pd, cc) * ld + l;
-                    long long hi;
-                    unsigned long long lo;
-                    if (phaseB) {
-                        // T = accA 2^(7 (s - 6)) + accB
-                        const long long a = scr[(size_t)(hh * 32 + c) * UD_M + rl];
-                        const int sh = 7 * (s - UD_PA);
-                        const unsigned long long al = (unsigned long long)a << sh;
-                        const long long ah = a >> (64 - sh);
-                        lo = al + (unsigned long long)acc[c];
-                        hi = ah + (acc[c] >> 63) + (lo < al ? 1 : 0);
-                    } else {
-                        lo = (unsigned long long)acc[c];
-                        hi = acc[c] >> 63;
+                for (int cb = 0; cb < 32; cb += 4) {
+                    int64_t idx[4];
+                    double xv[4];
+                    long long av[4];
+                    int wv[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int cc = CPLX ? cb + c : hh * 32 + cb + c;  // pivot column of the position
+                        idx[c] = cc < k ? (CPLX ? (ud_gcol(pd, cc) * ld + l) * 2 + hh : ud_gcol(pd, cc) * ld + l)
+                                        : -1;
                     }
-                    const double corr = i128_scaled_to_double(hi, lo, re + wx[hh * 32 + c] - 7 * (s + 1));
-                    Gd[idx] = Gs[idx] + corr;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        xv[c] = idx[c] >= 0 ? Gs[idx[c]] : 0.0;
+                        av[c] = phaseB ? scr[(size_t)(hh * 32 + cb + c) * UD_M + rl] : 0ll;
+                        wv[c] = wx[cb + c];
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (idx[c] < 0) continue;
+                        long long hi;
+                        unsigned long long lo;
+                        const long long b = acc[cb + c];
+                        if (phaseB) {
+                            // T = accA 2^(7 (s - 6)) + accB
+                            const int sh = 7 * (s - UD_PA);
+                            const unsigned long long al = (unsigned long long)av[c] << sh;
+                            const long long ah = av[c] >> (64 - sh);
+                            lo = al + (unsigned long long)b;
+                            hi = ah + (b >> 63) + (lo < al ? 1 : 0);
+                        } else {
+                            lo = (unsigned long long)b;
+                            hi = b >> 63;
+                        }
+                        Gd[idx[c]] = xv[c] + i128_scaled_to_double(hi, lo, re + wv[c] - 7 * (s + 1));
+                    }
                 }
             }
             __syncwarp();
@@ -407,10 +449,14 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
     } else {
         // ------------------------------------------------------------------
         // Builders: digits of Xh = X D^-1 relative to each row's exponent.
-        // A pass writes three digits of the warp's rows of the tile, in two
-        // batches of tasks; each batch issues all its loads at once (the first
-        // batch before the wait for free slots, so that the loads' latency
-        // overlaps it) and keeps its values in registers.
+        // A pass writes three digits (one 21-bit window of each value's 84-bit
+        // fixed-point image) of the warp's rows of the tile, in two batches of
+        // tasks; each batch issues all its loads at once (the first batch before
+        // the wait for free slots, so that the loads' latency overlaps it). The
+        // row exponents are found in the first pass and kept in shared memory.
+        // Each lane stores its u32 items in an order rotated by its row, so that
+        // the 32 lanes of one store instruction hit 32 different banks of the
+        // swizzled tile.
         // ------------------------------------------------------------------
         const int bw = warp - UD_BLD0;
         int q = S.q0, r = S.r0;
@@ -425,6 +471,7 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
         // complex: a task is 2 rows x 32 columns (lane: column pair 2c', 2c'+1 of
         // row rr); real: 4 rows x 64 columns (lane: columns 8c'..8c'+7 of row rr)
         constexpr int NV = CPLX ? 4 : 8;          // values per lane and task
+        constexpr int NI = NV / 2;                // u32 items (two positions) per lane and task
         constexpr int TASKS = CPLX ? 64 : 32;     // tasks per tile
         constexpr int RPT = CPLX ? 2 : 4;         // rows per task
         constexpr int TPW = (TASKS + UD_BLD - 1) / UD_BLD;  // tasks per builder warp (at most)
@@ -432,6 +479,32 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
         constexpr int NC = CPLX ? 2 : NV;         // columns per lane
         const int cl = CPLX ? (lane & 15) : (lane & 7);
         const int rr = CPLX ? (lane >> 4) : (lane >> 3);
+        // value v of this lane sits at real-form position vpos[v]; item i is the
+        // value pair (2i, 2i + 1). Complex: [re c0, re c1, im c0, im c1], with the
+        // two items swapped for rr = 1; real: columns 8c' + ((v + 2 rr) mod 8).
+        int vcol[NV];  // pivot column of value v
+        int ipos[NI];  // position of item i's first value
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (CPLX) {
+                vcol[v] = 2 * cl + (v & 1);
+            } else {
+                vcol[v] = 8 * cl + ((v + 2 * rr) & 7);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            if (CPLX)
+                ipos[i] = ((i ^ rr) == 0) ? 2 * cl : 32 + 2 * cl;
+            else
+                ipos[i] = vcol[2 * i];
+        }
+        uint32_t ichunk[NI], ilow[NI];  // 16-byte chunk and byte of item i within a row
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            ichunk[i] = (uint32_t)(ipos[i] * 2) >> 4;
+            ilow[i] = (uint32_t)(ipos[i] * 2) & 15u;
+        }
         for (int j = 0; j < count && ok; ++j) {
             const int32_t *pd = pairs + 4 * q;
             const int k = pd[1] + pd[3];
@@ -439,12 +512,16 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
             const int64_t l0 = (int64_t)r * UD_M;
             const int rho = j % UD_RING;
             int64_t colx[NC];
-            int ex[NC];
+            int ex[NV];
 #pragma unroll
             for (int v = 0; v < NC; ++v) {
-                const int c = CPLX ? 2 * cl + v : 8 * cl + v;
+                const int c = CPLX ? 2 * cl + v : vcol[v];
                 colx[v] = c < k ? ud_gcol(pd, c) : -1;
-                ex[v] = colx[v] >= 0 ? cexp[colx[v]] : -1021;
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const int64_t cx = colx[CPLX ? (v & 1) : v];
+                ex[v] = cx >= 0 ? cexp[cx] : -1021;
             }
             if (j >= UD_RING) waitb(&S.r_empty[rho], (uint32_t)((j / UD_RING - 1) & 1));
             for (int p = 0; p < 4 && ok; ++p) {
@@ -465,8 +542,8 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                             if (CPLX) {
                                 double2 z = make_double2(0.0, 0.0);
                                 if (in) z = reinterpret_cast<const double2 *>(Gs)[colx[v] * ld + l];
-                                x[i][v] = z.x;       // real part: position 2c' + v
-                                x[i][v + 2] = z.y;   // imaginary part: position 32 + 2c' + v
+                                x[i][v] = rr ? z.y : z.x;      // first item: re (rr = 0) or im
+                                x[i][v + 2] = rr ? z.x : z.y;
                             } else {
                                 x[i][v] = in ? Gs[colx[v] * ld + l] : 0.0;
                             }
@@ -481,36 +558,54 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                         }
                         if (!ok) break;
                     }
+                    uint8_t *slot0 = sA + (size_t)((t0 - 1) % UD_ASLOTS) * UD_ATILE;
 #pragma unroll
                     for (int i = 0; i < HB; ++i) {
                         const int task = bw + UD_BLD * (hb * HB + i);
                         if (hb * HB + i >= TPW || task >= TASKS) break;
                         const int row = task * RPT + rr;  // row of the tile
-                        // row exponent: max over the row of exp(x) - e_a
-                        int mx = -100000;
+                        int rexp;
+                        if (p == 0) {
+                            // row exponent: max over the row of exp(x) - e_a
+                            int mx = -100000;
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            const unsigned long long mb = dg_mag_bits(x[i][v]);
-                            if (mb) mx = max(mx, dg_exp_of_bits(mb) - ex[CPLX ? (v & 1) : v]);
+                            for (int v = 0; v < NV; ++v) {
+                                const unsigned long long mb = dg_mag_bits(x[i][v]);
+                                if (mb) mx = max(mx, dg_exp_of_bits(mb) - ex[v]);
+                            }
+#pragma unroll
+                            for (int o = 1; o < (CPLX ? 16 : 8); o <<= 1)
+                                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                            rexp = mx == -100000 ? -1021 : mx;
+                            if (cl == 0) S.rexp[rho][row] = rexp;
+                        } else {
+                            rexp = S.rexp[rho][row];
                         }
+                        // complex: the value order differs between rr = 0 and 1, and
+                        // e_a is the same for the real and imaginary part of a column
+                        uint32_t w[NV];
 #pragma unroll
-                        for (int o = 1; o < (CPLX ? 16 : 8); o <<= 1)
-                            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                        const int rexp = mx == -100000 ? -1021 : mx;
-                        if (p == 0 && cl == 0) S.rexp[rho][row] = rexp;
-                        Fx84 f[NV];
+                        for (int v = 0; v < NV; ++v) w[v] = dg_window21(x[i][v], rexp + ex[v], p);
+                        const uint32_t rowbase = (uint32_t)row * 128u, x7 = (uint32_t)row & 7u;
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) f[v] = dg_fixed84(x[i][v], rexp + ex[CPLX ? (v & 1) : v]);
-                        for (int t = t0; t <= t1; ++t) {
-                            uint8_t *slot = sA + (size_t)((t - 1) % UD_ASLOTS) * UD_ATILE;
+                        for (int it = 0; it < NI; ++it) {
+                            const uint32_t off = rowbase + ((ichunk[it] ^ x7) << 4) + ilow[it];
+                            const bool n0 = __double_as_longlong(x[i][2 * it]) < 0;
+                            const bool n1 = __double_as_longlong(x[i][2 * it + 1]) < 0;
+                            const uint32_t bias = (n0 ? 0xE400u : 0x6400u) | ((n1 ? 0xE400u : 0x6400u) << 16);
+                            const uint32_t add = bias ^ 0x80008000u;
 #pragma unroll
-                            for (int v = 0; v < NV; v += 2) {
-                                // positions: complex re pair 2c', 2c'+1 (v = 0) and im pair
-                                // 32 + 2c', 33 + 2c' (v = 2); real 8c' + v, 8c' + v + 1
-                                const int pos = CPLX ? (v == 0 ? 2 * cl : 32 + 2 * cl) : 8 * cl + v;
-                                *reinterpret_cast<uint32_t *>(slot + sw128_off(row, pos * 2)) =
-                                    dg_pack2(dg_digit84(f[v], t), __double_as_longlong(x[i][v]) < 0,
-                                             dg_digit84(f[v + 1], t), __double_as_longlong(x[i][v + 1]) < 0);
+                            for (int dd = 0; dd < 3; ++dd) {
+                                if (t0 + dd > t1) break;
+                                const uint32_t d0 = (w[2 * it] >> (14 - 7 * dd)) & 127u;
+                                const uint32_t d1 = (w[2 * it + 1] >> (14 - 7 * dd)) & 127u;
+                                const uint32_t v = d0 | (d1 << 16) | bias;
+                                uint32_t h2;
+                                asm("add.rn.f16x2 %0, %1, %2;" : "=r"(h2) : "r"(v), "r"(add));
+                                // slot of digit t0 + dd: the ring position advances by one
+                                uint8_t *sl = slot0 + (size_t)dd * UD_ATILE;
+                                if (sl >= sA + (size_t)UD_ASLOTS * UD_ATILE) sl -= (size_t)UD_ASLOTS * UD_ATILE;
+                                *reinterpret_cast<uint32_t *>(sl + off) = h2;
                             }
                         }
                     }

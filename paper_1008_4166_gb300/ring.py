@@ -13,9 +13,11 @@ steps of the ordering table (`jjacobi_schedule`): process q keeps the block
 its next pair shares with its current one, and receives the other from the
 process holding it now.
 
-The pivot-pair work itself (Gram, Cholesky, inner J-Jacobi, update) is the
-caller's `pair_fn(i, j, block_i, block_j) -> rotations`, which transforms the
-two blocks in place: on a GPU it runs the library's kernels on device tensors.
+The pivot-pair work itself (Gram, Cholesky, inner J-Jacobi, update) is a
+`pair_fn(i, j, block_i, block_j) -> rotations` that transforms the two blocks
+in place; `library_pair_fn` builds one that runs the library's kernels on the
+GPU (the blocks may live on the host between steps, as the gloo transport
+needs, or on the device).
 
 Failure handling is on the host: every receive and every reduction is
 bounded by the process group's timeout; a rank that never joins, leaves, or
@@ -84,6 +86,52 @@ def transitions(tab: np.ndarray, tab_next: np.ndarray) -> List[List[Transition]]
                                   recv_from=holder[recv]))
         out.append(row)
     return out
+
+
+def library_pair_fn(J, offs, sizes, gemm: int = 0, device="cuda", tol: float = 0.0,
+                    inner_max_sweeps: int = 30):
+    """A pair_fn running one pivot pair through the library's kernels: the Gram
+    (3.6), the Cholesky factor and the inner J-Jacobi with W accumulated (3.12)
+    (full block, Sec. 3.3), and the update (2.9), on one device.
+
+    J: the signs of the work columns (J-sorted order); offs/sizes: the block
+    partition (3.3); gemm: jj_gemm of the contractions. The pivot [X_i X_j] is
+    copied to the device in column-major order, transformed there, and copied
+    back into the caller's blocks (host or device tensors)."""
+    import torch
+
+    from . import jjacobi as jj
+
+    Jv = np.asarray(J, dtype=np.int8)
+    g_gram = jj.JJ_GEMM_FP64 if gemm == jj.JJ_GEMM_FP64 else jj.JJ_GEMM_OZAKI_FP16
+    g_upd = jj.JJ_GEMM_OZAKI_FP16 if gemm == jj.JJ_GEMM_OZAKI_FP16 else jj.JJ_GEMM_FP64
+
+    def fn(i, j, Xi, Xj):
+        ni, nj = int(sizes[i]), int(sizes[j])
+        k = ni + nj
+        X = torch.cat([Xi, Xj], dim=1).to(device)
+        m = X.shape[0]
+        cplx = X.is_complex()
+        G = X.t().contiguous().t()  # m x k, column-major (ld = m)
+        dt = jj.JJ_C128 if cplx else jj.JJ_F64
+        E = 2 if cplx else 1
+        pairs = torch.tensor([[0, ni, ni, nj]], dtype=torch.int32, device=device)
+        A = torch.zeros(k * k * E, dtype=torch.float64, device=device)
+        W = torch.zeros_like(A)
+        cols = np.r_[offs[i]:offs[i] + ni, offs[j]:offs[j] + nj]
+        Jd = torch.from_numpy(np.ascontiguousarray(Jv[cols])).to(device)
+        cnt = torch.zeros(8, dtype=torch.int64, device=device)
+        jj.jjk_gram(dt, g_gram, G, m, m, pairs, 1, A, k)
+        jj.jjk_inner(dt, A, W, k, pairs, 1, Jd, tol, inner_max_sweeps, 0, cnt)
+        jj.jjk_update(dt, g_upd, G, G, m, m, pairs, 1, W, k)
+        c = cnt.cpu()
+        if int(c[2]) != 0:
+            raise RuntimeError(f"pair ({i}, {j}): device error flags {int(c[2])}")
+        Xi.copy_(G[:, :ni])
+        Xj.copy_(G[:, ni:])
+        return int(c[0])
+
+    return fn
 
 
 def ring_sweeps(pg_rank: int, world: int, blocks: Dict[int, "object"], sizes: List[int],
