@@ -94,47 +94,46 @@ __device__ __forceinline__ int64_t ud_gcol(const int32_t *pd, int c) {
     return c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
 }
 
+// Out of the normal range (never for the method's inputs): ldexp, kept out of
+// line so that the common path carries none of its instructions.
+__device__ __noinline__ double ud_scaled_slow(unsigned long long mant, int e, bool neg) {
+    const double v = ldexp((double)mant, e);
+    return neg ? -v : v;
+}
+
 // (hi:lo) as a two's-complement 128-bit integer times 2^e, rounded to the
-// nearest double (ties to even): integer operations only, ldexp outside the
-// normal range.
+// nearest double (ties to even): integer operations only.
 __device__ __forceinline__ double i128_scaled_to_double(long long hi, unsigned long long lo, int e) {
-    const bool neg = hi < 0;
-    unsigned long long h = (unsigned long long)hi, l = lo;
-    if (neg) {
-        l = ~l + 1ull;
-        h = ~h + (l == 0ull ? 1ull : 0ull);
-    }
-    if (h == 0ull && l == 0ull) return 0.0;
-    unsigned long long m;
-    bool sticky;
-    int shift;  // |value| ~ m 2^(e + shift), leading one of m at bit 63
-    if (h != 0ull) {
-        const int lz = __clzll((long long)h);
-        m = lz ? (h << lz) | (l >> (64 - lz)) : h;
-        sticky = lz ? (l << lz) != 0ull : l != 0ull;
-        shift = 64 - lz;
+    const unsigned long long sg = (unsigned long long)(hi >> 63);  // all ones when negative
+    unsigned long long h = (unsigned long long)hi ^ sg, l = lo ^ sg;
+    const unsigned long long l2 = l + (sg & 1ull);  // + 1 when negative
+    h += (l2 < l) ? 1ull : 0ull;
+    l = l2;
+    if ((h | l) == 0ull) return 0.0;
+    const int lz = h ? __clzll((long long)h) : 64 + __clzll((long long)l);  // 0..127
+    unsigned long long top, rest;
+    if (lz >= 64) {
+        top = l << (lz - 64);
+        rest = 0ull;
+    } else if (lz == 0) {
+        top = h;
+        rest = l;
     } else {
-        const int lz = __clzll((long long)l);
-        m = l << lz;
-        sticky = false;
-        shift = -lz;
+        top = (h << lz) | (l >> (64 - lz));
+        rest = l << lz;
     }
-    unsigned long long mant = m >> 11;
-    const unsigned long long rem = m & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (sticky || (mant & 1ull)))) {
-        if (++mant == (1ull << 53)) {
-            mant >>= 1;
-            ++shift;
-        }
+    unsigned long long mant = top >> 11;  // 53 bits, leading one at bit 52
+    const unsigned long long rem = top & 0x7FFull;
+    mant += (rem > 0x400ull || (rem == 0x400ull && (rest != 0ull || (mant & 1ull)))) ? 1ull : 0ull;
+    int ex = 127 - lz + e;  // exponent of the leading bit
+    if (mant >> 53) {
+        mant >>= 1;
+        ++ex;
     }
-    const int biased = 63 + e + shift + 1023;
-    if (biased < 1 || biased > 2046) {
-        const double v = ldexp((double)mant, e + shift + 11);
-        return neg ? -v : v;
-    }
-    const unsigned long long bits = ((unsigned long long)neg << 63) |
-                                    ((unsigned long long)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
+    const int biased = ex + 1023;
+    if (__builtin_expect(biased < 1 || biased > 2046, 0)) return ud_scaled_slow(mant, ex - 52, sg != 0ull);
+    return __longlong_as_double((long long)((sg << 63) | ((unsigned long long)biased << 52) |
+                                            (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 template <bool CPLX>
@@ -558,7 +557,10 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                         }
                         if (!ok) break;
                     }
-                    uint8_t *slot0 = sA + (size_t)((t0 - 1) % UD_ASLOTS) * UD_ATILE;
+                    uint8_t *slotp[3];  // slots of the pass's digits t0, t0 + 1, t0 + 2
+#pragma unroll
+                    for (int dd = 0; dd < 3; ++dd)
+                        slotp[dd] = sA + (size_t)((t0 - 1 + dd) % UD_ASLOTS) * UD_ATILE;
 #pragma unroll
                     for (int i = 0; i < HB; ++i) {
                         const int task = bw + UD_BLD * (hb * HB + i);
@@ -602,10 +604,7 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                                 const uint32_t v = d0 | (d1 << 16) | bias;
                                 uint32_t h2;
                                 asm("add.rn.f16x2 %0, %1, %2;" : "=r"(h2) : "r"(v), "r"(add));
-                                // slot of digit t0 + dd: the ring position advances by one
-                                uint8_t *sl = slot0 + (size_t)dd * UD_ATILE;
-                                if (sl >= sA + (size_t)UD_ASLOTS * UD_ATILE) sl -= (size_t)UD_ASLOTS * UD_ATILE;
-                                *reinterpret_cast<uint32_t *>(sl + off) = h2;
+                                *reinterpret_cast<uint32_t *>(slotp[dd] + off) = h2;
                             }
                         }
                     }
