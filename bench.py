@@ -216,7 +216,7 @@ def bench_config(args, P, world: int = 1) -> dict:
     name = re.sub(r"_b\d+$", f"_b{args.block_width}", args.workload)
     return {"workload": name, "recipe": args.workload, "m": P.m, "n": P.n,
             "block_width": args.block_width, "gemm": args.gemm,
-            "update_digits": (args.digits or 12) if args.gemm == "ozaki" else None,
+            "update_digits": (args.digits or 12) if args.gemm == "ozaki" and args.block_width else None,
             "strategy": args.strategy, "order": "round_robin",
             "l2": "inputs larger than L2 (G = 256 MiB; every step reads and writes it)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
@@ -291,6 +291,17 @@ def kernel_roofline(jj, P, times, info, gemm_gram_digits, gemm_upd_digits, peaks
     cplx = P.is_complex
     mac = 8.0 if cplx else 2.0
     m = P.m
+    if not info["nbl"]:
+        # plain form: one dot product and one column-pair rotation (3 m MACs)
+        # for every column pair of every sweep, on the FP64 pipe
+        ms, launches = times["plain_step"]
+        work = info["sweeps"] * P.n * (P.n - 1) / 2 * 3.0 * m * mac
+        achieved = work / (ms * 1e-3) / 1e12
+        return {"kernel": "plain_step_kernel", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64: 152 SMs x 2 FMA/clk/SM x 2 flops x 2070 MHz (derived; 1.19 measured)",
+                "ms_per_launch": ms / max(launches, 1), "launches": launches,
+                "family_ms": {"plain_step": ms}}
     k = 2.0 * P.n / info["nbl"]
     K2 = 2 * k if cplx else k
     upd_digits = info.get("update_digits", 12)
@@ -394,9 +405,12 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     info = infos[-1]
-    flops = blocked_flops(n, m, cplx, info)
+    if info["nbl"]:
+        flops = blocked_flops(n, m, cplx, info)
+        flops_all = blocked_flops_all_pairs(n, m, cplx, info)
+    else:  # plain form
+        flops = flops_all = plain_flops(n, m, cplx, info["sweeps"])
     value = flops * world / (ms * 1e-3) / 1e9
-    flops_all = blocked_flops_all_pairs(n, m, cplx, info)
     launches = sum(x["kernel_launches"] + 1 for x in infos)  # + extraction kernel
     lam_blocked = lam.cpu().numpy().copy()
 
