@@ -218,6 +218,7 @@ def bench_config(args, P, world: int = 1) -> dict:
             "block_width": args.block_width, "gemm": args.gemm,
             "update_digits": (args.digits or 12) if args.gemm == "ozaki" and args.block_width else None,
             "strategy": args.strategy, "order": "round_robin",
+            "pivot_factor": getattr(args, "pivot_factor", "cholesky"),
             "l2": "inputs larger than L2 (G = 256 MiB; every step reads and writes it)",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
@@ -371,8 +372,10 @@ def run_ours(args):
         Gw = torch.empty_like(G0)
         lam = torch.empty(n, dtype=torch.float64, device="cuda")
     strat = {"full": jj.JJ_FULL_BLOCK, "oriented": jj.JJ_BLOCK_ORIENTED}[args.strategy]
+    pf = jj.JJ_PIVOT_SPECIAL if args.pivot_factor == "special" else jj.JJ_PIVOT_CHOLESKY
     h = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
-                  block_strategy=strat, max_sweeps=args.max_sweeps, ozaki_slices=args.digits)
+                  block_strategy=strat, max_sweeps=args.max_sweeps, ozaki_slices=args.digits,
+                  pivot_factor=pf)
     ok = (jj.JJ_OK, jj.JJ_NOT_CONVERGED) if args.max_sweeps else (jj.JJ_OK,)
 
     def step():
@@ -430,7 +433,7 @@ def run_ours(args):
     # dominant kernel's roofline
     hp_ = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
                     profile=True, max_sweeps=args.profile_sweeps, block_strategy=strat,
-                    ozaki_slices=args.digits)
+                    ozaki_slices=args.digits, pivot_factor=pf)
     with torch.cuda.stream(stream):
         Gw.copy_(G0)
         pinfo_ = hp_.jjacobi_solve(Gw, Gw.stride(1), P.J, allow=(jj.JJ_OK, jj.JJ_NOT_CONVERGED))
@@ -716,6 +719,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-width", type=int, default=16)
     ap.add_argument("--gemm", default="ozaki", choices=["hybrid", "ozaki", "fp64"])
+    ap.add_argument("--pivot-factor", default="cholesky", choices=["cholesky", "special"],
+                    help="full-block pivot factor: Cholesky of the pivot, or (3.9)-(3.11)")
     ap.add_argument("--digits", type=int, default=0,
                     help="digits per operand of the split-precision update (0: 12)")
     ap.add_argument("--strategy", default="oriented", choices=["oriented", "full"])

@@ -88,6 +88,20 @@ typedef enum {
  *                      to 128 real columns. */
 typedef enum { JJ_FULL_BLOCK = 0, JJ_BLOCK_ORIENTED = 1 } jj_block_strategy;
 
+/* How the full-block inner solve factors a pivot A_P = R^* R (Sec. 3.3):
+ *   JJ_PIVOT_CHOLESKY  the Cholesky factorization of the whole pivot (3.8);
+ *   JJ_PIVOT_SPECIAL   the structure (3.7): at the start of every sweep each
+ *                      block's own Gram A_ii is diagonalized (the one-sided
+ *                      method on the block's columns), so that every pivot has
+ *                      diagonal diagonal blocks Lambda_ii, Lambda_jj (their
+ *                      off-diagonal entries, at most tol sqrt(a_rr a_ss), are
+ *                      taken as zero) and R_ii = sqrt(Lambda_ii) (3.9),
+ *                      R_ij = R_ii^{-1} A_ij (3.10), R_jj the Cholesky factor of
+ *                      Lambda_jj - R_ij^* R_ij (3.11). Two-level full-block
+ *                      solves of single problems, pivots of up to 96 complex or
+ *                      128 real columns. */
+typedef enum { JJ_PIVOT_CHOLESKY = 0, JJ_PIVOT_SPECIAL = 1 } jj_pivot_factor;
+
 /* block_width value that lets the library pick the block width: at the first
  * solve of the handle, one sweep of every candidate width (powers of two from
  * 8 up to the widest pivot the contraction form takes, at most n/4) is timed on
@@ -125,6 +139,7 @@ typedef struct {
                                   (sweeps then run without graph capture); see
                                   jjacobi_kernel_times */
     int32_t block_strategy;    /* jj_block_strategy (blocked form) */
+    int32_t pivot_factor;      /* jj_pivot_factor (full-block two-level form) */
 } jj_params;
 
 typedef struct {

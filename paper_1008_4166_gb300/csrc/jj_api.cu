@@ -32,6 +32,9 @@ struct Plan {
     int steps = 0, maxnp = 0, kmax = 0, slots = 0;
     std::vector<int> step_np, step_slot0;
     int block_param = 0;                // block_width the plan was built with
+    // special pivot factor (3.9)-(3.11): the pass over every block's own Gram
+    // at the start of a sweep (one single-block "pair" per block)
+    int diag_np = 0, diag_slot0 = 0;
 };
 
 // Three-level form (Sec. 5.1, 3F): per outer step, the inner blocked method
@@ -484,6 +487,24 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
         P.slots += np;
         P.maxnp = std::max(P.maxnp, np);
     }
+    if (c->p.pivot_factor == JJ_PIVOT_SPECIAL && c->p.block_width != 0) {
+        if (batched || count != 1 || c->p.block_strategy != JJ_FULL_BLOCK ||
+            c->p.inner_block_width > 0)
+            return JJ_INVALID_ARG;
+        const int p = P.order[0];
+        P.diag_slot0 = P.slots;
+        P.diag_np = P.nbl[p];
+        for (int l = 0; l < P.nbl[p]; ++l) {
+            tab.push_back((int32_t)(P.coff[p] + offs[p][l]));
+            tab.push_back(sizes[p][l]);
+            tab.push_back((int32_t)(P.coff[p] + offs[p][l]));  // second block: none (size 0)
+            tab.push_back(0);
+            rows.push_back((int32_t)ms[p]);
+            prob.push_back(p);
+        }
+        P.slots += P.diag_np;
+        P.maxnp = std::max(P.maxnp, P.diag_np);
+    }
     c->plan_batched = batched;
     // the pair kernels index pairs with blockIdx.y (at most 65535 per launch)
     if (P.maxnp > 65535) return JJ_INVALID_ARG;
@@ -498,6 +519,7 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
     if (c->p.block_strategy == JJ_BLOCK_ORIENTED && !three &&
         !inner_single_pass_supported(c->cplx, P.kmax))
         return JJ_INVALID_ARG;
+    if (P.diag_np > 0 && !inner_single_pass_supported(c->cplx, P.kmax)) return JJ_INVALID_ARG;
     c->ozaki = oz_ok && c->p.gemm != JJ_GEMM_FP64;
     c->ozaki_update = c->ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
     c->oz_slices_update = ozaki_default_slices(false);
@@ -606,8 +628,11 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
         JJ_CUDA(cudaGetLastError());
         ++L;
         const int64_t mrows = c->plan_batched ? P.ldw : c->m;
-        for (int t = 0; t < P.steps; ++t) {
-            const int np = P.step_np[t], s0 = P.step_slot0[t];
+        // t = -1: the pass over every block's own Gram that opens a sweep of the
+        // special pivot factor (3.9)-(3.11), which needs diagonal A_ii
+        for (int t = P.diag_np > 0 ? -1 : 0; t < P.steps; ++t) {
+            const bool diag = t < 0;
+            const int np = diag ? P.diag_np : P.step_np[t], s0 = diag ? P.diag_slot0 : P.step_slot0[t];
             if (np == 0) continue;
             const int32_t *pr = c->d_pairs + (size_t)s0 * 4;
             StepCtl ctl;
@@ -650,7 +675,7 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
             const int pass = c->p.block_strategy == JJ_BLOCK_ORIENTED ? (t == 0 ? 2 : 1) : 0;
             JJ_CUDA(launch_inner(c->cplx, c->Ablk, c->Wblk, P.kmax, pr, np, c->d_Jw, c->tol,
                                  c->inner_max_sweeps, c->p.inner_block_width, c->d_cnt, st, ctl,
-                                 ud, pass));
+                                 ud, pass, P.diag_np > 0 && !diag));
             if (mark(2)) return JJ_CUDA_ERROR;
             if (c->ozaki_update)
                 JJ_CUDA(launch_update_digits(c->cplx, c->Gw, c->Gw, P.ldw, mrows, pr, np, P.kmax,
@@ -1205,6 +1230,7 @@ void jjacobi_default_params(jj_params *p, int64_t m, int64_t n, int32_t dtype) {
     p->max_sweeps = 60;
     p->inner_max_sweeps = 30;
     p->cuda_stream = nullptr;
+    p->pivot_factor = JJ_PIVOT_CHOLESKY;
 }
 
 const char *jjacobi_status_string(int status) {
@@ -1252,6 +1278,7 @@ int jjacobi_create(jj_handle *h, const jj_params *p) {
         (p->order != JJ_ORDER_ROUND_ROBIN && p->order != JJ_ORDER_MODULUS) ||
         (p->gemm < JJ_GEMM_FP64 || p->gemm > JJ_GEMM_AUTO) || p->ozaki_slices < 0 ||
         (p->block_strategy != JJ_FULL_BLOCK && p->block_strategy != JJ_BLOCK_ORIENTED) ||
+        (p->pivot_factor != JJ_PIVOT_CHOLESKY && p->pivot_factor != JJ_PIVOT_SPECIAL) ||
         p->n > (int64_t)1 << 30)
         return JJ_INVALID_ARG;
     jj_ctx *c = new jj_ctx();

@@ -357,7 +357,7 @@ template <bool CPLX, int ROWS, bool OFFD>
 __global__ void __launch_bounds__(ST) inner_smem_kernel(
     double *__restrict__ A, double *__restrict__ Wb, int kmax, const int32_t *__restrict__ pairs,
     const int8_t *__restrict__ J, double tol, int max_sweeps,
-    unsigned long long *__restrict__ counters, StepCtl ctl, UpdDigits ud, int pass) {
+    unsigned long long *__restrict__ counters, StepCtl ctl, UpdDigits ud, int pass, int special) {
     constexpr int E = CPLX ? 2 : 1;
     extern __shared__ double2 smem4[];
     double *sm = reinterpret_cast<double *>(smem4);
@@ -387,8 +387,58 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
     }
     if (tid == 0) s_fail = 0;
     __syncthreads();
+    int j0 = 0;  // first column of the right-looking Cholesky below
+    if (special && pd[3] > 0) {
+        // A pivot of the form (3.7), its diagonal blocks diagonal (their
+        // off-diagonal entries, at most tol sqrt(a_rr a_ss), are taken as zero):
+        // R_ii = sqrt(Lambda_ii) (3.9), R_ij = R_ii^{-1} A_ij (3.10), and the
+        // trailing block gets Lambda_jj - R_ij^* R_ij (3.11), whose Cholesky
+        // factor R_jj the loop below computes.
+        const int ni = pd[1], nj = pd[3];
+        for (int a = tid; a < ni; a += ST) {
+            const double ajj = R[((size_t)a * ldr + a) * E];
+            const bool ok = ajj > 0.0 && isfinite(ajj);
+            dsh[a] = ok ? sqrt(ajj) : 1.0;
+            if (!ok) s_fail = 1;
+        }
+        __syncthreads();
+        if (!s_fail) {
+            for (int t = tid; t < ni * k; t += ST) {
+                const int r = t % ni, cc = t / ni;
+                double *dst = R + ((size_t)cc * ldr + r) * E;
+                if (cc < ni) {
+                    dst[0] = r == cc ? dsh[r] : 0.0;
+                    if (CPLX) dst[1] = 0.0;
+                } else {
+                    const double inv = 1.0 / dsh[r];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) dst[e] *= inv;
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < nj * nj; t += ST) {
+                const int c1 = ni + t % nj, c2 = ni + t / nj;
+                if (c1 > c2) continue;
+                double sr = c1 == c2 ? R[((size_t)c1 * ldr + c1) * E] : 0.0, si = 0.0;
+                for (int r = 0; r < ni; ++r) {
+                    if (CPLX) {
+                        const double ur = R[((size_t)c1 * ldr + r) * 2], ui = R[((size_t)c1 * ldr + r) * 2 + 1];
+                        const double vr = R[((size_t)c2 * ldr + r) * 2], vi = R[((size_t)c2 * ldr + r) * 2 + 1];
+                        sr -= fma(ur, vr, ui * vi);
+                        si -= fma(ur, vi, -ui * vr);
+                    } else {
+                        sr -= R[(size_t)c1 * ldr + r] * R[(size_t)c2 * ldr + r];
+                    }
+                }
+                R[((size_t)c2 * ldr + c1) * E] = sr;
+                if (CPLX) R[((size_t)c2 * ldr + c1) * E + 1] = si;
+            }
+        }
+        __syncthreads();
+        j0 = s_fail ? k : ni;
+    }
     // Cholesky A = R^* R (upper), right-looking
-    for (int j = 0; j < k; ++j) {
+    for (int j = j0; j < k; ++j) {
         if (tid == 0) {
             const double ajj = R[((size_t)j * ldr + j) * E];
             if (!(ajj > 0.0) || !isfinite(ajj)) {
@@ -732,7 +782,7 @@ cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
                          int npairs, const int8_t *J, double tol, int inner_max_sweeps,
                          int inner_block, unsigned long long *counters, cudaStream_t st,
-                         StepCtl ctl, UpdDigits ud, int pass) {
+                         StepCtl ctl, UpdDigits ud, int pass, bool special) {
     (void)inner_block;
     if (npairs <= 0) return cudaSuccess;
     // Shared-memory resident form when R and W fit (227 KB per block).
@@ -744,7 +794,8 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)smb);                                       \
         if (e != cudaSuccess) return e;                                                       \
-        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl, ud, pass); \
+        kern<<<npairs, ST, smb, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl, ud, pass, \
+                                      special ? 1 : 0);                                        \
         return cudaGetLastError();                                                            \
     } while (0)
         const int rows = (kmax + 31) / 32;
@@ -760,7 +811,7 @@ cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_
         }
 #undef JJ_INNER_SMEM
     }
-    if (pass != 0) return cudaErrorNotSupported;  // single passes need the shared-memory form
+    if (pass != 0 || special) return cudaErrorNotSupported;  // single passes and (3.9)-(3.11) need the shared-memory form
     const size_t sh = (size_t)kmax * sizeof(double) + (size_t)kmax * sizeof(int);
     if (cplx)
         inner_kernel<true><<<npairs, IT, sh, st>>>(A, W, kmax, pairs, J, tol, inner_max_sweeps, counters, ctl);

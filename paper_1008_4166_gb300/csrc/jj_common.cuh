@@ -204,7 +204,8 @@ cudaError_t launch_gram(bool cplx, int gemm, const double *G, int64_t ld, int64_
 cudaError_t launch_inner(bool cplx, double *A, double *W, int kmax, const int32_t *pairs,
                          int npairs, const int8_t *J, double tol, int inner_max_sweeps,
                          int inner_block, unsigned long long *counters, cudaStream_t st,
-                         StepCtl ctl = StepCtl(), UpdDigits ud = UpdDigits(), int pass = 0);
+                         StepCtl ctl = StepCtl(), UpdDigits ud = UpdDigits(), int pass = 0,
+                         bool special = false);
 cudaError_t launch_update(bool cplx, int gemm, const double *Gs, double *Gd, int64_t ld,
                           int64_t m, const int32_t *pairs, int npairs, const double *W,
                           int kmax, cudaStream_t st, StepCtl ctl = StepCtl());

@@ -20,6 +20,7 @@ JJ_ORDER_ROUND_ROBIN, JJ_ORDER_MODULUS = 0, 1
 JJ_GEMM_FP64, JJ_GEMM_OZAKI_FP16, JJ_GEMM_OZAKI_GRAM, JJ_GEMM_AUTO = 0, 1, 2, 3
 JJ_BLOCK_AUTO = -1
 JJ_FULL_BLOCK, JJ_BLOCK_ORIENTED = 0, 1
+JJ_PIVOT_CHOLESKY, JJ_PIVOT_SPECIAL = 0, 1
 (JJ_OK, JJ_INVALID_ARG, JJ_NOT_CONVERGED, JJ_NOT_POSDEF, JJ_NONFINITE, JJ_DEVICE_TIMEOUT,
  JJ_CUDA_ERROR, JJ_NOT_SOLVED) = range(8)
 
@@ -41,7 +42,7 @@ class jj_params(ctypes.Structure):
                 ("ozaki_slices", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("inner_max_sweeps", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
-                ("block_strategy", ctypes.c_int32)]
+                ("block_strategy", ctypes.c_int32), ("pivot_factor", ctypes.c_int32)]
 
 
 class jj_info(ctypes.Structure):
@@ -204,7 +205,8 @@ class Handle:
                  inner_block_width: int = 0, order: int = JJ_ORDER_ROUND_ROBIN,
                  gemm: int = JJ_GEMM_FP64, tol: float = 0.0, max_sweeps: int = 0,
                  inner_max_sweeps: int = 0, ozaki_slices: int = 0, stream=None,
-                 profile: bool = False, block_strategy: int = JJ_FULL_BLOCK):
+                 profile: bool = False, block_strategy: int = JJ_FULL_BLOCK,
+                 pivot_factor: int = JJ_PIVOT_CHOLESKY):
         lib = load()
         p = jjacobi_default_params(m, n, dtype)
         p.block_width = block_width
@@ -222,6 +224,7 @@ class Handle:
         p.cuda_stream = sp
         p.profile = 1 if profile else 0
         p.block_strategy = block_strategy
+        p.pivot_factor = pivot_factor
         self.params = p
         self.h = ctypes.c_void_p()
         _check(lib.jjacobi_create(ctypes.byref(self.h), ctypes.byref(p)), "jjacobi_create")

@@ -99,7 +99,7 @@ def test_create_rejects_bad_params(jj):
         assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(p)) == jj.JJ_INVALID_ARG
         assert not h
     for field, bad in (("order", 2), ("gemm", 4), ("gemm", -1), ("block_strategy", 2),
-                       ("inner_block_width", -1), ("ozaki_slices", -1)):
+                       ("inner_block_width", -1), ("ozaki_slices", -1), ("pivot_factor", 2)):
         q = jj.jjacobi_default_params(8, 8, jj.JJ_F64)
         setattr(q, field, bad)
         assert lib.jjacobi_create(ctypes.byref(h), ctypes.byref(q)) == jj.JJ_INVALID_ARG, field

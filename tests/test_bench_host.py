@@ -94,6 +94,7 @@ def test_reference_arm_line_matches_the_measured_arm_config():
         gemm = "ozaki"
         digits = 0
         strategy = "oriented"
+        pivot_factor = "cholesky"
 
     class _P:
         m = n = 4096
