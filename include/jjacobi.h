@@ -235,6 +235,30 @@ const char *jjacobi_status_string(int status);
  * launches (host, 8 int64, may be NULL): the matching launch counts. */
 int jjacobi_kernel_times(jj_handle h, double *times_ms, int64_t *launches);
 
+/* Front end (Sec. 2.2, (2.5)): a factor G and signs J with H = G J G^* for a
+ * Hermitian H (device, n x n, column-major, ldh >= n, both triangles; the
+ * dtype's element type; not modified). Symmetric Gaussian elimination with
+ * complete (Bunch-Parlett) pivoting, P H P^T = M D M^*: at each step mu0 is
+ * the largest modulus of the Schur complement and mu1 the largest on its
+ * diagonal; a 1x1 pivot at the largest diagonal entry when
+ * mu1 >= (1 + sqrt 17)/8 mu0, else the 2x2 pivot on the off-diagonal entry
+ * of modulus mu0 (ties: the first entry in row-major order). Elimination stops
+ * when mu0 falls to rank_tol times the largest modulus of H (rank_tol <= 0:
+ * 16 n 2^-53); r is the number of eliminated columns. Each block of D is
+ * diagonalized (a 2x2 block as Q diag(delta) Q^*, delta ascending), the
+ * columns of M are scaled by |delta|^(1/2), and the rows are returned to H's
+ * order: G (device, column-major with ldg >= n, at least n columns; the
+ * first r are written) has full column rank, and J (host, n entries; the
+ * first r are written) holds sign(delta). perm (host, n, may be NULL) receives P (row i of P H P^T is
+ * row perm[i] of H), pivot_size (host, n, may be NULL) 1 or 2 at the first
+ * column of each pivot and 0 elsewhere, rank (host) r. The zero eigenvalues
+ * of a singular H (n - r of them) are not completed here. Works on the given
+ * stream and synchronizes it; scratch from the stream-ordered allocator.
+ * JJ_DEVICE_TIMEOUT if a grid-wide wait of the elimination ran out. */
+int jjacobi_factor(int32_t dtype, const void *H, int64_t ldh, int64_t n, double rank_tol, void *G,
+                   int64_t ldg, int8_t *J, int32_t *perm, int8_t *pivot_size, int64_t *rank,
+                   void *stream);
+
 /* Bound, in nanoseconds of wall-clock time, of every device-side wait in this
  * handle's tensor-core kernels (an mbarrier wait for a product, a copy or a
  * pipeline stage; the kernels' failure path for a barrier nothing arrives at).

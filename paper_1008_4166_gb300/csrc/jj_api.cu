@@ -1258,6 +1258,17 @@ int jjacobi_kernel_times(jj_handle c, double *times_ms, int64_t *launches) {
     return JJ_OK;
 }
 
+int jjacobi_factor(int32_t dtype, const void *H, int64_t ldh, int64_t n, double rank_tol, void *G,
+                   int64_t ldg, int8_t *J, int32_t *perm, int8_t *pivot_size, int64_t *rank,
+                   void *stream) {
+    if (rank) *rank = 0;
+    if ((dtype != JJ_F64 && dtype != JJ_C128) || !H || !G || !J || n < 1 || n > 65536 || ldh < n || ldg < n)
+        return JJ_INVALID_ARG;
+    const double tol = rank_tol > 0.0 ? rank_tol : 16.0 * (double)n * 1.1102230246251565404e-16;
+    return frontend_factor(dtype == JJ_C128, (const double *)H, ldh, (int)n, tol, (double *)G, ldg,
+                           J, perm, pivot_size, rank, 2000000000ull, (cudaStream_t)stream);
+}
+
 int jjacobi_set_wait_limit(jj_handle c, int64_t ns) {
     if (!c) return JJ_INVALID_ARG;
     const unsigned long long v = ns > 0 ? (unsigned long long)ns : 2000000000ull;

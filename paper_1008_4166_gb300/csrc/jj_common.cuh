@@ -319,6 +319,11 @@ cudaError_t launch_three_finish(bool cplx, const double *X, int64_t ldx, int kma
                                 const unsigned long long *inner_rot, const int32_t *fail,
                                 unsigned long long *counters, cudaStream_t st, StepCtl ctl);
 
+// Front end H -> (G, J) (jj_frontend.cu); returns a jj_status.
+int frontend_factor(bool cplx, const double *H, int64_t ldh, int n, double rank_tol, double *G,
+                    int64_t ldg, int8_t *J_host, int32_t *perm_host, int8_t *psize_host,
+                    int64_t *rank_host, uint64_t wait_ns, cudaStream_t st);
+
 // Host-side ordering tables (jj_schedule.cpp).
 int schedule_pairs(int nbl, int order, int sweep, int32_t *pairs);
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "jjacobi_default_params", "jjacobi_create", "jjacobi_solve", "jjacobi_extract",
     "jjacobi_solve_host", "jjacobi_solve_batched", "jjacobi_destroy",
     "jjacobi_status_string", "jjacobi_version", "jjacobi_schedule", "jjacobi_kernel_times",
-    "jjacobi_set_wait_limit",
+    "jjacobi_set_wait_limit", "jjacobi_factor",
     "jjk_column_norms", "jjk_plain_step", "jjk_gram", "jjk_inner", "jjk_update", "jjk_extract",
     "jjk_gram_noalloc",
 ]
@@ -91,6 +91,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "jjacobi_schedule": (i32, [i32, i32, i32, vp]),
         "jjacobi_kernel_times": (ctypes.c_int, [vp, vp, vp]),
         "jjacobi_set_wait_limit": (ctypes.c_int, [vp, i64]),
+        "jjacobi_factor": (ctypes.c_int, [i32, vp, i64, i64, dbl, vp, i64, vp, vp, vp, vp, vp]),
         "jjk_column_norms": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, vp]),
         "jjk_plain_step": (ctypes.c_int, [i32, vp, i64, i64, i64, vp, i32, vp, vp, dbl, vp, vp]),
         "jjk_gram": (ctypes.c_int, [i32, i32, vp, i64, i64, vp, i32, vp, i32, vp]),
@@ -331,6 +332,28 @@ class Handle:
 # ---------------------------------------------------------------------------
 # Building blocks (include/jjacobi_kernels.h)
 # ---------------------------------------------------------------------------
+
+def jjacobi_factor(H, rank_tol: float = 0.0, stream=None):
+    """H = G J G^* (Sec. 2.2): returns (G, J, perm, pivot_size, rank) with G a
+    device tensor n x r (column-major), J, perm, pivot_size numpy arrays."""
+    import torch
+
+    n = H.shape[0]
+    if H.shape != (n, n) or not H.is_cuda:
+        raise ValueError("H must be a square CUDA tensor")
+    dt = JJ_C128 if H.is_complex() else JJ_F64
+    Hc = H.t().contiguous().t()  # column-major
+    G = torch.zeros((n, n), dtype=H.dtype, device=H.device).t()  # column-major n x n
+    J = np.zeros(n, dtype=np.int8)
+    perm = np.zeros(n, dtype=np.int32)
+    psize = np.zeros(n, dtype=np.int8)
+    r = ctypes.c_int64(0)
+    _check(load().jjacobi_factor(dt, _ptr(Hc), n, n, float(rank_tol), _ptr(G), n, J.ctypes.data,
+                                 perm.ctypes.data, psize.ctypes.data, ctypes.byref(r),
+                                 _stream_ptr(stream)), "jjacobi_factor")
+    rr = int(r.value)
+    return G[:, :rr], J[:rr], perm, psize[:rr], rr
+
 
 def jjk_column_norms(dtype, G, ld, m, n, d, stream=None):
     _check(load().jjk_column_norms(dtype, _ptr(G), ld, m, n, _ptr(d), _stream_ptr(stream)),
