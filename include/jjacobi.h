@@ -66,7 +66,9 @@ typedef enum { JJ_ORDER_ROUND_ROBIN = 0, JJ_ORDER_MODULUS = 1 } jj_order;
  *                       strongly graded inputs;
  *   JJ_GEMM_OZAKI_GRAM  the Gram as digit products, the update in FP64;
  *   JJ_GEMM_AUTO        JJ_GEMM_OZAKI_GRAM when the pivot fits the digit
- *                       kernels (real pivot width <= 64), else FP64. */
+ *                       kernels, else FP64.
+ * The digit kernels take real pivot widths (2 kmax complex, kmax real) up to
+ * 256, as 64 x 64 tiles above 64. */
 typedef enum {
     JJ_GEMM_FP64 = 0,
     JJ_GEMM_OZAKI_FP16 = 1,
@@ -104,7 +106,7 @@ typedef enum { JJ_PIVOT_CHOLESKY = 0, JJ_PIVOT_SPECIAL = 1 } jj_pivot_factor;
 
 /* block_width value that lets the library pick the block width: at the first
  * solve of the handle, one sweep of every candidate width (powers of two from
- * 8 up to the widest pivot the contraction form takes, at most n/4) is timed on
+ * 8 up to 32 for the digit forms and 64 for FP64, at most n/4) is timed on
  * a scratch copy of the input and the fastest is kept (see jj_info.block_width). */
 #define JJ_BLOCK_AUTO (-1)
 
@@ -199,9 +201,9 @@ int jjacobi_solve_host(jj_handle h, const void *G_host, int64_t ldg, const int8_
  * G[k] (device, m[k] x n[k], ldg[k] >= m[k], 1 <= n[k] <= m[k]) is overwritten
  * by G~_k in its own column order; J[k] (host, n[k] entries of +-1).
  * The handle's m and n bound the sizes (m[k] <= p->m, n[k] <= p->n); its
- * block_width is used for every problem (capped at ceil(n[k]/2)), or, when 0 or JJ_BLOCK_AUTO,
- * the widest block the contraction form takes (16 complex / 32 real columns for
- * the digit forms, 32 for FP64). Batched solves are two-level (inner_block_width
+ * block_width is used for every problem (capped at ceil(n[k]/2)), or, when 0,
+ * a default width (16 complex / 32 real columns for the digit forms, 32 for
+ * FP64), or, for JJ_BLOCK_AUTO, the width autotuned per size class. Batched solves are two-level (inner_block_width
  * is not used). Workspaces are (re)allocated on the first call
  * and kept while the shapes repeat. lambda_out (host or device, detected; sum of
  * n[k] doubles, problem k at offset sum_{l<k} n[l], each in its own column

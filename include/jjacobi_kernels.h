@@ -49,8 +49,9 @@ int jjk_plain_step(int32_t dtype, void *G, int64_t ld, int64_t m, int64_t n,
  * Gram's form as the solver does: FP64 for JJ_GEMM_FP64; digit products for
  * JJ_GEMM_OZAKI_FP16 and JJ_GEMM_OZAKI_GRAM (JJ_INVALID_ARG when the pivot
  * width exceeds what they take: real width 2 kmax (complex) or kmax (real)
- * above 64); JJ_GEMM_AUTO: digit products where they apply, else FP64. Other
- * values: JJ_INVALID_ARG. */
+ * above 256; a pivot wider than 64 real columns runs as tiles of 64);
+ * JJ_GEMM_AUTO: digit products where they apply, else FP64. Other values:
+ * JJ_INVALID_ARG. */
 int jjk_gram(int32_t dtype, int32_t gemm, const void *G, int64_t ld, int64_t m,
              const int32_t *pairs, int32_t npairs, double *A, int32_t kmax, void *stream);
 

@@ -99,6 +99,7 @@ struct jj_ctx {
     int oz_slices_gram = 8, oz_slices_update = 12;
     long long *d_udscr = nullptr;       // scratch of the digit update (per persistent block)
     int ud_nctas = 0;
+    int ud_tmax = 0;                    // widest pivot (64-position tiles per side) it serves
     unsigned long long wait_ns = 2000000000ull;  // bound of device-side waits
     int32_t *d_cexp = nullptr;          // column exponents (Ozaki Gram)
     unsigned long long *d_ozacc = nullptr;  // int128 Gram accumulators
@@ -185,11 +186,14 @@ void dfree(T *&p) {
 
 // Scratch of the digit update: one row block per persistent block (kept while
 // the plan lives; shared by the outer and inner levels, which run in turn).
-cudaError_t alloc_ud_scratch(jj_ctx *c) {
-    if (c->d_udscr) return cudaSuccess;
+cudaError_t alloc_ud_scratch(jj_ctx *c, int tmax) {
+    if (c->d_udscr && c->ud_tmax >= tmax) return cudaSuccess;
+    if (c->d_udscr) cudaFree(c->d_udscr);
+    c->d_udscr = nullptr;
     c->ud_nctas = ud_num_ctas();
     if (c->ud_nctas < 1) return cudaErrorInvalidDevice;
-    return cudaMalloc((void **)&c->d_udscr, ud_scratch_bytes(c->ud_nctas));
+    c->ud_tmax = tmax;
+    return cudaMalloc((void **)&c->d_udscr, ud_scratch_bytes(c->ud_nctas, tmax));
 }
 
 void free_plan(jj_ctx *c) {
@@ -206,6 +210,7 @@ void free_plan(jj_ctx *c) {
     dfree(c->d_wdig);
     dfree(c->d_wdexp);
     dfree(c->d_udscr);
+    c->ud_tmax = 0;
     dfree(c->d_mod);
     dfree(c->d_clean);
     dfree(c->d_flags);
@@ -402,9 +407,10 @@ int build_three(jj_ctx *c, const std::vector<int32_t> &tab) {
         JJ_CUDA(dmalloc(&T.d_cexp2, xcols));
         JJ_CUDA(cudaMalloc((void **)&T.d_ozacc, ozaki_gram_workspace_bytes((int)npi, T.kmax_in, c->cplx)));
         if (T.ozaki_update) {
-            JJ_CUDA(dmalloc(&T.d_wdig, npi * kUdMaxSlices * kUpdSliceBytes));
-            JJ_CUDA(dmalloc(&T.d_wdexp, npi * 64));
-            JJ_CUDA(alloc_ud_scratch(c));
+            const int ti = ud_max_tiles(c->cplx, T.kmax_in);
+            JJ_CUDA(dmalloc(&T.d_wdig, npi * ti * ti * kUdMaxSlices * kUpdSliceBytes));
+            JJ_CUDA(dmalloc(&T.d_wdexp, npi * ti * ti * 64));
+            JJ_CUDA(alloc_ud_scratch(c, ti));
         }
     }
     return JJ_OK;
@@ -541,9 +547,10 @@ int build_plan(jj_ctx *c, int count, const int64_t *ms, const int64_t *ns, const
     JJ_CUDA(dmalloc(&c->d_touched, 2 * np));
     if (c->ozaki) {
         if (c->ozaki_update) {
-            JJ_CUDA(dmalloc(&c->d_wdig, np * kUdMaxSlices * kUpdSliceBytes));
-            JJ_CUDA(dmalloc(&c->d_wdexp, np * 64));
-            JJ_CUDA(alloc_ud_scratch(c));
+            const int tm = ud_max_tiles(c->cplx, P.kmax);
+            JJ_CUDA(dmalloc(&c->d_wdig, np * tm * tm * kUdMaxSlices * kUpdSliceBytes));
+            JJ_CUDA(dmalloc(&c->d_wdexp, np * tm * tm * 64));
+            JJ_CUDA(alloc_ud_scratch(c, tm));
         }
         JJ_CUDA(dmalloc(&c->d_cexp, (size_t)P.ncols));
         JJ_CUDA(cudaMalloc((void **)&c->d_ozacc, ozaki_gram_workspace_bytes((int)np, P.kmax, c->cplx)));
@@ -672,11 +679,20 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
                 ud.cexp = c->d_cexp;
                 ud.slices = c->oz_slices_update;
             }
+            // the inner solve builds the W-side digits of a narrow pivot itself;
+            // those of a wide one (more than one 64-position tile) follow it
+            const bool wide = c->ozaki_update && ud_max_tiles(c->cplx, P.kmax) > 1;
+            UpdDigits iud = ud;
+            if (wide) iud.img = nullptr;
             const int pass = c->p.block_strategy == JJ_BLOCK_ORIENTED ? (t == 0 ? 2 : 1) : 0;
             JJ_CUDA(launch_inner(c->cplx, c->Ablk, c->Wblk, P.kmax, pr, np, c->d_Jw, c->tol,
                                  c->inner_max_sweeps, c->p.inner_block_width, c->d_cnt, st, ctl,
-                                 ud, pass, P.diag_np > 0 && !diag));
+                                 iud, pass, P.diag_np > 0 && !diag));
             if (mark(2)) return JJ_CUDA_ERROR;
+            if (wide) {
+                JJ_CUDA(launch_wimage(c->cplx, c->Wblk, P.kmax, pr, np, c->d_cexp, ud, st, ctl));
+                ++L;
+            }
             if (c->ozaki_update)
                 JJ_CUDA(launch_update_digits(c->cplx, c->Gw, c->Gw, P.ldw, mrows, pr, np, P.kmax,
                                              c->d_cexp, ud, c->d_udscr, c->ud_nctas, c->d_cnt, st,
@@ -954,9 +970,9 @@ bool j_sort(const int8_t *J, int64_t n, std::vector<int32_t> &perm) {
 }
 
 // Block widths the autotuner tries (block_width = JJ_BLOCK_AUTO): powers of two
-// from 8 up to the widest pivot the chosen contraction form takes (the digit
-// kernels: 64 real columns per pivot, i.e. b <= 16 complex / 32 real), and not
-// wider than a quarter of n (at least two block pairs per step).
+// from 8 up to 32 for the digit forms (the widest whose inner solve stays in
+// shared memory for both element types) and 64 for FP64, and not wider than a
+// quarter of n (at least two block pairs per step).
 std::vector<int> autotune_candidates(const jj_ctx *c) {
     std::vector<int> out;
     if (c->p.block_width > 0) {
@@ -964,7 +980,7 @@ std::vector<int> autotune_candidates(const jj_ctx *c) {
         return out;
     }
     const bool digits = c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM;
-    const int bmax = digits ? (c->cplx ? 16 : 32) : 64;
+    const int bmax = digits ? 32 : 64;
     for (int b = 8; b <= bmax; b *= 2)
         if (4 * (int64_t)b <= c->n || b == 8) out.push_back(b);
     return out;
@@ -1071,7 +1087,7 @@ int batch_autotune(jj_ctx *c, int count, void *const *G, const int64_t *m, const
     JJ_CUDA(cudaEventCreate(&e1));
     int rc = JJ_OK;
     const bool digits = c->p.gemm == JJ_GEMM_OZAKI_FP16 || c->p.gemm == JJ_GEMM_OZAKI_GRAM;
-    const int bmax = digits ? (c->cplx ? 16 : 32) : 64;
+    const int bmax = digits ? 32 : 64;
     for (auto &kv : classes) {
         if (c->class_bw.count(kv.first)) continue;
         const std::vector<int> &idx = kv.second;
@@ -1777,16 +1793,17 @@ int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld
         // digits of every pair, and the update's row blocks.
         const int nctas = ud_num_ctas();
         if (nctas < 1) return JJ_CUDA_ERROR;
+        const int tm = ud_max_tiles(cplx, kmax);
         UpdDigits ud;
         ud.slices = kUdMaxSlices;
         int32_t *cexp = nullptr;
         long long *scr = nullptr;
         cudaError_t e = cudaMallocAsync((void **)&cexp, std::max<int64_t>(ncols, 1) * sizeof(int32_t), st);
         if (e == cudaSuccess)
-            e = cudaMallocAsync((void **)&ud.img, (size_t)std::max(npairs, 1) * ud.slices * kUpdSliceBytes, st);
+            e = cudaMallocAsync((void **)&ud.img, (size_t)std::max(npairs, 1) * tm * tm * ud.slices * kUpdSliceBytes, st);
         if (e == cudaSuccess)
-            e = cudaMallocAsync((void **)&ud.wexp, (size_t)std::max(npairs, 1) * 64 * sizeof(int32_t), st);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&scr, ud_scratch_bytes(nctas), st);
+            e = cudaMallocAsync((void **)&ud.wexp, (size_t)std::max(npairs, 1) * tm * tm * 64 * sizeof(int32_t), st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&scr, ud_scratch_bytes(nctas, tm), st);
         ud.cexp = cexp;
         if (e == cudaSuccess) e = launch_colexp(cplx, (const double *)Gs, ld, m, ncols, cexp, st);
         if (e == cudaSuccess) e = launch_wimage(cplx, W, kmax, pairs, npairs, cexp, ud, st);

@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(ST) inner_smem_kernel(
         }
         __syncthreads();
         auto wacc = [&](int rr, int cc, int part) -> double { return W[((size_t)cc * ldr + rr) * E + part]; };
-        ud_wimage_build<CPLX>(wacc, k, s_xexp, s_wexp, ud.slices,
+        ud_wimage_build<CPLX>(wacc, k, k, true, s_xexp, s_wexp, ud.slices,
                               ud.img + (size_t)blockIdx.x * ud.slices * kUpdSliceBytes,
                               ud.wexp + (size_t)blockIdx.x * kUdPositions, tid, ST);
     }

@@ -125,20 +125,23 @@ struct StepCtl {
 constexpr int kPairSkipped = 1;
 constexpr int kPairIdentity = 2;
 
-// Operand of the split-precision update produced by the inner solve: the fp16
-// digits of D (W2 - I) as shared-memory images (SWIZZLE_128B, K-major: 64 rows
-// of 128 bytes per digit, row j = output position j, K position a = row of
-// W2, on the real-form positions of jj_digits.cuh), and their column
-// exponents. D holds the column exponents of the pivot columns (cexp). Used
-// only when the update runs as digit products.
+// Operand of the split-precision update: the fp16 digits of D (W2 - I) as
+// shared-memory images (SWIZZLE_128B, K-major: 64 rows of 128 bytes per
+// digit, row j = output position j, K position a = row of W2, on the
+// real-form positions of jj_digits.cuh), and their column exponents, one
+// image per 64 x 64 tile (kc, nc) of a wide pivot (T tiles per side, T = 1 up
+// to 64 real-form positions; the inner solve builds the image of such a
+// pivot itself, launch_wimage the others). D holds the column exponents of
+// the pivot columns (cexp). Used only when the update runs as digit products.
 struct UpdDigits {
-    uint8_t *img = nullptr;        // [npairs][slices][64 * 128]
-    int32_t *wexp = nullptr;       // [npairs][64]
+    uint8_t *img = nullptr;        // [npairs][T][T][slices][64 * 128]
+    int32_t *wexp = nullptr;       // [npairs][T][T][64]
     const int32_t *cexp = nullptr; // column exponents of G (by work column)
     int slices = 0;
 };
 constexpr int kUpdSliceBytes = 64 * 128;
 constexpr int kUdMaxSlices = 12;  // digits per operand of the update (84 bits)
+constexpr int kUdMaxTiles = 4;    // 64-position tiles per pivot side (256 real-form positions)
 
 // Decide (Gram kernels) whether pair q of this step can be skipped: the slot was
 // found clean at step `clean` and neither block changed after it.
@@ -231,7 +234,8 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
 // Split-precision block update (jj_update_digits.cu): ud.img / ud.wexp hold the
 // W-side digits of every active pair (built by the inner solve, or by
 // launch_wimage), cexp the column exponents of Gs, scratch
-// ud_scratch_bytes(nctas) bytes; nctas persistent blocks (ud_num_ctas()).
+// ud_scratch_bytes(nctas, ud_max_tiles(cplx, kmax)) bytes; nctas persistent
+// blocks (ud_num_ctas()).
 cudaError_t launch_update_digits(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
                                  const int32_t *pairs, int npairs, int kmax, const int32_t *cexp,
                                  const UpdDigits &ud, long long *scratch, int nctas,
@@ -240,7 +244,8 @@ cudaError_t launch_update_digits(bool cplx, const double *Gs, double *Gd, int64_
 cudaError_t launch_wimage(bool cplx, const double *W, int kmax, const int32_t *pairs, int npairs,
                           const int32_t *cexp, const UpdDigits &ud, cudaStream_t st,
                           StepCtl ctl = StepCtl());
-size_t ud_scratch_bytes(int nctas);
+size_t ud_scratch_bytes(int nctas, int tmax);
+int ud_max_tiles(bool cplx, int kmax);
 int ud_num_ctas();
 // Digit helpers shared by the inner solve (W-side digits) and the digit kernels.
 __device__ __forceinline__ unsigned long long dg_mag_bits(double x) {

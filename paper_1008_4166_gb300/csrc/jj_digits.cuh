@@ -77,23 +77,29 @@ __device__ __forceinline__ uint32_t dg_pack2(uint32_t d0, bool n0, uint32_t d1, 
     return r;
 }
 
-// (W2 - I) at real-form positions (a, j) of a pivot with k columns; w(r, c, part)
-// returns part 0 (real) or 1 (imaginary) of W_P[r][c].
+// One 64 x 64 tile of W2 - delta I on real-form positions (a, j): the tile of
+// row block kc and column block nc of a (possibly wide) pivot, w(r, c, part)
+// returning part 0 (real) or 1 (imaginary) of W_P[r][c] relative to the
+// tile's corner (complex: 32 pivot columns per tile, position p < 32 the real
+// part of column p and 32 + p its imaginary part; real: 64 columns per tile).
+// kr and kn: pivot columns present in the row and the column block; diag:
+// the tile lies on the diagonal (kc = nc), where the identity is subtracted.
 template <bool CPLX, typename WAcc>
-__device__ __forceinline__ double ud_w2m(const WAcc &w, int k, int a, int j) {
+__device__ __forceinline__ double ud_w2m(const WAcc &w, int kr, int kn, bool diag, int a, int j) {
     if (CPLX) {
         const int ra = a >> 5, ca = a & 31, rj = j >> 5, cj = j & 31;
-        if (ca >= k || cj >= k) return 0.0;
+        if (ca >= kr || cj >= kn) return 0.0;
         double v = ra == rj ? w(ca, cj, 0) : (ra == 0 ? w(ca, cj, 1) : -w(ca, cj, 1));
-        return a == j ? v - 1.0 : v;
+        return (diag && a == j) ? v - 1.0 : v;
     }
-    if (a >= k || j >= k) return 0.0;
+    if (a >= kr || j >= kn) return 0.0;
     const double v = w(a, j, 0);
-    return a == j ? v - 1.0 : v;
+    return (diag && a == j) ? v - 1.0 : v;
 }
 
-// The W-side operand of the digit update for one pair: the digits of
-// D' = diag(2^e_a) (W2 - I), column j relative to its own exponent w_j
+// The W-side operand of the digit update for one pair (one tile (kc, nc) of a
+// wide pivot, as ud_w2m): the digits of D' = diag(2^e_a) (W2 - delta I),
+// column j relative to its own exponent w_j
 // (D'_aj < 2^w_j), as `slices` SWIZZLE_128B K-major tiles of 64 rows (row j =
 // output position j) x 128 bytes (64 fp16 along K = position a), tile u at
 // (u - 1) * kUpdSliceBytes, and the exponents w_j. The power-of-two scaling is
@@ -102,13 +108,13 @@ __device__ __forceinline__ double ud_w2m(const WAcc &w, int k, int a, int j) {
 // empty). Called by every thread of the block; s_wexp is 64 ints of shared
 // memory.
 template <bool CPLX, typename WAcc>
-__device__ void ud_wimage_build(const WAcc &w, int k, const int *xexp, int *s_wexp, int slices,
-                                uint8_t *img, int32_t *wexp_out, int tid, int nthreads) {
+__device__ void ud_wimage_build(const WAcc &w, int kr, int kn, bool diag, const int *xexp, int *s_wexp,
+                                int slices, uint8_t *img, int32_t *wexp_out, int tid, int nthreads) {
     const int warp = tid >> 5, lane = tid & 31, nw = nthreads >> 5;
     for (int j = warp; j < kUdPositions; j += nw) {
         int mx = -100000;
         for (int a = lane; a < kUdPositions; a += 32) {
-            const unsigned long long mb = dg_mag_bits(ud_w2m<CPLX>(w, k, a, j));
+            const unsigned long long mb = dg_mag_bits(ud_w2m<CPLX>(w, kr, kn, diag, a, j));
             if (mb) mx = max(mx, dg_exp_of_bits(mb) + xexp[a]);
         }
 #pragma unroll
@@ -118,7 +124,7 @@ __device__ void ud_wimage_build(const WAcc &w, int k, const int *xexp, int *s_we
     __syncthreads();
     for (int it = tid; it < kUdPositions * (kUdPositions / 2); it += nthreads) {
         const int j = it / (kUdPositions / 2), a = (it % (kUdPositions / 2)) * 2;
-        const double x0 = ud_w2m<CPLX>(w, k, a, j), x1 = ud_w2m<CPLX>(w, k, a + 1, j);
+        const double x0 = ud_w2m<CPLX>(w, kr, kn, diag, a, j), x1 = ud_w2m<CPLX>(w, kr, kn, diag, a + 1, j);
         const Fx84 f0 = dg_fixed84(x0, s_wexp[j] - xexp[a]);
         const Fx84 f1 = dg_fixed84(x1, s_wexp[j] - xexp[a + 1]);
         const bool n0 = __double_as_longlong(x0) < 0, n1 = __double_as_longlong(x1) < 0;

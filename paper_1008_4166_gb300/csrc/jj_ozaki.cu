@@ -35,7 +35,7 @@
 namespace jj {
 
 constexpr int kBeta = 7;          // bits per digit
-constexpr int kOzMaxK2 = 64;      // real width 2k (complex) or k (real) handled here
+constexpr int kOzMaxK2 = 256;     // real width 2k (complex) or k (real) handled here
 
 namespace {
 
@@ -147,6 +147,12 @@ __global__ void __launch_bounds__(256) colexp_pairs_kernel(const double *__restr
 // drained into two signed 64-bit words per output (no carries until the end).
 // At the end each block adds its partial sums atomically into the global
 // int128 accumulator (lo, hi words with an explicit carry).
+//
+// Wide pivots (K2 > 64) are cut into 64-position tiles; the grid's third
+// dimension runs over the tile pairs (ta, tb), ta <= tb, of the upper
+// triangle (the Gram is symmetric and its integer sums are exact, so the lower
+// tiles are the transposes). A diagonal tile is the case above; an
+// off-diagonal one takes its two operands from two buffers, one stage deep.
 // ---------------------------------------------------------------------------
 constexpr int GZ_THREADS = 512;
 constexpr int GZ_KC = 64;                 // rows of G per shared-memory buffer
@@ -169,12 +175,22 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
     const int32_t *pd = pairs + 4 * blockIdx.y;
     if (ctl.mod_step) {
         const bool skip = pair_skip_decide(ctl, pd, blockIdx.y);
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctl.flags[blockIdx.y] = skip ? kPairSkipped : 0;
+        if (blockIdx.x == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+            ctl.flags[blockIdx.y] = skip ? kPairSkipped : 0;
         if (skip) return;
     }
     const int k = pd[1] + pd[3];
     const int K2 = CPLX ? 2 * k : k;
-    const int NP = (K2 + 15) & ~15;  // N of the MMA (multiple of 16)
+    // tile pair (ta, tb) of this block: blockIdx.z = tb (tb + 1) / 2 + ta
+    int ta = blockIdx.z, tb = 0;
+    while (ta > tb) {
+        ta -= tb + 1;
+        ++tb;
+    }
+    if (64 * tb >= K2) return;
+    const bool offd = ta != tb;
+    const int pa0 = 64 * ta, pb0 = 64 * tb;  // first positions of the A and B tiles
+    const int NP = (min(64, K2 - pb0) + 15) & ~15;  // N of the MMA (multiple of 16)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     m = pair_rows(ctl, blockIdx.y, m);
     const int64_t row0 = (int64_t)blockIdx.x * rows_per_block;
@@ -192,8 +208,8 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         mbar_init(su32(&bar_mma[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    // operand rows K2..63 stay zero for every chunk
-    if (K2 < 64)
+    // operand rows beyond K2 of a partial last tile stay zero for every chunk
+    if (K2 - pb0 < 64)
         for (int i = tid; i < 2 * GZ_BUF_BYTES / 16; i += GZ_THREADS)
             reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
     tc_fence_before();
@@ -206,7 +222,7 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
     // for lane < 16 (M = 64 layout); columns [cq*16, cq*16 + 16)
     const int quad = warp & 3, cq = warp >> 2;
     const int orow = quad * 16 + lane;
-    const bool owns = lane < 16 && orow < K2;
+    const bool owns = lane < 16 && pa0 + orow < K2;
     long long w0[16], w1[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -232,14 +248,14 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
             s_abort = 1;
         }
     };
-    // digits of rows [row0 + 64 i, +64) of the K2 real columns into buffer b,
-    // by warps 1..15 (warp 0 issues the tensor-core products meanwhile);
+    // digits of rows [row0 + 64 i, +64) of the 64 positions from pos0 into
+    // buffer b, by warps 1..15 (warp 0 issues the tensor-core products meanwhile);
     // item -> (column a, row pair): rows l, l+1 packed into one 32-bit store.
     // Two items per thread at a time, loads first (the 64 accumulator
     // registers of the drain leave no room for more).
     constexpr int GZ_BUILDERS = GZ_THREADS - 32;
     constexpr int GZ_NITEMS = 64 * (GZ_KC / 2);
-    auto build = [&](int i, int b) {
+    auto build = [&](int i, int b, int pos0) {
         const int64_t c0 = row0 + (int64_t)i * GZ_KC;
         const int nrow = (int)min((int64_t)GZ_KC, row1 - c0);
         uint8_t *buf = sm + (size_t)b * GZ_BUF_BYTES;
@@ -248,7 +264,7 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int idx = base + u * GZ_BUILDERS;
-                const int a = idx / (GZ_KC / 2);
+                const int a = pos0 + idx / (GZ_KC / 2);
                 const int lp = (idx % (GZ_KC / 2)) * 2;
                 xv0[u] = 0.0;
                 xv1[u] = 0.0;
@@ -264,13 +280,13 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int idx = base + u * GZ_BUILDERS;
-                const int a = idx / (GZ_KC / 2);
+                const int a = pos0 + idx / (GZ_KC / 2);
                 const int lp = (idx % (GZ_KC / 2)) * 2;
                 if (idx >= GZ_NITEMS || a >= K2) continue;
                 const int e = sexp[a];
                 const unsigned long long q0 = fixed63(xv0[u], e), q1 = fixed63(xv1[u], e);
                 const bool n0 = neg_bits(xv0[u]), n1 = neg_bits(xv1[u]);
-                const uint32_t off = sw128_off(a, lp * 2);
+                const uint32_t off = sw128_off(a - pos0, lp * 2);
 #pragma unroll
                 for (int t = 1; t <= GZ_SLICES; ++t)
                     *reinterpret_cast<uint32_t *>(buf + (t - 1) * GZ_SLICE_BYTES + off) =
@@ -279,87 +295,123 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         }
     };
 
-    if (nsc > 0 && warp != 0) build(0, 0);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    for (int i = 0; i < nsc && !s_abort; ++i) {
-        const int b = i & 1;
-        const bool first = (i & 1) == 0;  // first 64 rows of a 128-row accumulation
-        if (tid == 0) {
-            // For each A digit t, the B tiles of digits u, u + 1, ... are
-            // adjacent in shared memory and their diagonals t + u, t + u + 1, ...
-            // are adjacent 64-column groups in TMEM: one product with
-            // N = 64 * run covers a run of up to four (rows of a digit tile
-            // beyond K2 are zero, so the columns beyond K2 of each group receive
-            // zeros). Digit t = 1 meets every diagonal once, so its products
-            // (accumulate = 0 in the first chunk of a 128-row accumulation)
-            // initialize all groups.
-            const uint32_t base = sbase + (uint32_t)(b * GZ_BUF_BYTES);
-            for (int t = 1; t <= GZ_SLICES; ++t) {
-                const int umax = GZ_SLICES + 1 - t;
-                const uint32_t a0 = base + (uint32_t)((t - 1) * GZ_SLICE_BYTES);
-                for (int u = 1; u <= umax;) {
-                    // adjacent tiles in one product (only when a tile has no
-                    // padding rows, which a wider N would multiply)
-                    const int run = NP == 64 ? min(4, umax - u + 1) : 1;
-                    const uint32_t id = run == 1 ? idesc : idesc_f16(64, 64 * run);
-                    const uint32_t dt = tmem + (uint32_t)((t + u - 2) * 64);
-                    const uint32_t b0 = base + (uint32_t)((u - 1) * GZ_SLICE_BYTES);
+    // For each A digit t, the B tiles of digits u, u + 1, ... are adjacent in
+    // shared memory and their diagonals t + u, t + u + 1, ... are adjacent
+    // 64-column groups in TMEM: one product with N = 64 * run covers a run of
+    // up to four (rows of a digit tile beyond K2 are zero, so the columns
+    // beyond K2 of each group receive zeros). Digit t = 1 meets every diagonal
+    // once, so its products (accumulate = 0 in the first chunk of a 128-row
+    // accumulation) initialize all groups. One thread issues.
+    auto issue = [&](uint32_t abase, uint32_t bbase, bool first) {
+        for (int t = 1; t <= GZ_SLICES; ++t) {
+            const int umax = GZ_SLICES + 1 - t;
+            const uint32_t a0 = abase + (uint32_t)((t - 1) * GZ_SLICE_BYTES);
+            for (int u = 1; u <= umax;) {
+                // adjacent tiles in one product (only when a tile has no
+                // padding rows, which a wider N would multiply)
+                const int run = NP == 64 ? min(4, umax - u + 1) : 1;
+                const uint32_t id = run == 1 ? idesc : idesc_f16(64, 64 * run);
+                const uint32_t dt = tmem + (uint32_t)((t + u - 2) * 64);
+                const uint32_t b0 = bbase + (uint32_t)((u - 1) * GZ_SLICE_BYTES);
 #pragma unroll
-                    for (int ks = 0; ks < GZ_KC / 16; ++ks)
-                        mma_f16(dt, desc_sw128(a0 + ks * 32), desc_sw128(b0 + ks * 32), id,
-                                (first && t == 1 && ks == 0) ? 0u : 1u);
-                    u += run;
-                }
+                for (int ks = 0; ks < GZ_KC / 16; ++ks)
+                    mma_f16(dt, desc_sw128(a0 + ks * 32), desc_sw128(b0 + ks * 32), id,
+                            (first && t == 1 && ks == 0) ? 0u : 1u);
+                u += run;
             }
-            mma_commit(su32(&bar_mma[b]));
         }
-        pending[b] = true;
-        if (i + 1 < nsc) {
-            wait_buf(b ^ 1, ctl.wait_ns);  // the products that read the other buffer are done
-            if (warp != 0) build(i + 1, b ^ 1);
-            fence_async_smem();
-        }
-        if ((i & 1) == 1 || i == nsc - 1) {
-            wait_buf(b ^ 1, ctl.wait_ns);
-            wait_buf(b, ctl.wait_ns);
-            tc_fence_after();
-            if (!s_abort) {
-                // two groups (32 columns of this thread) per TMEM round trip
+    };
+    // every group of the last 128 rows into the two int64 words of each output
+    auto drain = [&]() {
+        // two groups (32 columns of this thread) per TMEM round trip
 #pragma unroll
-                for (int d0 = 2; d0 <= GZ_SLICES + 1; d0 += 2) {
-                    uint32_t v[4][8];
+        for (int d0 = 2; d0 <= GZ_SLICES + 1; d0 += 2) {
+            uint32_t v[4][8];
 #pragma unroll
-                    for (int g = 0; g < 2; ++g)
+            for (int g = 0; g < 2; ++g)
 #pragma unroll
-                        for (int h = 0; h < 2; ++h)
-                            tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) +
-                                         (uint32_t)((d0 + g - 2) * 64 + cq * 16 + 8 * h),
-                                     v[2 * g + h]);
-                    tmem_wait_ld();
+                for (int h = 0; h < 2; ++h)
+                    tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)((d0 + g - 2) * 64 + cq * 16 + 8 * h),
+                             v[2 * g + h]);
+            tmem_wait_ld();
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
-                        const int sh = kBeta * (GZ_SLICES + 1 - (d0 + g));
-                        const long long mul = 1ll << (sh & 31);
+            for (int g = 0; g < 2; ++g) {
+                const int sh = kBeta * (GZ_SLICES + 1 - (d0 + g));
+                const long long mul = 1ll << (sh & 31);
 #pragma unroll
-                        for (int h = 0; h < 2; ++h)
+                for (int h = 0; h < 2; ++h)
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const int iv = __float2int_rn(__uint_as_float(v[2 * g + h][j]));  // exact, |v| < 2^24
-                                if (sh >= 32)
-                                    w1[8 * h + j] += (long long)iv * mul;
-                                else
-                                    w0[8 * h + j] += (long long)iv * mul;
-                            }
+                    for (int j = 0; j < 8; ++j) {
+                        const int iv = __float2int_rn(__uint_as_float(v[2 * g + h][j]));  // exact, |v| < 2^24
+                        if (sh >= 32)
+                            w1[8 * h + j] += (long long)iv * mul;
+                        else
+                            w0[8 * h + j] += (long long)iv * mul;
                     }
-                }
             }
-            tc_fence_before();
         }
+    };
+
+    if (!offd) {
+        // diagonal tile: one operand tile serves as A and B; two buffers, the
+        // digits of the next 64 rows built while the products read the current
+        if (nsc > 0 && warp != 0) build(0, 0, pa0);
+        fence_async_smem();
+        tc_fence_before();
         __syncthreads();
         tc_fence_after();
+        for (int i = 0; i < nsc && !s_abort; ++i) {
+            const int b = i & 1;
+            const bool first = (i & 1) == 0;  // first 64 rows of a 128-row accumulation
+            if (tid == 0) {
+                const uint32_t base = sbase + (uint32_t)(b * GZ_BUF_BYTES);
+                issue(base, base, first);
+                mma_commit(su32(&bar_mma[b]));
+            }
+            pending[b] = true;
+            if (i + 1 < nsc) {
+                wait_buf(b ^ 1, ctl.wait_ns);  // the products that read the other buffer are done
+                if (warp != 0) build(i + 1, b ^ 1, pa0);
+                fence_async_smem();
+            }
+            if ((i & 1) == 1 || i == nsc - 1) {
+                wait_buf(b ^ 1, ctl.wait_ns);
+                wait_buf(b, ctl.wait_ns);
+                tc_fence_after();
+                if (!s_abort) drain();
+                tc_fence_before();
+            }
+            __syncthreads();
+            tc_fence_after();
+        }
+    } else {
+        // off-diagonal tile: A digits in buffer 0, B digits in buffer 1
+        for (int i = 0; i < nsc && !s_abort; ++i) {
+            const bool first = (i & 1) == 0;
+            wait_buf(0, ctl.wait_ns);  // the previous chunk's products have read both buffers
+            if (s_abort) break;
+            if (warp != 0) {
+                build(i, 0, pa0);
+                build(i, 1, pb0);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                issue(sbase, sbase + (uint32_t)GZ_BUF_BYTES, first);
+                mma_commit(su32(&bar_mma[0]));
+            }
+            pending[0] = true;
+            if ((i & 1) == 1 || i == nsc - 1) {
+                wait_buf(0, ctl.wait_ns);
+                tc_fence_after();
+                if (!s_abort) drain();
+                tc_fence_before();
+            }
+            __syncthreads();
+            tc_fence_after();
+        }
     }
     if (s_abort) {
         // in-flight products finish before the TMEM is freed (the default bound:
@@ -372,14 +424,14 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         unsigned long long *dst = acc_out + (size_t)blockIdx.y * k2max * k2max * 2;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int bcol = cq * 16 + j;
+            const int bcol = pb0 + cq * 16 + j;
             if (bcol < K2) {
                 // T = w0 + w1 * 2^32 as (lo, hi)
                 const unsigned long long l1 = (unsigned long long)w1[j] << 32;
                 const long long h1 = w1[j] >> 32;
                 const unsigned long long lo = (unsigned long long)w0[j] + l1;
                 const long long hi = (w0[j] >> 63) + h1 + (lo < l1 ? 1 : 0);
-                unsigned long long *w = dst + ((size_t)bcol * k2max + orow) * 2;
+                unsigned long long *w = dst + ((size_t)bcol * k2max + pa0 + orow) * 2;
                 const unsigned long long old = atomicAdd(w, lo);
                 const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
                 atomicAdd(w + 1, (unsigned long long)hi + carry);
@@ -404,7 +456,14 @@ __global__ void __launch_bounds__(256) gram_fixed_to_double_kernel(
     if (idx >= k * k) return;
     const int a = idx % k, b = idx / k;
     const unsigned long long *P = acc + (size_t)blockIdx.y * k2max * k2max * 2;
+    // only the tiles (ta, tb) with ta <= tb (64 positions each) are formed: a
+    // lower one is read as the transpose
     auto ld128 = [&](int r, int c, unsigned long long &lo, long long &hi) {
+        if ((r >> 6) > (c >> 6)) {
+            const int x = r;
+            r = c;
+            c = x;
+        }
         lo = P[((size_t)c * k2max + r) * 2];
         hi = (long long)P[((size_t)c * k2max + r) * 2 + 1];
     };
@@ -496,10 +555,13 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
     if (k2max > kOzMaxK2 || slices != GZ_SLICES) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(acc, 0, ozaki_gram_workspace_bytes(npairs, kmax, cplx), st);
     if (e != cudaSuccess) return e;
+    // tile pairs of the widest pivot (upper triangle of T x T tiles of 64)
+    const int T = (k2max + 63) / 64;
+    const int ntp = T * (T + 1) / 2;
     // rows per block: enough blocks to fill the GPU, a multiple of 128 rows
     int rpb = 2 * GZ_KC * 8;
-    while (rpb > 2 * GZ_KC && (int64_t)npairs * ((m + rpb - 1) / rpb) < 2 * 152) rpb /= 2;
-    dim3 grid((unsigned)((m + rpb - 1) / rpb), npairs);
+    while (rpb > 2 * GZ_KC && (int64_t)npairs * ntp * ((m + rpb - 1) / rpb) < 2 * 152) rpb /= 2;
+    dim3 grid((unsigned)((m + rpb - 1) / rpb), npairs, ntp);
     const size_t smem = (size_t)2 * GZ_BUF_BYTES + 1024;
     if (cplx) {
         if ((e = set_smem(gram_ozaki_kernel<true>, smem)) != cudaSuccess) return e;

@@ -38,6 +38,17 @@
 //     group as soon as its last product is done (8 rotating TMEM slots of 64
 //     columns), fold it into int64 Horner sums, park the phase-A sum in an
 //     L2-resident scratch row, and write Y = X + corr.
+// Wide pivots (more than 64 real-form positions: b > 32 columns per block in
+// the complex case, b > 64 in the real one) are cut into 64-position tiles,
+// T per pivot side: output tile nc of a 128-row tile is
+//     Y_nc = X_nc + sum_kc X_kc (W2 - I)_(kc, nc),
+// and each work item runs its T^2 tile products (kc, nc) through the same
+// pipeline, each with its own row and column exponents. Their exact int128
+// results are summed exactly (the smaller exponent's sum shifted to the
+// larger one), one rounding to FP64 per output tile, and Y = X + corr is
+// written once the item's last product is drained (in place: every tile of X
+// is read by the products of every output tile).
+//
 // Every wait is bounded (tc::mbar_wait); a wait that runs out sets an error
 // flag and every role leaves its loop, so the kernel returns with its TMEM
 // freed.
@@ -61,7 +72,15 @@ constexpr int UD_THREADS = (UD_EPI + 1 + UD_BLD) * 32;
 constexpr int UD_ATILE = UD_M * 128;            // 16 KB per A digit tile
 constexpr int UD_PA = 6;                        // digits of phase A (groups 2..7)
 constexpr int UD_RING = 4;                      // row-exponent ring (items)
-constexpr size_t UD_SCRATCH_PER_CTA = (size_t)kUdPositions * UD_M * sizeof(long long);
+constexpr int UD_TILE_LONGS = kUdPositions * UD_M;  // one 64-position tile of 64-bit words
+
+// Per-CTA scratch (64-bit words): the parked phase-A sums; for wide pivots
+// also the running int128 sums (lo, hi, exponent) of the current output tile
+// and the FP64 corrections of every output tile.
+__host__ __device__ constexpr size_t ud_scratch_longs(int tmax) {
+    return (size_t)UD_TILE_LONGS +
+           (tmax > 1 ? (size_t)UD_TILE_LONGS * 2 + UD_TILE_LONGS / 2 + (size_t)UD_TILE_LONGS * tmax : 0);
+}
 
 struct UdShared {
     unsigned long long a_full[UD_ASLOTS], a_empty[UD_ASLOTS];
@@ -92,6 +111,28 @@ __device__ __forceinline__ void ud_next(const StepCtl &c, int npairs, int64_t m,
 
 __device__ __forceinline__ int64_t ud_gcol(const int32_t *pd, int c) {
     return c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
+}
+
+// 64-position tiles per side of a pivot with k columns (32 complex or 64 real
+// columns per tile).
+template <bool CPLX>
+__host__ __device__ __forceinline__ int ud_ntiles(int k) {
+    return CPLX ? (k + 31) / 32 : (k + 63) / 64;
+}
+
+// Arithmetic shift right of the two's-complement int128 (hi:lo) by n >= 0.
+__device__ __forceinline__ void i128_sar(long long &hi, unsigned long long &lo, int n) {
+    if (n <= 0) return;
+    if (n >= 127) {
+        lo = (unsigned long long)(hi >> 63);
+        hi >>= 63;
+    } else if (n >= 64) {
+        lo = (unsigned long long)(hi >> (n - 64));
+        hi >>= 63;
+    } else {
+        lo = (lo >> n) | ((unsigned long long)hi << (64 - n));
+        hi >>= n;
+    }
 }
 
 // Out of the normal range (never for the method's inputs): ldexp, kept out of
@@ -136,11 +177,12 @@ __device__ __forceinline__ double i128_scaled_to_double(long long hi, unsigned l
                                             (mant & 0xFFFFFFFFFFFFFull)));
 }
 
-template <bool CPLX>
+// WIDE: pivots of more than one 64-position tile per side (tmax > 1).
+template <bool CPLX, bool WIDE>
 __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
     const double *Gs, double *Gd, int64_t ld, int64_t m, const int32_t *__restrict__ pairs,
     int npairs, const int32_t *__restrict__ cexp, const uint8_t *__restrict__ wimg,
-    const int32_t *__restrict__ wexp, int slices, int s, long long *__restrict__ scratch,
+    const int32_t *__restrict__ wexp, int slices, int s, int tmax, long long *__restrict__ scratch,
     unsigned long long *__restrict__ counters, uint64_t wait_ns, StepCtl ctl) {
     extern __shared__ __align__(1024) uint8_t ud_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)ud_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -151,6 +193,7 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int hA = s < UD_PA ? s : UD_PA;  // digits (= groups) of phase A
+    if (!WIDE) tmax = 1;
     const bool phaseB = s > UD_PA;
 
     // ---- set-up: barriers, TMEM, this CTA's range of work items ----
@@ -223,7 +266,11 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
         // ------------------------------------------------------------------
         const int quad = warp & 3, hh = warp >> 2;
         const int rl = quad * 32 + lane;
-        long long *scr = scratch + (size_t)blockIdx.x * kUdPositions * UD_M;
+        long long *scr = scratch + (size_t)blockIdx.x * ud_scratch_longs(tmax);
+        unsigned long long *slo = reinterpret_cast<unsigned long long *>(scr + UD_TILE_LONGS);
+        long long *shi = scr + 2 * UD_TILE_LONGS;
+        int *sex = reinterpret_cast<int *>(scr + 3 * UD_TILE_LONGS);
+        double *ysum = reinterpret_cast<double *>(scr + 3 * UD_TILE_LONGS + UD_TILE_LONGS / 2);
         int q = S.q0, r = S.r0;
         long long acc[32];
         // Drain n = 1 or 2 consecutive groups g (and g + 1) into the Horner sums.
@@ -276,73 +323,154 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                 if (!drain(g0 + d - 2, d + 1 <= d_hi ? 2 : 1, d == d_lo)) return false;
             return true;
         };
+        int J = 0;  // tile products of this CTA so far
         for (int j = 0; j < count; ++j) {
             if (*abort_flag) break;
             const int32_t *pd = pairs + 4 * q;
             const int k = pd[1] + pd[3];
+            const int Tq = WIDE ? ud_ntiles<CPLX>(k) : 1;
             const int64_t rows = pair_rows(ctl, q, m);
             const int64_t l = (int64_t)r * UD_M + rl;
-            const long long g0 = (long long)j * s;
             bool ok = true;
-            ok = drain_range(g0, 2, hA + 1);
-            if (!ok) break;
-            if (phaseB) {
-#pragma unroll
-                for (int c = 0; c < 32; ++c) scr[(size_t)(hh * 32 + c) * UD_M + rl] = acc[c];
-                ok = drain_range(g0, UD_PA + 2, s + 1);
+            for (int sp = 0; sp < Tq * Tq; ++sp, ++J) {
+                const int nc = sp / Tq, kc = sp % Tq;
+                const long long g0 = (long long)J * s;
+                ok = drain_range(g0, 2, hA + 1);
                 if (!ok) break;
-            }
-            const int rho = j % UD_RING;
-            if (!__all_sync(0xffffffffu, mbar_wait(su32(&S.r_full[rho]), (uint32_t)((j / UD_RING) & 1), wait_ns))) {
-                *abort_flag = 1;
-                break;
-            }
-            const int re = S.rexp[rho][rl];
-            const int32_t *wx = wexp + (size_t)q * kUdPositions + hh * 32;
-            // Y = X + corr, 4 outputs at a time: all loads of a batch are issued
-            // before its stores (Gd may be Gs, so a load cannot move above a store)
-            if (l < rows) {
+                if (phaseB) {
 #pragma unroll
-                for (int cb = 0; cb < 32; cb += 4) {
-                    int64_t idx[4];
-                    double xv[4];
-                    long long av[4];
-                    int wv[4];
+                    for (int c = 0; c < 32; ++c) scr[(size_t)(hh * 32 + c) * UD_M + rl] = acc[c];
+                    ok = drain_range(g0, UD_PA + 2, s + 1);
+                    if (!ok) break;
+                }
+                const int rho = (int)(J % UD_RING);
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(su32(&S.r_full[rho]), (uint32_t)((J / UD_RING) & 1), wait_ns))) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                const int re = S.rexp[rho][rl];
+                const int32_t *wx = wexp + ((size_t)q * tmax * tmax + nc * tmax + kc) * kUdPositions + hh * 32;
+                // pivot column of output position hh * 32 + cc of tile nc
+                auto pcol = [&](int cc) { return CPLX ? 32 * nc + cc : 64 * nc + hh * 32 + cc; };
+                if (l < rows && (!WIDE || Tq == 1)) {
+                    // Y = X + corr, 4 outputs at a time: all loads of a batch are
+                    // issued before its stores (Gd may be Gs, so a load cannot move
+                    // above a store)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int cc = CPLX ? cb + c : hh * 32 + cb + c;  // pivot column of the position
-                        idx[c] = cc < k ? (CPLX ? (ud_gcol(pd, cc) * ld + l) * 2 + hh : ud_gcol(pd, cc) * ld + l)
-                                        : -1;
+                    for (int cb = 0; cb < 32; cb += 4) {
+                        int64_t idx[4];
+                        double xv[4];
+                        long long av[4];
+                        int wv[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int cc = pcol(cb + c);
+                            idx[c] = cc < k ? (CPLX ? (ud_gcol(pd, cc) * ld + l) * 2 + hh : ud_gcol(pd, cc) * ld + l)
+                                            : -1;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            xv[c] = idx[c] >= 0 ? Gs[idx[c]] : 0.0;
+                            av[c] = phaseB ? scr[(size_t)(hh * 32 + cb + c) * UD_M + rl] : 0ll;
+                            wv[c] = wx[cb + c];
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if (idx[c] < 0) continue;
+                            long long hi;
+                            unsigned long long lo;
+                            const long long b = acc[cb + c];
+                            if (phaseB) {
+                                // T = accA 2^(7 (s - 6)) + accB
+                                const int sh = 7 * (s - UD_PA);
+                                const unsigned long long al = (unsigned long long)av[c] << sh;
+                                const long long ah = av[c] >> (64 - sh);
+                                lo = al + (unsigned long long)b;
+                                hi = ah + (b >> 63) + (lo < al ? 1 : 0);
+                            } else {
+                                lo = (unsigned long long)b;
+                                hi = b >> 63;
+                            }
+                            Gd[idx[c]] = xv[c] + i128_scaled_to_double(hi, lo, re + wv[c] - 7 * (s + 1));
+                        }
                     }
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        xv[c] = idx[c] >= 0 ? Gs[idx[c]] : 0.0;
-                        av[c] = phaseB ? scr[(size_t)(hh * 32 + cb + c) * UD_M + rl] : 0ll;
-                        wv[c] = wx[cb + c];
-                    }
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (idx[c] < 0) continue;
+                } else if (WIDE && l < rows) {
+                    // wide pivot: add this tile product to the running int128 sum
+                    // of output tile nc; its last one is rounded to FP64
+#pragma unroll 4
+                    for (int c = 0; c < 32; ++c) {
+                        if (pcol(c) >= k) continue;
                         long long hi;
                         unsigned long long lo;
-                        const long long b = acc[cb + c];
+                        const long long b = acc[c];
+                        const size_t si = (size_t)(hh * 32 + c) * UD_M + rl;
                         if (phaseB) {
-                            // T = accA 2^(7 (s - 6)) + accB
+                            const long long a = scr[si];
                             const int sh = 7 * (s - UD_PA);
-                            const unsigned long long al = (unsigned long long)av[c] << sh;
-                            const long long ah = av[c] >> (64 - sh);
+                            const unsigned long long al = (unsigned long long)a << sh;
+                            const long long ah = a >> (64 - sh);
                             lo = al + (unsigned long long)b;
                             hi = ah + (b >> 63) + (lo < al ? 1 : 0);
                         } else {
                             lo = (unsigned long long)b;
                             hi = b >> 63;
                         }
-                        Gd[idx[c]] = xv[c] + i128_scaled_to_double(hi, lo, re + wv[c] - 7 * (s + 1));
+                        int e = re + wx[c];
+                        if (kc > 0) {
+                            unsigned long long rlo = slo[si];
+                            long long rhi = shi[si];
+                            const int re2 = sex[si];
+                            if (e > re2) {
+                                i128_sar(rhi, rlo, e - re2);
+                            } else {
+                                i128_sar(hi, lo, re2 - e);
+                                e = re2;
+                            }
+                            const unsigned long long sl = rlo + lo;
+                            hi = rhi + hi + (sl < rlo ? 1 : 0);
+                            lo = sl;
+                        }
+                        if (kc == Tq - 1) {
+                            ysum[(size_t)(nc * kUdPositions + hh * 32 + c) * UD_M + rl] =
+                                i128_scaled_to_double(hi, lo, e - 7 * (s + 1));
+                        } else {
+                            slo[si] = lo;
+                            shi[si] = hi;
+                            sex[si] = e;
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(su32(&S.r_empty[rho]));
+            }
+            if (!ok) break;
+            if (WIDE && Tq > 1 && l < rows) {
+                // the item's products are all drained, so every tile of X has
+                // been read: Y = X + corr for every output tile
+                for (int nc = 0; nc < Tq; ++nc) {
+#pragma unroll
+                    for (int cb = 0; cb < 32; cb += 4) {
+                        int64_t idx[4];
+                        double xv[4], yv[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int cc = CPLX ? 32 * nc + cb + c : 64 * nc + hh * 32 + cb + c;
+                            idx[c] = cc < k ? (CPLX ? (ud_gcol(pd, cc) * ld + l) * 2 + hh : ud_gcol(pd, cc) * ld + l)
+                                            : -1;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            xv[c] = idx[c] >= 0 ? Gs[idx[c]] : 0.0;
+                            yv[c] = idx[c] >= 0 ? ysum[(size_t)(nc * kUdPositions + hh * 32 + cb + c) * UD_M + rl] : 0.0;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (idx[c] >= 0) Gd[idx[c]] = xv[c] + yv[c];
                     }
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(su32(&S.r_empty[rho]));
             ud_next(ctl, npairs, m, q, r);
         }
     } else if (warp == UD_MMA) {
@@ -350,7 +478,8 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
         // Product issue (one thread).
         // ------------------------------------------------------------------
         if (lane == 0) {
-            int q = S.q0, r = S.r0, prev_q = -1;
+            int q = S.q0, r = S.r0;
+            long long prev_key = -1;
             uint32_t bpar = 0, dpar = 0;
             // a bulk copy / a commit whose completion has not been seen yet (a
             // barrier must not complete two phases unobserved: its parity wait
@@ -390,51 +519,57 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                     if (g >= UD_TSLOTS) waitb(&S.t_empty[g & (UD_TSLOTS - 1)], (uint32_t)(((g >> 3) - 1) & 1));
                 }
             };
+            int J = 0;  // tile products of this CTA so far
             for (int j = 0; j < count && ok; ++j) {
-                if (q != prev_q) {
-                    // the B tiles of the new pair, once the products reading the old ones are done
-                    if (prev_q >= 0) {
-                        mma_commit(su32(&S.mma_done));
-                        d_pending = true;
-                        waitb(&S.mma_done, dpar);
+                const int Tq = WIDE ? ud_ntiles<CPLX>(pairs[4 * q + 1] + pairs[4 * q + 3]) : 1;
+                for (int sp = 0; sp < Tq * Tq && ok; ++sp, ++J) {
+                    const int nc = sp / Tq, kc = sp % Tq;
+                    const long long key = ((long long)q * tmax + nc) * tmax + kc;  // W tile (q, kc, nc)
+                    if (key != prev_key) {
+                        // the B tiles of the new W tile, once the products reading the old ones are done
+                        if (prev_key >= 0) {
+                            mma_commit(su32(&S.mma_done));
+                            d_pending = true;
+                            waitb(&S.mma_done, dpar);
+                            if (!ok) break;
+                            d_pending = false;
+                            dpar ^= 1u;
+                        }
+                        mbar_expect_tx(su32(&S.b_full), (uint32_t)(s * kUpdSliceBytes));
+                        bulk_g2s(b_base, wimg + (size_t)key * slices * kUpdSliceBytes,
+                                 (uint32_t)(s * kUpdSliceBytes), su32(&S.b_full));
+                        b_pending = true;
+                        waitb(&S.b_full, bpar);
                         if (!ok) break;
-                        d_pending = false;
-                        dpar ^= 1u;
+                        b_pending = false;
+                        bpar ^= 1u;
+                        prev_key = key;
                     }
-                    mbar_expect_tx(su32(&S.b_full), (uint32_t)(s * kUpdSliceBytes));
-                    bulk_g2s(b_base, wimg + (size_t)q * slices * kUpdSliceBytes,
-                             (uint32_t)(s * kUpdSliceBytes), su32(&S.b_full));
-                    b_pending = true;
-                    waitb(&S.b_full, bpar);
-                    if (!ok) break;
-                    b_pending = false;
-                    bpar ^= 1u;
-                    prev_q = q;
-                }
-                const long long g0 = (long long)j * s;
-                // phase A: groups 2..hA+1 from A_1..A_hA
-                for (int t = 1; t <= hA && ok; ++t) {
-                    const int sl = t - 1;
-                    const int nuse = (sl + UD_PA + 1 <= s) ? 2 : 1;
-                    waitb(&S.a_full[sl], (uint32_t)(((long long)j * nuse) & 1));
-                    if (t == 1) wait_slots(g0, 2, hA + 1);
-                    if (!ok) break;
-                    tc_fence_after();
-                    issue(g0, t, 1, hA + 1 - t);
-                    const long long gf = g0 + t - 1;  // group t + 1 is complete
-                    mma_commit(su32(&S.t_full[gf & (UD_TSLOTS - 1)]));
-                    if (!phaseB) mma_commit(su32(&S.a_empty[sl]));
-                }
-                // phase B: groups 8..s+1 from A_1..A_s
-                for (int t = 1; phaseB && t <= s && ok; ++t) {
-                    const int sl = (t - 1) % UD_ASLOTS;
-                    if (t > UD_PA) waitb(&S.a_full[sl], (uint32_t)(((long long)j * 2 + 1) & 1));
-                    if (t == 1) wait_slots(g0, UD_PA + 2, s + 1);
-                    if (!ok) break;
-                    tc_fence_after();
-                    issue(g0, t, max(1, UD_PA + 2 - t), s + 1 - t);
-                    mma_commit(su32(&S.a_empty[sl]));
-                    if (t + 1 >= UD_PA + 2) mma_commit(su32(&S.t_full[(g0 + t - 1) & (UD_TSLOTS - 1)]));
+                    const long long g0 = (long long)J * s;
+                    // phase A: groups 2..hA+1 from A_1..A_hA
+                    for (int t = 1; t <= hA && ok; ++t) {
+                        const int sl = t - 1;
+                        const int nuse = (sl + UD_PA + 1 <= s) ? 2 : 1;
+                        waitb(&S.a_full[sl], (uint32_t)((J * nuse) & 1));
+                        if (t == 1) wait_slots(g0, 2, hA + 1);
+                        if (!ok) break;
+                        tc_fence_after();
+                        issue(g0, t, 1, hA + 1 - t);
+                        const long long gf = g0 + t - 1;  // group t + 1 is complete
+                        mma_commit(su32(&S.t_full[gf & (UD_TSLOTS - 1)]));
+                        if (!phaseB) mma_commit(su32(&S.a_empty[sl]));
+                    }
+                    // phase B: groups 8..s+1 from A_1..A_s
+                    for (int t = 1; phaseB && t <= s && ok; ++t) {
+                        const int sl = (t - 1) % UD_ASLOTS;
+                        if (t > UD_PA) waitb(&S.a_full[sl], (uint32_t)((J * 2 + 1) & 1));
+                        if (t == 1) wait_slots(g0, UD_PA + 2, s + 1);
+                        if (!ok) break;
+                        tc_fence_after();
+                        issue(g0, t, max(1, UD_PA + 2 - t), s + 1 - t);
+                        mma_commit(su32(&S.a_empty[sl]));
+                        if (t + 1 >= UD_PA + 2) mma_commit(su32(&S.t_full[(g0 + t - 1) & (UD_TSLOTS - 1)]));
+                    }
                 }
                 ud_next(ctl, npairs, m, q, r);
             }
@@ -504,117 +639,122 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
             ichunk[i] = (uint32_t)(ipos[i] * 2) >> 4;
             ilow[i] = (uint32_t)(ipos[i] * 2) & 15u;
         }
+        int J = 0;  // tile products of this CTA so far
         for (int j = 0; j < count && ok; ++j) {
             const int32_t *pd = pairs + 4 * q;
             const int k = pd[1] + pd[3];
+            const int Tq = WIDE ? ud_ntiles<CPLX>(k) : 1;
             const int64_t rows = pair_rows(ctl, q, m);
             const int64_t l0 = (int64_t)r * UD_M;
-            const int rho = j % UD_RING;
-            int64_t colx[NC];
-            int ex[NV];
+            for (int sp = 0; sp < Tq * Tq && ok; ++sp, ++J) {
+                const int kc = sp % Tq;  // the tile of X this product reads
+                const int rho = (int)(J % UD_RING);
+                int64_t colx[NC];
+                int ex[NV];
 #pragma unroll
-            for (int v = 0; v < NC; ++v) {
-                const int c = CPLX ? 2 * cl + v : vcol[v];
-                colx[v] = c < k ? ud_gcol(pd, c) : -1;
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const int64_t cx = colx[CPLX ? (v & 1) : v];
-                ex[v] = cx >= 0 ? cexp[cx] : -1021;
-            }
-            if (j >= UD_RING) waitb(&S.r_empty[rho], (uint32_t)((j / UD_RING - 1) & 1));
-            for (int p = 0; p < 4 && ok; ++p) {
-                const int t0 = 3 * p + 1;
-                if (t0 > s) break;
-                const int t1 = min(3 * p + 3, s);
-                for (int hb = 0; hb < 2 && ok; ++hb) {
-                    // this batch's values, all loads in flight together
-                    double x[HB][NV];
-#pragma unroll
-                    for (int i = 0; i < HB; ++i) {
-                        const int task = bw + UD_BLD * (hb * HB + i);
-                        const bool has = hb * HB + i < TPW && task < TASKS;
-                        const int64_t l = l0 + task * RPT + rr;
-#pragma unroll
-                        for (int v = 0; v < NC; ++v) {
-                            const bool in = has && colx[v] >= 0 && l < rows;
-                            if (CPLX) {
-                                double2 z = make_double2(0.0, 0.0);
-                                if (in) z = reinterpret_cast<const double2 *>(Gs)[colx[v] * ld + l];
-                                x[i][v] = rr ? z.y : z.x;      // first item: re (rr = 0) or im
-                                x[i][v + 2] = rr ? z.x : z.y;
-                            } else {
-                                x[i][v] = in ? Gs[colx[v] * ld + l] : 0.0;
-                            }
-                        }
-                    }
-                    if (hb == 0) {  // the slots of this pass's digits are free
-                        for (int t = t0; t <= t1; ++t) {
-                            const int sl = (t - 1) % UD_ASLOTS;
-                            const int nuse = (sl + UD_PA + 1 <= s) ? 2 : 1;
-                            const long long use = (long long)j * nuse + (t > UD_PA ? 1 : 0);
-                            if (use >= 1) waitb(&S.a_empty[sl], (uint32_t)((use - 1) & 1));
-                        }
-                        if (!ok) break;
-                    }
-                    uint8_t *slotp[3];  // slots of the pass's digits t0, t0 + 1, t0 + 2
-#pragma unroll
-                    for (int dd = 0; dd < 3; ++dd)
-                        slotp[dd] = sA + (size_t)((t0 - 1 + dd) % UD_ASLOTS) * UD_ATILE;
-#pragma unroll
-                    for (int i = 0; i < HB; ++i) {
-                        const int task = bw + UD_BLD * (hb * HB + i);
-                        if (hb * HB + i >= TPW || task >= TASKS) break;
-                        const int row = task * RPT + rr;  // row of the tile
-                        int rexp;
-                        if (p == 0) {
-                            // row exponent: max over the row of exp(x) - e_a
-                            int mx = -100000;
-#pragma unroll
-                            for (int v = 0; v < NV; ++v) {
-                                const unsigned long long mb = dg_mag_bits(x[i][v]);
-                                if (mb) mx = max(mx, dg_exp_of_bits(mb) - ex[v]);
-                            }
-#pragma unroll
-                            for (int o = 1; o < (CPLX ? 16 : 8); o <<= 1)
-                                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                            rexp = mx == -100000 ? -1021 : mx;
-                            if (cl == 0) S.rexp[rho][row] = rexp;
-                        } else {
-                            rexp = S.rexp[rho][row];
-                        }
-                        // complex: the value order differs between rr = 0 and 1, and
-                        // e_a is the same for the real and imaginary part of a column
-                        uint32_t w[NV];
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) w[v] = dg_window21(x[i][v], rexp + ex[v], p);
-                        const uint32_t rowbase = (uint32_t)row * 128u, x7 = (uint32_t)row & 7u;
-#pragma unroll
-                        for (int it = 0; it < NI; ++it) {
-                            const uint32_t off = rowbase + ((ichunk[it] ^ x7) << 4) + ilow[it];
-                            const bool n0 = __double_as_longlong(x[i][2 * it]) < 0;
-                            const bool n1 = __double_as_longlong(x[i][2 * it + 1]) < 0;
-                            const uint32_t bias = (n0 ? 0xE400u : 0x6400u) | ((n1 ? 0xE400u : 0x6400u) << 16);
-                            const uint32_t add = bias ^ 0x80008000u;
-#pragma unroll
-                            for (int dd = 0; dd < 3; ++dd) {
-                                if (t0 + dd > t1) break;
-                                const uint32_t d0 = (w[2 * it] >> (14 - 7 * dd)) & 127u;
-                                const uint32_t d1 = (w[2 * it + 1] >> (14 - 7 * dd)) & 127u;
-                                const uint32_t v = d0 | (d1 << 16) | bias;
-                                uint32_t h2;
-                                asm("add.rn.f16x2 %0, %1, %2;" : "=r"(h2) : "r"(v), "r"(add));
-                                *reinterpret_cast<uint32_t *>(slotp[dd] + off) = h2;
-                            }
-                        }
-                    }
+                for (int v = 0; v < NC; ++v) {
+                    const int c = CPLX ? 32 * kc + 2 * cl + v : 64 * kc + vcol[v];
+                    colx[v] = c < k ? ud_gcol(pd, c) : -1;
                 }
-                if (!ok) break;
-                fence_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    for (int t = t0; t <= t1; ++t) mbar_arrive(su32(&S.a_full[(t - 1) % UD_ASLOTS]));
-                    if (p == 0) mbar_arrive(su32(&S.r_full[rho]));
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const int64_t cx = colx[CPLX ? (v & 1) : v];
+                    ex[v] = cx >= 0 ? cexp[cx] : -1021;
+                }
+                if (J >= UD_RING) waitb(&S.r_empty[rho], (uint32_t)((J / UD_RING - 1) & 1));
+                for (int p = 0; p < 4 && ok; ++p) {
+                    const int t0 = 3 * p + 1;
+                    if (t0 > s) break;
+                    const int t1 = min(3 * p + 3, s);
+                    for (int hb = 0; hb < 2 && ok; ++hb) {
+                        // this batch's values, all loads in flight together
+                        double x[HB][NV];
+#pragma unroll
+                        for (int i = 0; i < HB; ++i) {
+                            const int task = bw + UD_BLD * (hb * HB + i);
+                            const bool has = hb * HB + i < TPW && task < TASKS;
+                            const int64_t l = l0 + task * RPT + rr;
+#pragma unroll
+                            for (int v = 0; v < NC; ++v) {
+                                const bool in = has && colx[v] >= 0 && l < rows;
+                                if (CPLX) {
+                                    double2 z = make_double2(0.0, 0.0);
+                                    if (in) z = reinterpret_cast<const double2 *>(Gs)[colx[v] * ld + l];
+                                    x[i][v] = rr ? z.y : z.x;      // first item: re (rr = 0) or im
+                                    x[i][v + 2] = rr ? z.x : z.y;
+                                } else {
+                                    x[i][v] = in ? Gs[colx[v] * ld + l] : 0.0;
+                                }
+                            }
+                        }
+                        if (hb == 0) {  // the slots of this pass's digits are free
+                            for (int t = t0; t <= t1; ++t) {
+                                const int sl = (t - 1) % UD_ASLOTS;
+                                const int nuse = (sl + UD_PA + 1 <= s) ? 2 : 1;
+                                const long long use = (long long)J * nuse + (t > UD_PA ? 1 : 0);
+                                if (use >= 1) waitb(&S.a_empty[sl], (uint32_t)((use - 1) & 1));
+                            }
+                            if (!ok) break;
+                        }
+                        uint8_t *slotp[3];  // slots of the pass's digits t0, t0 + 1, t0 + 2
+#pragma unroll
+                        for (int dd = 0; dd < 3; ++dd)
+                            slotp[dd] = sA + (size_t)((t0 - 1 + dd) % UD_ASLOTS) * UD_ATILE;
+#pragma unroll
+                        for (int i = 0; i < HB; ++i) {
+                            const int task = bw + UD_BLD * (hb * HB + i);
+                            if (hb * HB + i >= TPW || task >= TASKS) break;
+                            const int row = task * RPT + rr;  // row of the tile
+                            int rexp;
+                            if (p == 0) {
+                                // row exponent: max over the row of exp(x) - e_a
+                                int mx = -100000;
+#pragma unroll
+                                for (int v = 0; v < NV; ++v) {
+                                    const unsigned long long mb = dg_mag_bits(x[i][v]);
+                                    if (mb) mx = max(mx, dg_exp_of_bits(mb) - ex[v]);
+                                }
+#pragma unroll
+                                for (int o = 1; o < (CPLX ? 16 : 8); o <<= 1)
+                                    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                                rexp = mx == -100000 ? -1021 : mx;
+                                if (cl == 0) S.rexp[rho][row] = rexp;
+                            } else {
+                                rexp = S.rexp[rho][row];
+                            }
+                            // complex: the value order differs between rr = 0 and 1, and
+                            // e_a is the same for the real and imaginary part of a column
+                            uint32_t w[NV];
+#pragma unroll
+                            for (int v = 0; v < NV; ++v) w[v] = dg_window21(x[i][v], rexp + ex[v], p);
+                            const uint32_t rowbase = (uint32_t)row * 128u, x7 = (uint32_t)row & 7u;
+#pragma unroll
+                            for (int it = 0; it < NI; ++it) {
+                                const uint32_t off = rowbase + ((ichunk[it] ^ x7) << 4) + ilow[it];
+                                const bool n0 = __double_as_longlong(x[i][2 * it]) < 0;
+                                const bool n1 = __double_as_longlong(x[i][2 * it + 1]) < 0;
+                                const uint32_t bias = (n0 ? 0xE400u : 0x6400u) | ((n1 ? 0xE400u : 0x6400u) << 16);
+                                const uint32_t add = bias ^ 0x80008000u;
+#pragma unroll
+                                for (int dd = 0; dd < 3; ++dd) {
+                                    if (t0 + dd > t1) break;
+                                    const uint32_t d0 = (w[2 * it] >> (14 - 7 * dd)) & 127u;
+                                    const uint32_t d1 = (w[2 * it + 1] >> (14 - 7 * dd)) & 127u;
+                                    const uint32_t v = d0 | (d1 << 16) | bias;
+                                    uint32_t h2;
+                                    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(h2) : "r"(v), "r"(add));
+                                    *reinterpret_cast<uint32_t *>(slotp[dd] + off) = h2;
+                                }
+                            }
+                        }
+                    }
+                    if (!ok) break;
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        for (int t = t0; t <= t1; ++t) mbar_arrive(su32(&S.a_full[(t - 1) % UD_ASLOTS]));
+                        if (p == 0) mbar_arrive(su32(&S.r_full[rho]));
+                    }
                 }
             }
             ud_next(ctl, npairs, m, q, r);
@@ -629,34 +769,49 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
 }
 
 // The W-side operand of the update (ud_wimage_build) for every active pair of
-// a step, from W_P in global memory: one block per pair. The solver's inner
-// solve builds it itself; this kernel serves the building-block entry point.
+// a step, from W_P in global memory: one block per (pair, W tile (kc, nc)),
+// images at [pair][nc][kc] with tmax tiles per side. The solver's inner solve
+// builds the image of a narrow pivot itself; this kernel serves wide pivots
+// and the building-block entry point.
 template <bool CPLX>
 __global__ void __launch_bounds__(256) wimage_kernel(const double *__restrict__ W, int kmax,
                                                      const int32_t *__restrict__ pairs,
                                                      const int32_t *__restrict__ cexp, int slices,
-                                                     uint8_t *__restrict__ img,
+                                                     int tmax, uint8_t *__restrict__ img,
                                                      int32_t *__restrict__ wexp, StepCtl ctl) {
     constexpr int E = CPLX ? 2 : 1;
+    constexpr int CW = CPLX ? 32 : 64;  // pivot columns per tile
     __shared__ int s_xexp[kUdPositions], s_wexp[kUdPositions];
-    const int q = blockIdx.x;
+    const int q = blockIdx.x, sp = blockIdx.y;
     if (pair_passthrough(ctl, q)) return;
     const int32_t *pd = pairs + 4 * q;
     const int k = pd[1] + pd[3];
+    const int Tq = ud_ntiles<CPLX>(k);
+    const int nc = sp / tmax, kc = sp % tmax;
+    if (nc >= Tq || kc >= Tq) return;
+    const int kr = min(CW, k - CW * kc), kn = min(CW, k - CW * nc);
     for (int a = threadIdx.x; a < kUdPositions; a += blockDim.x) {
         const int c = CPLX ? (a & 31) : a;
-        s_xexp[a] = c < k ? cexp[ud_gcol(pd, c)] : -1021;
+        s_xexp[a] = c < kr ? cexp[ud_gcol(pd, CW * kc + c)] : -1021;
     }
     __syncthreads();
     const double *Wp = W + (size_t)q * kmax * kmax * E;
-    auto wacc = [&](int rr, int cc, int part) -> double { return Wp[((size_t)cc * kmax + rr) * E + part]; };
-    ud_wimage_build<CPLX>(wacc, k, s_xexp, s_wexp, slices, img + (size_t)q * slices * kUpdSliceBytes,
-                          wexp + (size_t)q * kUdPositions, threadIdx.x, blockDim.x);
+    auto wacc = [&](int rr, int cc, int part) -> double {
+        return Wp[((size_t)(CW * nc + cc) * kmax + CW * kc + rr) * E + part];
+    };
+    const size_t tile = (size_t)q * tmax * tmax + sp;
+    ud_wimage_build<CPLX>(wacc, kr, kn, kc == nc, s_xexp, s_wexp, slices,
+                          img + tile * slices * kUpdSliceBytes, wexp + tile * kUdPositions, threadIdx.x,
+                          blockDim.x);
 }
 
 }  // namespace
 
-size_t ud_scratch_bytes(int nctas) { return (size_t)nctas * UD_SCRATCH_PER_CTA; }
+int ud_max_tiles(bool cplx, int kmax) { return cplx ? ud_ntiles<true>(kmax) : ud_ntiles<false>(kmax); }
+
+size_t ud_scratch_bytes(int nctas, int tmax) {
+    return (size_t)nctas * ud_scratch_longs(tmax) * sizeof(long long);
+}
 
 int ud_num_ctas() {
     static int sms[64] = {0};
@@ -673,12 +828,13 @@ int ud_num_ctas() {
 cudaError_t launch_wimage(bool cplx, const double *W, int kmax, const int32_t *pairs, int npairs,
                           const int32_t *cexp, const UpdDigits &ud, cudaStream_t st, StepCtl ctl) {
     if (npairs <= 0) return cudaSuccess;
-    if ((cplx ? 2 * kmax : kmax) > kUdPositions || ud.slices < 1 || ud.slices > kUdMaxSlices)
-        return cudaErrorInvalidValue;
+    const int tmax = ud_max_tiles(cplx, kmax);
+    if (tmax > kUdMaxTiles || ud.slices < 1 || ud.slices > kUdMaxSlices) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)npairs, (unsigned)(tmax * tmax));
     if (cplx)
-        wimage_kernel<true><<<npairs, 256, 0, st>>>(W, kmax, pairs, cexp, ud.slices, ud.img, ud.wexp, ctl);
+        wimage_kernel<true><<<grid, 256, 0, st>>>(W, kmax, pairs, cexp, ud.slices, tmax, ud.img, ud.wexp, ctl);
     else
-        wimage_kernel<false><<<npairs, 256, 0, st>>>(W, kmax, pairs, cexp, ud.slices, ud.img, ud.wexp, ctl);
+        wimage_kernel<false><<<grid, 256, 0, st>>>(W, kmax, pairs, cexp, ud.slices, tmax, ud.img, ud.wexp, ctl);
     return cudaGetLastError();
 }
 
@@ -688,26 +844,25 @@ cudaError_t launch_update_digits(bool cplx, const double *Gs, double *Gd, int64_
                                  unsigned long long *counters, cudaStream_t st, StepCtl ctl) {
     if (npairs <= 0) return cudaSuccess;
     const int s = ud.slices;
-    if ((cplx ? 2 * kmax : kmax) > kUdPositions || s < 1 || s > kUdMaxSlices || !ud.img ||
-        !ud.wexp || !scratch || nctas < 1)
+    const int tmax = ud_max_tiles(cplx, kmax);
+    if (tmax > kUdMaxTiles || s < 1 || s > kUdMaxSlices || !ud.img || !ud.wexp || !scratch || nctas < 1)
         return cudaErrorInvalidValue;
     // skipped pairs are left in place, so an out-of-place update needs every pair active
     if (Gd != Gs && ctl.flags) return cudaErrorInvalidValue;
     const size_t smem = (size_t)s * kUpdSliceBytes + (size_t)UD_ASLOTS * UD_ATILE + 1024;
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<nctas, UD_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, npairs, cexp, ud.img, ud.wexp, ud.slices, s,
+                                              tmax, scratch, counters, ctl.wait_ns, ctl);
+        return cudaSuccess;
+    };
     cudaError_t e;
-    if (cplx) {
-        auto kern = update_digits_kernel<true>;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-        kern<<<nctas, UD_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, npairs, cexp, ud.img, ud.wexp,
-                                              ud.slices, s, scratch, counters, ctl.wait_ns, ctl);
-    } else {
-        auto kern = update_digits_kernel<false>;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-        kern<<<nctas, UD_THREADS, smem, st>>>(Gs, Gd, ld, m, pairs, npairs, cexp, ud.img, ud.wexp,
-                                              ud.slices, s, scratch, counters, ctl.wait_ns, ctl);
-    }
+    if (cplx)
+        e = tmax > 1 ? run(update_digits_kernel<true, true>) : run(update_digits_kernel<true, false>);
+    else
+        e = tmax > 1 ? run(update_digits_kernel<false, true>) : run(update_digits_kernel<false, false>);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -124,14 +124,14 @@ def test_kernel_entry_points_validate_arguments(jj):
     assert lib.jjk_extract(0, None, 1, 1, 1, None, None, None, 0, None) == jj.JJ_INVALID_ARG
     assert lib.jjacobi_extract(None, None, None, 0, 0) == jj.JJ_INVALID_ARG
     # gemm outside jj_gemm, and digit products asked for a pivot wider than they
-    # take (complex kmax 40: real width 80 > 64); every case returns before any
+    # take (complex kmax 129: real width 258 > 256); every case returns before any
     # device work (the dummy addresses are never dereferenced)
     x = 256
     for g in (-1, 4):
         assert lib.jjk_gram(0, g, x, 1, 1, x, 0, x, 1, None) == jj.JJ_INVALID_ARG
         assert lib.jjk_update(0, g, x, x, 1, 1, x, 0, x, 1, None) == jj.JJ_INVALID_ARG
     for g in (jj.JJ_GEMM_OZAKI_FP16, jj.JJ_GEMM_OZAKI_GRAM):
-        assert lib.jjk_gram(jj.JJ_C128, g, x, 1, 1, x, 0, x, 40, None) == jj.JJ_INVALID_ARG
+        assert lib.jjk_gram(jj.JJ_C128, g, x, 1, 1, x, 0, x, 129, None) == jj.JJ_INVALID_ARG
     # negative sizes
     assert lib.jjk_plain_step(0, x, 1, 1, -1, x, 0, x, x, 0.0, x, None) == jj.JJ_INVALID_ARG
     assert lib.jjk_plain_step(0, x, 1, 1, 1, x, -1, x, x, 0.0, x, None) == jj.JJ_INVALID_ARG

@@ -44,9 +44,10 @@ def test_three_level_complex_ragged(gemm):
 
 def test_three_level_agrees_with_two_level_wide_pivot():
     """Outer pivots of 256 columns (the 16 384-column workload's b = 128) with
-    inner blocks of 16, at n = 1024: the outer contractions run in FP64, the
-    inner ones as digit products; eigenvalues by construction and against the
-    two-level form."""
+    inner blocks of 16, at n = 1024: the outer contractions run as digit
+    products over 4 x 4 tiles of 64 positions, the inner ones as single-tile
+    digit products; eigenvalues by construction and against the two-level
+    form in FP64."""
     require_gpu()
     P = synth.make_workload("threelevel_f64_n16384_b128", n=1024)
     three = solve_gpu(P.G, P.J, block_width=128, inner_block_width=16, gemm=1)
