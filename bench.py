@@ -216,7 +216,7 @@ def bench_config(args, P, world: int = 1) -> dict:
     name = re.sub(r"_b\d+$", f"_b{args.block_width}", args.workload)
     return {"workload": name, "recipe": args.workload, "m": P.m, "n": P.n,
             "block_width": args.block_width, "gemm": args.gemm,
-            "update_digits": (args.digits or 12) if args.gemm == "ozaki" and args.block_width else None,
+            "update_digits": (args.digits or 11) if args.gemm == "ozaki" and args.block_width else None,
             "strategy": args.strategy, "order": "round_robin",
             "pivot_factor": getattr(args, "pivot_factor", "cholesky"),
             "l2": "inputs larger than L2 (G = 256 MiB; every step reads and writes it)",
@@ -305,7 +305,7 @@ def kernel_roofline(jj, P, times, info, gemm_gram_digits, gemm_upd_digits, peaks
                 "family_ms": {"plain_step": ms}}
     k = 2.0 * P.n / info["nbl"]
     K2 = 2 * k if cplx else k
-    upd_digits = info.get("update_digits", 12)
+    upd_digits = info.get("update_digits", 11)
     fam = {f: times[f] for f in ("gram", "inner", "update")}
     dom = max(fam, key=lambda f: fam[f][0])
     ms, launches = fam[dom]
@@ -440,7 +440,7 @@ def run_ours(args):
     stream.synchronize()
     times = hp_.jjacobi_kernel_times()
     hp_.close()
-    roof = kernel_roofline(jj, P, times, dict(pinfo_.as_dict(), update_digits=args.digits or 12),
+    roof = kernel_roofline(jj, P, times, dict(pinfo_.as_dict(), update_digits=args.digits or 11),
                            g_gram == jj.JJ_GEMM_OZAKI_FP16,
                            g_upd == jj.JJ_GEMM_OZAKI_FP16, _peaks())
     # DRAM bytes per launch from the ncu capture of the same kernel (one step of
@@ -722,7 +722,7 @@ def main():
     ap.add_argument("--pivot-factor", default="cholesky", choices=["cholesky", "special"],
                     help="full-block pivot factor: Cholesky of the pivot, or (3.9)-(3.11)")
     ap.add_argument("--digits", type=int, default=0,
-                    help="digits per operand of the split-precision update (0: 12)")
+                    help="digits per operand of the split-precision update (0: 11)")
     ap.add_argument("--strategy", default="oriented", choices=["oriented", "full"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-plain", dest="plain", action="store_false")

@@ -61,9 +61,9 @@ typedef enum { JJ_ORDER_ROUND_ROBIN = 0, JJ_ORDER_MODULUS = 1 } jj_order;
  *   JJ_GEMM_OZAKI_FP16  both as sums of exact fp16 digit products on the
  *                       tensor cores (tcgen05), recombined in integers; the
  *                       update carries one exponent per row and per column,
- *                       and with its default 12 digits (84 bits) per operand
- *                       its error stays within FP64's per-entry bound on
- *                       strongly graded inputs;
+ *                       and with its default 11 balanced 8-bit digits
+ *                       (88 bits) per operand its error stays within FP64's
+ *                       per-entry bound on strongly graded inputs;
  *   JJ_GEMM_OZAKI_GRAM  the Gram as digit products, the update in FP64;
  *   JJ_GEMM_AUTO        JJ_GEMM_OZAKI_GRAM when the pivot fits the digit
  *                       kernels, else FP64.
@@ -131,8 +131,8 @@ typedef struct {
     int32_t inner_block_width; /* 0: two-level; >0: inner block width (three-level) */
     int32_t order;             /* jj_order (blocked form; the plain form is round-robin) */
     int32_t gemm;              /* jj_gemm */
-    int32_t ozaki_slices;      /* 7-bit digits per operand of the split-precision update,
-                                  1..12, 0: 12 */
+    int32_t ozaki_slices;      /* balanced 8-bit digits per operand of the split-precision
+                                  update, 1..11, 0: 11 */
     double tol;                /* <= 0: 128 * 2^-53; rotate when |a_rs| > tol sqrt(a_rr a_ss) */
     int32_t max_sweeps;        /* <= 0: 60 */
     int32_t inner_max_sweeps;  /* <= 0: 30 (inner J-Jacobi on R, blocked form) */

@@ -42,7 +42,7 @@ struct Plan {
 struct Three {
     bool on = false;
     int ib = 0, kmax_in = 0;
-    int64_t ldx = 0;
+    int64_t ldx = 0, xcols = 0;
     int max_np = 0, max_slots = 0;
     std::vector<std::vector<int>> np, slot0;  // [outer step][inner step]
     std::vector<int> steps;                   // inner steps per inner sweep, by outer step
@@ -96,7 +96,7 @@ struct jj_ctx {
     int32_t *d_mod = nullptr, *d_clean = nullptr, *d_flags = nullptr, *d_sweep = nullptr;
     uint8_t *d_wdig = nullptr;          // W-side digits of the digit update (per pair)
     int32_t *d_wdexp = nullptr;
-    int oz_slices_gram = 8, oz_slices_update = 12;
+    int oz_slices_gram = 8, oz_slices_update = kUdMaxSlices;
     long long *d_udscr = nullptr;       // scratch of the digit update (per persistent block)
     int ud_nctas = 0;
     int ud_tmax = 0;                    // widest pivot (64-position tiles per side) it serves
@@ -385,6 +385,7 @@ int build_three(jj_ctx *c, const std::vector<int32_t> &tab) {
     T.ozaki_update = T.ozaki && c->p.gemm == JJ_GEMM_OZAKI_FP16;
     const size_t np = (size_t)std::max(P.maxnp, 1), npi = (size_t)std::max(T.max_np, 1);
     const size_t xcols = np * P.kmax;
+    T.xcols = (int64_t)xcols;
     JJ_CUDA(dmalloc(&T.d_tab, itab.size()));
     JJ_CUDA(dmalloc(&T.d_prob, iprob.size()));
     JJ_CUDA(cudaMemcpy(T.d_tab, itab.data(), itab.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -694,7 +695,7 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
                 ++L;
             }
             if (c->ozaki_update)
-                JJ_CUDA(launch_update_digits(c->cplx, c->Gw, c->Gw, P.ldw, mrows, pr, np, P.kmax,
+                JJ_CUDA(launch_update_digits(c->cplx, c->Gw, c->Gw, P.ldw, mrows, P.ncols, pr, np, P.kmax, P.kmax / 2,
                                              c->d_cexp, ud, c->d_udscr, c->ud_nctas, c->d_cnt, st,
                                              ctl));
             else
@@ -825,8 +826,8 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
                 JJ_CUDA(launch_inner(c->cplx, T.Ain, T.Win, T.kmax_in, ip, ni, T.d_JX, c->tol,
                                      c->inner_max_sweeps, 0, T.d_cnt, st, ic, ud, ipass));
                 if (T.ozaki_update)
-                    JJ_CUDA(launch_update_digits(c->cplx, T.X, T.X, T.ldx, 2 * P.kmax, ip, ni,
-                                                 T.kmax_in, T.d_cexp2, ud, c->d_udscr, c->ud_nctas,
+                    JJ_CUDA(launch_update_digits(c->cplx, T.X, T.X, T.ldx, 2 * P.kmax, T.xcols, ip, ni,
+                                                 T.kmax_in, T.kmax_in / 2, T.d_cexp2, ud, c->d_udscr, c->ud_nctas,
                                                  T.d_cnt, st, ic));
                 else
                     JJ_CUDA(launch_update(c->cplx, c->p.gemm, T.X, T.X, T.ldx, 2 * P.kmax, ip, ni,
@@ -854,7 +855,7 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
             oud.cexp = c->d_cexp;
             oud.slices = c->oz_slices_update;
             JJ_CUDA(launch_wimage(c->cplx, c->Wblk, P.kmax, pr, np, c->d_cexp, oud, st, ctl));
-            JJ_CUDA(launch_update_digits(c->cplx, c->Gw, c->Gw, P.ldw, c->m, pr, np, P.kmax,
+            JJ_CUDA(launch_update_digits(c->cplx, c->Gw, c->Gw, P.ldw, c->m, P.ncols, pr, np, P.kmax, P.kmax / 2,
                                          c->d_cexp, oud, c->d_udscr, c->ud_nctas, c->d_cnt, st, ctl));
             L += 1;
         }
@@ -1780,14 +1781,17 @@ int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld
         if (!ozaki_supported(cplx, kmax)) return JJ_INVALID_ARG;
         cudaStream_t st = (cudaStream_t)stream;
         int64_t ncols = 0;
+        int maxblk = 0;
         {
             std::vector<int32_t> hp((size_t)npairs * 4);
             JJ_CUDA(cudaMemcpyAsync(hp.data(), pairs, hp.size() * sizeof(int32_t),
                                     cudaMemcpyDeviceToHost, st));
             JJ_CUDA(cudaStreamSynchronize(st));
-            for (int q = 0; q < npairs; ++q)
+            for (int q = 0; q < npairs; ++q) {
                 ncols = std::max<int64_t>(ncols, std::max(hp[4 * q] + hp[4 * q + 1],
                                                           hp[4 * q + 2] + hp[4 * q + 3]));
+                maxblk = std::max(maxblk, std::max(hp[4 * q + 1], hp[4 * q + 3]));
+            }
         }
         // Scratch from the stream-ordered allocator: column exponents, the W-side
         // digits of every pair, and the update's row blocks.
@@ -1808,8 +1812,8 @@ int jjk_update(int32_t dtype, int32_t gemm, const void *Gs, void *Gd, int64_t ld
         if (e == cudaSuccess) e = launch_colexp(cplx, (const double *)Gs, ld, m, ncols, cexp, st);
         if (e == cudaSuccess) e = launch_wimage(cplx, W, kmax, pairs, npairs, cexp, ud, st);
         if (e == cudaSuccess)
-            e = launch_update_digits(cplx, (const double *)Gs, (double *)Gd, ld, m, pairs, npairs,
-                                     kmax, cexp, ud, scr, nctas, nullptr, st);
+            e = launch_update_digits(cplx, (const double *)Gs, (double *)Gd, ld, m, ncols, pairs, npairs,
+                                     kmax, maxblk, cexp, ud, scr, nctas, nullptr, st);
         if (cexp) cudaFreeAsync(cexp, st);
         if (ud.img) cudaFreeAsync(ud.img, st);
         if (ud.wexp) cudaFreeAsync(ud.wexp, st);

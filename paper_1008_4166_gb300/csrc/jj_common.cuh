@@ -140,7 +140,7 @@ struct UpdDigits {
     int slices = 0;
 };
 constexpr int kUpdSliceBytes = 64 * 128;
-constexpr int kUdMaxSlices = 12;  // digits per operand of the update (84 bits)
+constexpr int kUdMaxSlices = 11;  // balanced 8-bit digits per operand of the update (88 bits)
 constexpr int kUdMaxTiles = 4;    // 64-position tiles per pivot side (256 real-form positions)
 
 // Decide (Gram kernels) whether pair q of this step can be skipped: the slot was
@@ -236,11 +236,19 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
 // launch_wimage), cexp the column exponents of Gs, scratch
 // ud_scratch_bytes(nctas, ud_max_tiles(cplx, kmax)) bytes; nctas persistent
 // blocks (ud_num_ctas()).
+// ncols: columns of Gs (the extent the narrow kernel's tensor map covers);
+// maxblk: the largest block of any pair (0: unknown). Narrow pivots whose
+// blocks fit a TMA box run update_narrow_kernel (jj_update_narrow.cu), the
+// others update_digits_kernel.
 cudaError_t launch_update_digits(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
-                                 const int32_t *pairs, int npairs, int kmax, const int32_t *cexp,
-                                 const UpdDigits &ud, long long *scratch, int nctas,
+                                 int64_t ncols, const int32_t *pairs, int npairs, int kmax, int maxblk,
+                                 const int32_t *cexp, const UpdDigits &ud, long long *scratch, int nctas,
                                  unsigned long long *counters, cudaStream_t st,
                                  StepCtl ctl = StepCtl());
+bool un_supported(bool cplx, const double *Gs, int64_t ld, int64_t m, int64_t ncols, int kmax, int maxblk);
+cudaError_t launch_update_narrow(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m, int64_t ncols,
+                                 const int32_t *pairs, int npairs, const int32_t *cexp, const UpdDigits &ud,
+                                 int nctas, unsigned long long *counters, cudaStream_t st, StepCtl ctl);
 cudaError_t launch_wimage(bool cplx, const double *W, int kmax, const int32_t *pairs, int npairs,
                           const int32_t *cexp, const UpdDigits &ud, cudaStream_t st,
                           StepCtl ctl = StepCtl());

@@ -1,6 +1,14 @@
-// Digits of the split-precision block update (2.9): fixed-point images with
-// up to twelve 7-bit digits (84 bits) per operand, and the W-side operand of
-// the update built from W_P.
+// Digits of the split-precision block update (2.9): fixed-point images cut
+// into up to eleven balanced 8-bit digits (88 bits) per operand, and the
+// W-side operand of the update built from W_P.
+//
+// Balanced digits. For |x| < 2^e the signed integer V = +-floor(|x| 2^(86-e))
+// (|V| < 2^86, two's complement) plus the bias B = sum_{i=0..10} 128 * 256^i
+// is a non-negative 88-bit number U whose bytes u_i give V = sum (u_i - 128)
+// 256^i. Digit t (1..11) is d_t = u_(11-t) - 128 in [-128, 127], so that
+//     x = 2^(e+2) sum_t d_t 2^(-8t) + r,   |r| < 2^(e-86).
+// A digit is exact in fp16: the bit pattern 0x6500 + u is 1280 + u, and one
+// f16x2 addition of -1408 leaves u - 128 in each half.
 //
 // Real-form positions of the update. A complex pivot X = Xr + i Xi with
 // k <= 32 columns is handled as the real 64-position matrix whose position
@@ -17,63 +25,46 @@ namespace jj {
 
 constexpr int kUdPositions = 64;  // real-form positions of a pivot
 
-// V = floor(|x| 2^(84 - e)) for |x| < 2^e, as hi = V >> 20 (64 bits) and
-// lo = V mod 2^21 (bit 20 is in both). Integer shifts of the significand
-// only; zeros and subnormals give 0.
-struct Fx84 {
-    unsigned long long hi;
-    uint32_t lo;
-};
-__device__ __forceinline__ Fx84 dg_fixed84(double x, int e) {
+// The biased image U = V + B of x relative to 2^e (|x| < 2^e), 96 bits
+// (the top byte is zero). Integer operations on the significand only; zeros
+// and subnormals give V = 0.
+__device__ __forceinline__ unsigned __int128 dg_image88(double x, int e) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int E = (int)((b >> 52) & 0x7FF);
-    Fx84 r{0ull, 0u};
-    if (E == 0) return r;
-    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = E - 991 - e;  // V = mant 2^sh, and sh <= 31 because |x| < 2^e
-    const int shh = sh - 20;
-    if (shh >= 0)
-        r.hi = mant << shh;  // shh <= 11: below 2^64
-    else if (shh > -64)
-        r.hi = mant >> (-shh);
-    if (sh >= 0)
-        r.lo = (uint32_t)((mant << sh) & 0x1FFFFFull);  // the low bits survive the wrap
-    else if (sh > -64)
-        r.lo = (uint32_t)((mant >> (-sh)) & 0x1FFFFFull);
-    return r;
+    unsigned __int128 M = 0;
+    if (E != 0) {
+        const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = E - 989 - e;  // V = mant 2^sh, sh <= 33 because |x| < 2^e
+        if (sh >= 0)
+            M = (unsigned __int128)mant << sh;
+        else if (sh > -64)
+            M = mant >> (-sh);
+    }
+    if ((long long)b < 0) M = (unsigned __int128)0 - M;
+    const unsigned __int128 B = ((unsigned __int128)0x808080u << 64) |
+                                (unsigned __int128)0x8080808080808080ull;
+    return M + B;
 }
 
-// 7-bit digit t (1..12) of V: bits [84 - 7t, 91 - 7t).
-__device__ __forceinline__ uint32_t dg_digit84(const Fx84 &f, int t) {
-    return t <= 9 ? (uint32_t)(f.hi >> (64 - 7 * t)) & 127u : (f.lo >> (84 - 7 * t)) & 127u;
+// Byte u of digit t (1..11) of an image.
+__device__ __forceinline__ uint32_t dg_byte88(unsigned __int128 U, int t) {
+    return (uint32_t)(U >> (8 * (11 - t))) & 255u;
 }
 
-// The 21-bit window of V = floor(|x| 2^(84 - e)) (|x| < 2^e) that holds the
-// digits 3p + 1, 3p + 2, 3p + 3: bits [63 - 21p, 84 - 21p) of V, so that digit
-// 3p + 1 + i is (window >> (14 - 7i)) & 127. Integer shifts only.
-__device__ __forceinline__ uint32_t dg_window21(double x, int e, int p) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int E = (int)((b >> 52) & 0x7FF);
-    if (E == 0) return 0u;
-    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = E - 1054 - e + 21 * p;  // V >> (63 - 21p) = mant 2^sh, sh <= 31
-    unsigned long long w = 0ull;
-    if (sh >= 0)
-        w = mant << sh;  // only the low 21 bits are kept
-    else if (sh > -64)
-        w = mant >> (-sh);
-    return (uint32_t)w & 0x1FFFFFu;
+// The 24-bit window of U holding the bytes of digits 3p + 1, 3p + 2, 3p + 3
+// (bits [64 - 24p, 88 - 24p), zero below bit 0): digit 3p + 1 + i has byte
+// (window >> (16 - 8i)) & 255.
+__device__ __forceinline__ uint32_t dg_window24(double x, int e, int p) {
+    const unsigned __int128 U = dg_image88(x, e);
+    const int sh = 64 - 24 * p;
+    return (uint32_t)(sh >= 0 ? (U >> sh) : (U << (-sh))) & 0xFFFFFFu;
 }
 
-// Two signed digits as packed fp16 bits: +-d is (1024 + d) - 1024 in fp16 (the
-// bit pattern of +-(1024 + d) is (0x6400 or 0xE400) | d; adding -+1024 leaves
-// +-d exactly).
-__device__ __forceinline__ uint32_t dg_pack2(uint32_t d0, bool n0, uint32_t d1, bool n1) {
-    const uint32_t bias = (n0 ? 0xE400u : 0x6400u) | ((n1 ? 0xE400u : 0x6400u) << 16);
-    const uint32_t add = bias ^ 0x80008000u;
-    const uint32_t v = d0 | (d1 << 16) | bias;
+// Two digits given by their bytes u0, u1 as packed fp16 (u - 128 each).
+__device__ __forceinline__ uint32_t dg_pack2(uint32_t u0, uint32_t u1) {
+    const uint32_t v = u0 | (u1 << 16) | 0x65006500u;
     uint32_t r;
-    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(add));
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(0xE580E580u));
     return r;
 }
 
@@ -125,13 +116,12 @@ __device__ void ud_wimage_build(const WAcc &w, int kr, int kn, bool diag, const 
     for (int it = tid; it < kUdPositions * (kUdPositions / 2); it += nthreads) {
         const int j = it / (kUdPositions / 2), a = (it % (kUdPositions / 2)) * 2;
         const double x0 = ud_w2m<CPLX>(w, kr, kn, diag, a, j), x1 = ud_w2m<CPLX>(w, kr, kn, diag, a + 1, j);
-        const Fx84 f0 = dg_fixed84(x0, s_wexp[j] - xexp[a]);
-        const Fx84 f1 = dg_fixed84(x1, s_wexp[j] - xexp[a + 1]);
-        const bool n0 = __double_as_longlong(x0) < 0, n1 = __double_as_longlong(x1) < 0;
+        const unsigned __int128 U0 = dg_image88(x0, s_wexp[j] - xexp[a]);
+        const unsigned __int128 U1 = dg_image88(x1, s_wexp[j] - xexp[a + 1]);
         const uint32_t off = tc::sw128_off(j, a * 2);
         for (int t = 1; t <= slices; ++t)
             *reinterpret_cast<uint32_t *>(img + (size_t)(t - 1) * kUpdSliceBytes + off) =
-                dg_pack2(dg_digit84(f0, t), n0, dg_digit84(f1, t), n1);
+                dg_pack2(dg_byte88(U0, t), dg_byte88(U1, t));
     }
     for (int j = tid; j < kUdPositions; j += nthreads) wexp_out[j] = s_wexp[j];
 }

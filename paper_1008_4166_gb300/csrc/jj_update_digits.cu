@@ -10,18 +10,19 @@
 // columns; X (W2 - I) = Xh D'. The rows of Xh carry one exponent each (r_l)
 // and the columns of D' = D (W2 - I) one each (w_j), so the digit products
 // approximate
-//     corr_lj = 2^(r_l + w_j) sum_{t + u <= s + 1} 2^(-7 (t + u)) (Q_t P_u)_lj
-// with Q_t, P_u the t-th and u-th 7-bit digit matrices (|digit| <= 127, exact
-// in fp16) of Xh 2^-r and D' 2^-w. The error is relative to 2^(r_l + w_j), a
-// row scale times a column scale; with s = 12 digits (84 bits) it stays below
-// FP64's own per-entry bound u (|x_lj| + sum_a |x_la| |d_aj|) on the graded
-// iterates of the method, where 8 digits exceed it by up to 7e5.
+//     corr_lj = 2^(r_l + w_j + 4) sum_{t + u <= s + 1} 2^(-8 (t + u)) (Q_t P_u)_lj
+// with Q_t, P_u the t-th and u-th balanced 8-bit digit matrices (digits in
+// [-128, 127], exact in fp16; jj_digits.cuh) of Xh and D' relative to 2^r and
+// 2^w. The error is relative to 2^(r_l + w_j), a row scale times a column
+// scale; with s = 11 digits (88 bits) it stays below FP64's own per-entry
+// bound u (|x_lj| + sum_a |x_la| |d_aj|) on the graded iterates of the method,
+// where 56 bits exceed it by up to 7e5.
 //
-// Exactness. All products of one diagonal d = t + u share the weight 2^-7d
-// and accumulate in one fp32 TMEM group: at most 12 products of K = 64 terms
-// of at most 127^2, below 2^24, so every group sum is an exact integer. The
-// groups are combined with integer shifts (Horner in int64), and one rounding
-// to FP64 ends each output.
+// Exactness. All products of one diagonal d = t + u share the weight 2^-8d
+// and accumulate in one fp32 TMEM group: at most 11 products of K = 64 terms
+// of at most 128^2 in magnitude, below 2^24, so every group sum is an exact
+// integer. The groups are combined with integer shifts (Horner in int64), and
+// one rounding to FP64 ends each output.
 //
 // Pipeline (one persistent CTA per SM, a contiguous range of (pair, 128-row
 // tile) work items each, pairs that the inner solve left unchanged skipped):
@@ -273,10 +274,9 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
         double *ysum = reinterpret_cast<double *>(scr + 3 * UD_TILE_LONGS + UD_TILE_LONGS / 2);
         int q = S.q0, r = S.r0;
         long long acc[32];
-        // Drain n = 1 or 2 consecutive groups g (and g + 1) into the Horner sums.
-        // Two groups fold exactly in int32 first (|S_d| < 2^23.6, so
-        // S_d 128 + S_(d+1) < 2^31), then into int64 with one shift; both TMEM
-        // slots are released after the pair. False when a wait ran out.
+        // Drain n = 1 or 2 consecutive groups g (and g + 1) into the Horner sums
+        // (int64, base 256; |S_d| < 11 * 2^20); both TMEM slots are released
+        // after the pair. False when a wait ran out.
         auto drain = [&](long long g, int n, bool first) -> bool {
             for (int i = 0; i < n; ++i) {
                 const int slot = (int)((g + i) & (UD_TSLOTS - 1));
@@ -302,10 +302,10 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                     const int i0 = __float2int_rn(__uint_as_float(v0[c]));  // exact integers
                     long long& a = acc[h * 8 + c];
                     if (n == 2) {
-                        const int pr = i0 * 128 + __float2int_rn(__uint_as_float(v1[c]));
-                        a = first ? (long long)pr : a * 16384 + pr;
+                        const long long pr = (long long)i0 * 256 + __float2int_rn(__uint_as_float(v1[c]));
+                        a = first ? pr : a * 65536 + pr;
                     } else {
-                        a = first ? (long long)i0 : a * 128 + i0;
+                        a = first ? (long long)i0 : a * 256 + i0;
                     }
                 }
             }
@@ -383,8 +383,8 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                             unsigned long long lo;
                             const long long b = acc[cb + c];
                             if (phaseB) {
-                                // T = accA 2^(7 (s - 6)) + accB
-                                const int sh = 7 * (s - UD_PA);
+                                // T = accA 2^(8 (s - 6)) + accB
+                                const int sh = 8 * (s - UD_PA);
                                 const unsigned long long al = (unsigned long long)av[c] << sh;
                                 const long long ah = av[c] >> (64 - sh);
                                 lo = al + (unsigned long long)b;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                                 lo = (unsigned long long)b;
                                 hi = b >> 63;
                             }
-                            Gd[idx[c]] = xv[c] + i128_scaled_to_double(hi, lo, re + wv[c] - 7 * (s + 1));
+                            Gd[idx[c]] = xv[c] + i128_scaled_to_double(hi, lo, re + wv[c] + 4 - 8 * (s + 1));
                         }
                     }
                 } else if (WIDE && l < rows) {
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                         const size_t si = (size_t)(hh * 32 + c) * UD_M + rl;
                         if (phaseB) {
                             const long long a = scr[si];
-                            const int sh = 7 * (s - UD_PA);
+                            const int sh = 8 * (s - UD_PA);
                             const unsigned long long al = (unsigned long long)a << sh;
                             const long long ah = a >> (64 - sh);
                             lo = al + (unsigned long long)b;
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                         }
                         if (kc == Tq - 1) {
                             ysum[(size_t)(nc * kUdPositions + hh * 32 + c) * UD_M + rl] =
-                                i128_scaled_to_double(hi, lo, e - 7 * (s + 1));
+                                i128_scaled_to_double(hi, lo, e + 4 - 8 * (s + 1));
                         } else {
                             slo[si] = lo;
                             shi[si] = hi;
@@ -583,8 +583,8 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
     } else {
         // ------------------------------------------------------------------
         // Builders: digits of Xh = X D^-1 relative to each row's exponent.
-        // A pass writes three digits (one 21-bit window of each value's 84-bit
-        // fixed-point image) of the warp's rows of the tile, in two batches of
+        // A pass writes three digits (one 24-bit window of each value's 88-bit
+        // biased image) of the warp's rows of the tile, in two batches of
         // tasks; each batch issues all its loads at once (the first batch before
         // the wait for free slots, so that the loads' latency overlaps it). The
         // row exponents are found in the first pass and kept in shared memory.
@@ -726,24 +726,17 @@ __global__ void __launch_bounds__(UD_THREADS, 1) update_digits_kernel(
                             // e_a is the same for the real and imaginary part of a column
                             uint32_t w[NV];
 #pragma unroll
-                            for (int v = 0; v < NV; ++v) w[v] = dg_window21(x[i][v], rexp + ex[v], p);
+                            for (int v = 0; v < NV; ++v) w[v] = dg_window24(x[i][v], rexp + ex[v], p);
                             const uint32_t rowbase = (uint32_t)row * 128u, x7 = (uint32_t)row & 7u;
 #pragma unroll
                             for (int it = 0; it < NI; ++it) {
                                 const uint32_t off = rowbase + ((ichunk[it] ^ x7) << 4) + ilow[it];
-                                const bool n0 = __double_as_longlong(x[i][2 * it]) < 0;
-                                const bool n1 = __double_as_longlong(x[i][2 * it + 1]) < 0;
-                                const uint32_t bias = (n0 ? 0xE400u : 0x6400u) | ((n1 ? 0xE400u : 0x6400u) << 16);
-                                const uint32_t add = bias ^ 0x80008000u;
 #pragma unroll
                                 for (int dd = 0; dd < 3; ++dd) {
                                     if (t0 + dd > t1) break;
-                                    const uint32_t d0 = (w[2 * it] >> (14 - 7 * dd)) & 127u;
-                                    const uint32_t d1 = (w[2 * it + 1] >> (14 - 7 * dd)) & 127u;
-                                    const uint32_t v = d0 | (d1 << 16) | bias;
-                                    uint32_t h2;
-                                    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(h2) : "r"(v), "r"(add));
-                                    *reinterpret_cast<uint32_t *>(slotp[dd] + off) = h2;
+                                    const uint32_t u0 = (w[2 * it] >> (16 - 8 * dd)) & 255u;
+                                    const uint32_t u1 = (w[2 * it + 1] >> (16 - 8 * dd)) & 255u;
+                                    *reinterpret_cast<uint32_t *>(slotp[dd] + off) = dg_pack2(u0, u1);
                                 }
                             }
                         }
@@ -839,10 +832,13 @@ cudaError_t launch_wimage(bool cplx, const double *W, int kmax, const int32_t *p
 }
 
 cudaError_t launch_update_digits(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m,
-                                 const int32_t *pairs, int npairs, int kmax, const int32_t *cexp,
-                                 const UpdDigits &ud, long long *scratch, int nctas,
+                                 int64_t ncols, const int32_t *pairs, int npairs, int kmax, int maxblk,
+                                 const int32_t *cexp, const UpdDigits &ud, long long *scratch, int nctas,
                                  unsigned long long *counters, cudaStream_t st, StepCtl ctl) {
     if (npairs <= 0) return cudaSuccess;
+    if (Gd != Gs && ctl.flags) return cudaErrorInvalidValue;
+    if (maxblk > 0 && un_supported(cplx, Gs, ld, m, ncols, kmax, maxblk))
+        return launch_update_narrow(cplx, Gs, Gd, ld, m, ncols, pairs, npairs, cexp, ud, nctas, counters, st, ctl);
     const int s = ud.slices;
     const int tmax = ud_max_tiles(cplx, kmax);
     if (tmax > kUdMaxTiles || s < 1 || s > kUdMaxSlices || !ud.img || !ud.wexp || !scratch || nctas < 1)
