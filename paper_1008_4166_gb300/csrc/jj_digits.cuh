@@ -46,6 +46,41 @@ __device__ __forceinline__ unsigned __int128 dg_image88(double x, int e) {
     return M + B;
 }
 
+// The same image as three 32-bit words (w0 the least significant), built with
+// 32-bit funnel shifts and selects only (no branch, no 128-bit arithmetic):
+// the significand, left-aligned in a 96-bit word, is shifted right by
+// t = 43 - sh words and bits.
+struct Img96 {
+    uint32_t w0, w1, w2;
+};
+__device__ __forceinline__ Img96 dg_image96(double x, int e) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const int E = (int)((bh >> 20) & 0x7FFu);
+    const uint32_t z2 = __funnelshift_l(bl, bh, 11) | 0x80000000u;  // significand bits 52..21
+    const uint32_t z1 = bl << 11;                                      // bits 20..0, then zeros
+    // V = significand 2^(E - 1075 + 86 - e) = (z2:z1:0) >> t, t >= 10
+    int t = 1032 - E + e;
+    t = (E == 0 || t > 127) ? 127 : t;  // zeros and subnormals: V = 0
+    const uint32_t q = (uint32_t)t >> 5, r = (uint32_t)t & 31u;
+    const uint32_t c2 = z2 >> r;
+    const uint32_t c1 = __funnelshift_r(z1, z2, r);
+    const uint32_t c0 = __funnelshift_r(0u, z1, r);
+    uint32_t w2 = q == 0 ? c2 : 0u;
+    uint32_t w1 = q == 0 ? c1 : (q == 1 ? c2 : 0u);
+    uint32_t w0 = q == 0 ? c0 : (q == 1 ? c1 : (q == 2 ? c2 : 0u));
+    // two's complement when negative: (w ^ m) - m over 96 bits
+    const uint32_t m = (uint32_t)((int32_t)bh >> 31);
+    unsigned long long lo = ((unsigned long long)w1 << 32) | w0;
+    const bool lz = lo == 0ull;
+    lo = (lo ^ (((unsigned long long)m << 32) | m)) + (unsigned long long)(m & 1u);
+    w2 = (w2 ^ m) + ((m & 1u) && lz ? 1u : 0u);
+    // plus the bias 0x80 in each of the bytes 0..10
+    const unsigned long long lb = lo + 0x8080808080808080ull;
+    w2 += 0x808080u + (lb < lo ? 1u : 0u);
+    return Img96{(uint32_t)lb, (uint32_t)(lb >> 32), w2};
+}
+
 // Byte u of digit t (1..11) of an image.
 __device__ __forceinline__ uint32_t dg_byte88(unsigned __int128 U, int t) {
     return (uint32_t)(U >> (8 * (11 - t))) & 255u;

@@ -837,7 +837,7 @@ cudaError_t launch_update_digits(bool cplx, const double *Gs, double *Gd, int64_
                                  unsigned long long *counters, cudaStream_t st, StepCtl ctl) {
     if (npairs <= 0) return cudaSuccess;
     if (Gd != Gs && ctl.flags) return cudaErrorInvalidValue;
-    if (maxblk > 0 && un_supported(cplx, Gs, ld, m, ncols, kmax, maxblk))
+    if (maxblk > 0 && ud.slices == kUdMaxSlices && un_supported(cplx, Gs, ld, m, ncols, kmax, maxblk))
         return launch_update_narrow(cplx, Gs, Gd, ld, m, ncols, pairs, npairs, cexp, ud, nctas, counters, st, ctl);
     const int s = ud.slices;
     const int tmax = ud_max_tiles(cplx, kmax);

@@ -166,14 +166,15 @@ __device__ __forceinline__ double un_i128_to_double(long long hi, unsigned long 
 // Digits T0 .. T0 + NT - 1 (those up to t_hi) of two values at positions
 // (a, a + 1) of one row: a 32-bit store per digit tile.
 template <int T0, int NT>
-__device__ __forceinline__ void un_store_digits(uint8_t *sA, uint32_t off, unsigned __int128 U0,
-                                                unsigned __int128 U1, int t_hi) {
+__device__ __forceinline__ void un_store_digits(uint8_t *sA, uint32_t off, const Img96 &U0, const Img96 &U1,
+                                                int t_hi) {
 #pragma unroll
     for (int i = 0; i < NT; ++i) {
         const int t = T0 + i;
         if (t > t_hi) break;
         const int kb = 11 - t, wi = kb >> 2, bi = kb & 3;
-        const uint32_t w0 = (uint32_t)(U0 >> (32 * wi)), w1 = (uint32_t)(U1 >> (32 * wi));
+        const uint32_t w0 = wi == 0 ? U0.w0 : (wi == 1 ? U0.w1 : U0.w2);
+        const uint32_t w1 = wi == 0 ? U1.w0 : (wi == 1 ? U1.w1 : U1.w2);
         const uint32_t v = (__byte_perm(w0, w1, (uint32_t)(bi | ((4 + bi) << 8))) & 0x00FF00FFu) | 0x65006500u;
         uint32_t h2;
         asm("add.rn.f16x2 %0, %1, %2;" : "=r"(h2) : "r"(v), "r"(0xE580E580u));
@@ -181,12 +182,13 @@ __device__ __forceinline__ void un_store_digits(uint8_t *sA, uint32_t off, unsig
     }
 }
 
-template <bool CPLX>
+template <bool CPLX, int NS>
 __global__ void __launch_bounds__(UN_THREADS, 1) update_narrow_kernel(
     const __grid_constant__ CUtensorMap xmap, const double *Gs, double *Gd, int64_t ld, int64_t m,
     const int32_t *__restrict__ pairs, int npairs, const int32_t *__restrict__ cexp,
-    const uint8_t *__restrict__ wimg, const int32_t *__restrict__ wexp, int slices, int s,
+    const uint8_t *__restrict__ wimg, const int32_t *__restrict__ wexp, int slices,
     unsigned long long *__restrict__ counters, uint64_t wait_ns, StepCtl ctl) {
+    constexpr int s = NS;  // digits per operand
     extern __shared__ __align__(1024) uint8_t un_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)un_smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sB = sm;                                    // s tiles of 8 KB (digits of D')
@@ -196,9 +198,9 @@ __global__ void __launch_bounds__(UN_THREADS, 1) update_narrow_kernel(
     volatile int *abort_flag = &S.abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int hA = s < UN_PA ? s : UN_PA;  // digits (= groups) of phase A
-    const bool phaseB = s > UN_PA;
-    const int UPI = phaseB ? 8 : 4;        // chunk units per item (passes x 4 chunks)
+    constexpr int hA = s < UN_PA ? s : UN_PA;  // digits (= groups) of phase A
+    constexpr bool phaseB = s > UN_PA;
+    constexpr int UPI = phaseB ? 8 : 4;        // chunk units per item (passes x 4 chunks)
     constexpr int E = CPLX ? 2 : 1;
     constexpr int BOXC = un_boxc<CPLX>();
 
@@ -279,53 +281,71 @@ __global__ void __launch_bounds__(UN_THREADS, 1) update_narrow_kernel(
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
         int q = S.q0, r = S.r0;
         long long acc[32];
-        // Drain n = 1 or 2 consecutive groups g (and g + 1) into the Horner
-        // sums (int64, base 256; |S_d| < 11 * 2^20, so S_d 256 + S_(d+1) fits
-        // int64 with room); the TMEM slots are released after the pair. False
-        // when a wait ran out.
-        auto drain = [&](long long g, int n, bool first) -> bool {
-            for (int i = 0; i < n; ++i) {
-                const long long gi = g + i;
-                const int slot = (int)(gi % UN_TSLOTS);
-                const uint32_t par = (uint32_t)((gi / UN_TSLOTS) & 1);
-                const bool ok = __all_sync(0xffffffffu,
-                                           !*abort_flag && mbar_wait(su32(&S.t_full[slot]), par, wait_ns));
-                if (!ok) {
-                    *abort_flag = 1;
-                    return false;
-                }
-            }
+        // Fold N = 1 or 2 consecutive groups g (and g + 1) into the Horner sums
+        // (int64, base 256: acc <- acc 256^N + sum). Group d holds at most d - 1
+        // products, |S_d| <= (d - 1) 2^20, so a pair with d <= 8 folds in int32
+        // first (|S_d 256 + S_(d+1)| <= 1800 * 2^20 < 2^31). The TMEM slots are
+        // released after the fold. False when a wait ran out.
+        auto wait_group = [&](long long gi) -> bool {
+            const int slot = (int)(gi % UN_TSLOTS);
+            const uint32_t par = (uint32_t)((gi / UN_TSLOTS) & 1);
+            const bool ok = __all_sync(0xffffffffu, !*abort_flag && mbar_wait(su32(&S.t_full[slot]), par, wait_ns));
+            if (!ok) *abort_flag = 1;
+            return ok;
+        };
+        auto drain2 = [&](long long g) -> bool {
+            if (!wait_group(g) || !wait_group(g + 1)) return false;
             tc_fence_after();
             const int s0 = (int)(g % UN_TSLOTS), s1 = (int)((g + 1) % UN_TSLOTS);
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 uint32_t v0[8], v1[8];
                 tmem_ld8(lane_base + (uint32_t)(s0 * 64 + hh * 32 + h * 8), v0);
-                if (n == 2) tmem_ld8(lane_base + (uint32_t)(s1 * 64 + hh * 32 + h * 8), v1);
+                tmem_ld8(lane_base + (uint32_t)(s1 * 64 + hh * 32 + h * 8), v1);
                 tmem_wait_ld();
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const int i0 = __float2int_rn(__uint_as_float(v0[c]));  // exact integers
-                    long long &a = acc[h * 8 + c];
-                    if (n == 2) {
-                        const long long pr = (long long)i0 * 256 + __float2int_rn(__uint_as_float(v1[c]));
-                        a = first ? pr : a * 65536 + pr;
-                    } else {
-                        a = first ? (long long)i0 : a * 256 + i0;
-                    }
+                    const int pr = __float2int_rn(__uint_as_float(v0[c])) * 256 + __float2int_rn(__uint_as_float(v1[c]));
+                    acc[h * 8 + c] = acc[h * 8 + c] * 65536 + pr;  // exact integers
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(su32(&S.t_empty[s0]));
-                if (n == 2) mbar_arrive(su32(&S.t_empty[s1]));
+                mbar_arrive(su32(&S.t_empty[s1]));
             }
             return true;
         };
+        auto drain1 = [&](long long g) -> bool {
+            if (!wait_group(g)) return false;
+            tc_fence_after();
+            const int s0 = (int)(g % UN_TSLOTS);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                uint32_t v0[8];
+                tmem_ld8(lane_base + (uint32_t)(s0 * 64 + hh * 32 + h * 8), v0);
+                tmem_wait_ld();
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    acc[h * 8 + c] = acc[h * 8 + c] * 256 + __float2int_rn(__uint_as_float(v0[c]));
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(su32(&S.t_empty[s0]));
+            return true;
+        };
+        // groups [d_lo, d_hi] of an item, from zero sums
         auto drain_range = [&](long long g0, int d_lo, int d_hi) -> bool {
-            for (int d = d_lo; d <= d_hi; d += 2)
-                if (!drain(g0 + d - 2, d + 1 <= d_hi ? 2 : 1, d == d_lo)) return false;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[c] = 0;
+            int d = d_lo;
+#pragma unroll 1
+            for (; d + 1 <= d_hi && d <= 8; d += 2)
+                if (!drain2(g0 + d - 2)) return false;
+#pragma unroll 1
+            for (; d <= d_hi; ++d)
+                if (!drain1(g0 + d - 2)) return false;
             return true;
         };
         const uint32_t park = lane_base + UN_PARK_COL + (uint32_t)(hh * 64);
@@ -358,9 +378,17 @@ __global__ void __launch_bounds__(UN_THREADS, 1) update_narrow_kernel(
                 break;
             }
             const int re = S.rexp[rho][rl];
-            const int32_t *wx = wexp + (size_t)q * kUdPositions + hh * 32;
-            const int sh = 8 * (s - UN_PA);  // T = accA 2^(8 (s - 6)) + accB
+            // output position hh * 32 + c: pivot column c of part hh (complex), column
+            // hh * 32 + c (real); element offsets of the row in the two blocks
+            const int n1 = pd[1];
+            const int64_t ldE = ld * E;
+            const int64_t off_i = ((int64_t)pd[0] * ld + l) * E + (CPLX ? hh : 0);
+            const int64_t off_j = ((int64_t)pd[2] * ld + l) * E + (CPLX ? hh : 0) - (int64_t)n1 * ldE;
+            const int pc0 = CPLX ? 0 : hh * 32;
+            const int4 *wx4 = reinterpret_cast<const int4 *>(wexp + (size_t)q * kUdPositions + hh * 32);
+            constexpr int SH = 8 * (s - UN_PA);  // T = accA 2^(8 (s - 6)) + accB
             const int ebase = re + 4 - 8 * (s + 1);
+            const bool row_ok = l < rows;
             tc_fence_after();
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
@@ -369,38 +397,39 @@ __global__ void __launch_bounds__(UN_THREADS, 1) update_narrow_kernel(
                     tmem_ld8(park + (uint32_t)(8 * b), w);
                     tmem_wait_ld();
                 }
-                int64_t idx[4];
-                double xv[4];
-                int wv[4];
+                const int4 w4 = wx4[b];
+                const int wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int p = hh * 32 + 4 * b + c;  // output position
-                    const int pc = CPLX ? (p & 31) : p;
-                    idx[c] = (pc < k && l < rows) ? (CPLX ? (un_gcol(pd, pc) * ld + l) * 2 + hh : un_gcol(pd, pc) * ld + l)
-                                                  : -1;
-                }
+                for (int hp = 0; hp < 2; ++hp) {  // two outputs at a time (register pressure)
+                    int64_t off[2];
+                    bool in[2];
+                    double xv[2];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    xv[c] = idx[c] >= 0 ? Gs[idx[c]] : 0.0;
-                    wv[c] = wx[4 * b + c];
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (idx[c] < 0) continue;
-                    const long long bb = acc[4 * b + c];
-                    long long hi;
-                    unsigned long long lo;
-                    if (phaseB) {
-                        const long long a = (long long)(((unsigned long long)w[2 * c + 1] << 32) | w[2 * c]);
-                        const unsigned long long al = (unsigned long long)a << sh;
-                        const long long ah = a >> (64 - sh);
-                        lo = al + (unsigned long long)bb;
-                        hi = ah + (bb >> 63) + (lo < al ? 1 : 0);
-                    } else {
-                        lo = (unsigned long long)bb;
-                        hi = bb >> 63;
+                    for (int c = 0; c < 2; ++c) {
+                        const int pc = pc0 + 4 * b + 2 * hp + c;
+                        in[c] = row_ok && pc < k;
+                        off[c] = (pc < n1 ? off_i : off_j) + (int64_t)pc * ldE;
+                        xv[c] = in[c] ? Gs[off[c]] : 0.0;
                     }
-                    Gd[idx[c]] = xv[c] + un_i128_to_double(hi, lo, ebase + wv[c]);
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int cc = 2 * hp + c;
+                        const long long bb = acc[4 * b + cc];
+                        long long hi;
+                        unsigned long long lo;
+                        if (phaseB) {
+                            const long long a = (long long)(((unsigned long long)w[2 * cc + 1] << 32) | w[2 * cc]);
+                            const unsigned long long al = (unsigned long long)a << SH;
+                            const long long ah = a >> (64 - SH);
+                            lo = al + (unsigned long long)bb;
+                            hi = ah + (bb >> 63) + (lo < al ? 1 : 0);
+                        } else {
+                            lo = (unsigned long long)bb;
+                            hi = bb >> 63;
+                        }
+                        const double y = xv[c] + un_i128_to_double(hi, lo, ebase + wv[cc]);
+                        if (in[c]) Gd[off[c]] = y;
+                    }
                 }
             }
             tc_fence_before();
@@ -648,8 +677,8 @@ __global__ void __launch_bounds__(UN_THREADS, 1) update_narrow_kernel(
                         if (CPLX) {
                             const double2 z0 = in0 ? reinterpret_cast<const double2 *>(col(pc0))[lane] : make_double2(0.0, 0.0);
                             const double2 z1 = in1 ? reinterpret_cast<const double2 *>(col(pc0 + 1))[lane] : make_double2(0.0, 0.0);
-                            const unsigned __int128 R0 = dg_image88(z0.x, e0), R1 = dg_image88(z1.x, e1);
-                            const unsigned __int128 I0 = dg_image88(z0.y, e0), I1 = dg_image88(z1.y, e1);
+                            const Img96 R0 = dg_image96(z0.x, e0), R1 = dg_image96(z1.x, e1);
+                            const Img96 I0 = dg_image96(z0.y, e0), I1 = dg_image96(z1.y, e1);
                             const uint32_t offr = sw128_off(row, pc0 * 2), offi = sw128_off(row, (32 + pc0) * 2);
                             if (p == 0) {
                                 un_store_digits<1, UN_PA>(sA, offr, R0, R1, t_hi);
@@ -661,7 +690,7 @@ __global__ void __launch_bounds__(UN_THREADS, 1) update_narrow_kernel(
                         } else {
                             const double v0 = in0 ? reinterpret_cast<const double *>(col(pc0))[lane] : 0.0;
                             const double v1 = in1 ? reinterpret_cast<const double *>(col(pc0 + 1))[lane] : 0.0;
-                            const unsigned __int128 U0 = dg_image88(v0, e0), U1 = dg_image88(v1, e1);
+                            const Img96 U0 = dg_image96(v0, e0), U1 = dg_image96(v1, e1);
                             const uint32_t off = sw128_off(row, pc0 * 2);
                             if (p == 0)
                                 un_store_digits<1, UN_PA>(sA, off, U0, U1, t_hi);
@@ -718,7 +747,7 @@ bool un_supported(bool cplx, const double *Gs, int64_t ld, int64_t m, int64_t nc
     if (ud_max_tiles(cplx, kmax) != 1) return false;
     if (maxblk < 0 || maxblk > (cplx ? un_boxc<true>() : un_boxc<false>())) return false;
     if (((uintptr_t)Gs & 15) != 0 || ((ld * E * 8) & 15) != 0) return false;
-    if (m < 1 || ncols < 1 || (uint64_t)m * E >= (1ull << 31) || ncols >= (1ll << 31)) return false;
+    if (m < 1 || ncols < 1 || (uint64_t)ld * E >= (1ull << 31) || ncols >= (1ll << 31)) return false;
     return encode_tiled() != nullptr;
 }
 
@@ -727,7 +756,7 @@ cudaError_t launch_update_narrow(bool cplx, const double *Gs, double *Gd, int64_
                                  int nctas, unsigned long long *counters, cudaStream_t st, StepCtl ctl) {
     const int E = cplx ? 2 : 1;
     const int s = ud.slices;
-    if (s < 1 || s > kUdMaxSlices || !ud.img || !ud.wexp || nctas < 1) return cudaErrorInvalidValue;
+    if (s != kUdMaxSlices || !ud.img || !ud.wexp || nctas < 1) return cudaErrorInvalidValue;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
@@ -744,10 +773,10 @@ cudaError_t launch_update_narrow(bool cplx, const double *Gs, double *Gd, int64_
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<nctas, UN_THREADS, smem, st>>>(map, Gs, Gd, ld, m, pairs, npairs, cexp, ud.img, ud.wexp, ud.slices,
-                                              s, counters, ctl.wait_ns, ctl);
+                                              counters, ctl.wait_ns, ctl);
         return cudaGetLastError();
     };
-    return cplx ? run(update_narrow_kernel<true>) : run(update_narrow_kernel<false>);
+    return cplx ? run(update_narrow_kernel<true, kUdMaxSlices>) : run(update_narrow_kernel<false, kUdMaxSlices>);
 }
 
 }  // namespace jj
