@@ -663,7 +663,7 @@ int enqueue_sweep(jj_ctx *c, bool plain, int *launches, std::vector<ProfMark> *m
             if (c->ozaki) {
                 JJ_CUDA(launch_colexp_pairs(c->cplx, c->Gw, P.ldw, mrows, pr, np, P.kmax, c->d_cexp,
                                             st, ctl));
-                JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw, P.ldw, mrows, pr, np, c->Ablk, P.kmax,
+                JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw, P.ldw, mrows, P.ncols, pr, np, c->Ablk, P.kmax, P.kmax / 2,
                                           c->d_cexp, c->d_ozacc, c->oz_slices_gram, c->d_cnt, st,
                                           ctl));
                 L += 3;
@@ -756,7 +756,7 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
         if (mark(0)) return JJ_CUDA_ERROR;
         if (c->ozaki) {
             JJ_CUDA(launch_colexp_pairs(c->cplx, c->Gw, P.ldw, c->m, pr, np, P.kmax, c->d_cexp, st, ctl));
-            JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw, P.ldw, c->m, pr, np, c->Ablk, P.kmax, c->d_cexp,
+            JJ_CUDA(launch_gram_ozaki(c->cplx, c->Gw, P.ldw, c->m, P.ncols, pr, np, c->Ablk, P.kmax, P.kmax / 2, c->d_cexp,
                                       c->d_ozacc, c->oz_slices_gram, c->d_cnt, st, ctl));
             L += 3;
         } else {
@@ -806,7 +806,7 @@ int run_three_sweep(jj_ctx *c, int *launches, std::vector<ProfMark> *marks) {
                 if (T.ozaki) {
                     // Gram exponents over the R rows; update exponents over R and W rows
                     JJ_CUDA(launch_colexp_pairs(c->cplx, T.X, T.ldx, P.kmax, ip, ni, T.kmax_in, T.d_cexp, st, ic));
-                    JJ_CUDA(launch_gram_ozaki(c->cplx, T.X, T.ldx, P.kmax, ip, ni, T.Ain, T.kmax_in,
+                    JJ_CUDA(launch_gram_ozaki(c->cplx, T.X, T.ldx, P.kmax, T.xcols, ip, ni, T.Ain, T.kmax_in, T.kmax_in / 2,
                                               T.d_cexp, T.d_ozacc, c->oz_slices_gram, T.d_cnt, st, ic));
                     L += 3;
                     if (T.ozaki_update) {
@@ -1726,14 +1726,17 @@ int jjk_gram(int32_t dtype, int32_t gemm, const void *G, int64_t ld, int64_t m,
         // Scratch from the stream-ordered allocator: column exponents of every
         // column the pairs touch and the int128 accumulators.
         int64_t ncols = 0;
+        int maxblk = 0;
         {
             std::vector<int32_t> hp((size_t)npairs * 4);
             JJ_CUDA(cudaMemcpyAsync(hp.data(), pairs, hp.size() * sizeof(int32_t),
                                     cudaMemcpyDeviceToHost, st));
             JJ_CUDA(cudaStreamSynchronize(st));
-            for (int q = 0; q < npairs; ++q)
+            for (int q = 0; q < npairs; ++q) {
                 ncols = std::max<int64_t>(ncols, std::max(hp[4 * q] + hp[4 * q + 1],
                                                           hp[4 * q + 2] + hp[4 * q + 3]));
+                maxblk = std::max(maxblk, std::max(hp[4 * q + 1], hp[4 * q + 3]));
+            }
         }
         int32_t *cexp = nullptr;
         unsigned long long *acc = nullptr;
@@ -1745,7 +1748,7 @@ int jjk_gram(int32_t dtype, int32_t gemm, const void *G, int64_t ld, int64_t m,
         }
         cudaError_t e = launch_colexp(cplx, (const double *)G, ld, m, ncols, cexp, st);
         if (e == cudaSuccess)
-            e = launch_gram_ozaki(cplx, (const double *)G, ld, m, pairs, npairs, A, kmax, cexp, acc,
+            e = launch_gram_ozaki(cplx, (const double *)G, ld, m, ncols, pairs, npairs, A, kmax, maxblk, cexp, acc,
                                   ozaki_default_slices(true), nullptr, st);
         cudaFreeAsync(cexp, st);
         cudaFreeAsync(acc, st);

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libjjacobi.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -226,8 +227,10 @@ cudaError_t launch_colexp(bool cplx, const double *G, int64_t ld, int64_t m, int
 cudaError_t launch_colexp_pairs(bool cplx, const double *G, int64_t ld, int64_t m,
                                 const int32_t *pairs, int npairs, int kmax, int32_t *cexp,
                                 cudaStream_t st, StepCtl ctl);
-cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
-                              const int32_t *pairs, int npairs, double *A, int kmax,
+// ncols: columns of G; maxblk: the largest block of any pair (0: unknown):
+// narrow pivots whose blocks fit a TMA box take their rows by TMA.
+cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m, int64_t ncols,
+                              const int32_t *pairs, int npairs, double *A, int kmax, int maxblk,
                               const int32_t *cexp, unsigned long long *acc, int slices,
                               unsigned long long *counters, cudaStream_t st,
                               StepCtl ctl = StepCtl());
@@ -246,6 +249,11 @@ cudaError_t launch_update_digits(bool cplx, const double *Gs, double *Gd, int64_
                                  unsigned long long *counters, cudaStream_t st,
                                  StepCtl ctl = StepCtl());
 bool un_supported(bool cplx, const double *Gs, int64_t ld, int64_t m, int64_t ncols, int kmax, int maxblk);
+// Tensor map of a column-major work matrix (complex interleaved) as a 2-D array
+// of doubles: E m x ncols with row stride ld E; boxes of box_rows rows of
+// box_cols columns. False when the driver's encoder is unavailable or refuses.
+bool encode_x_map(CUtensorMap *map, bool cplx, const double *G, int64_t ld, int64_t m, int64_t ncols,
+                  int box_rows, int box_cols);
 cudaError_t launch_update_narrow(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m, int64_t ncols,
                                  const int32_t *pairs, int npairs, const int32_t *cexp, const UpdDigits &ud,
                                  int nctas, unsigned long long *counters, cudaStream_t st, StepCtl ctl);

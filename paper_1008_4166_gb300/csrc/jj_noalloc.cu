@@ -75,7 +75,7 @@ extern "C" int jjk_gram_noalloc(int32_t dtype, const void *G, int64_t ld, int64_
     // previous call's contents).
     if (launch_colexp(cplx, (const double *)G, ld, m, ncols, cexp, st) != cudaSuccess)
         return JJ_CUDA_ERROR;
-    if (launch_gram_ozaki(cplx, (const double *)G, ld, m, pairs, npairs, A, kmax, cexp, acc,
+    if (launch_gram_ozaki(cplx, (const double *)G, ld, m, ncols, pairs, npairs, A, kmax, 0, cexp, acc,
                           ozaki_default_slices(true), nullptr, st) != cudaSuccess)
         return JJ_CUDA_ERROR;
     return JJ_OK;

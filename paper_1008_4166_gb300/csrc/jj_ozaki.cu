@@ -29,6 +29,8 @@
 // chunks of row r XOR-ed with r mod 8. They are written by the producer
 // threads (the digits are computed, not copied), then fenced to the async
 // proxy before the single issuing thread launches tcgen05.mma.
+#include <cstring>
+
 #include "jj_common.cuh"
 #include "jj_tc.cuh"
 
@@ -160,14 +162,23 @@ constexpr int GZ_SLICE_BYTES = 64 * 128;  // 64 operand rows x 128 bytes
 constexpr int GZ_SLICES = 8;              // digits of the Gram operands
 constexpr int GZ_BUF_BYTES = GZ_SLICES * GZ_SLICE_BYTES;
 
-template <bool CPLX>
+constexpr int GZ_XBOX = 16384;            // one TMA box: 64 rows x 16 complex or 32 real columns
+constexpr int GZ_XSLOT = 2 * GZ_XBOX;     // both blocks of a pivot
+
+// TMA: a narrow pivot (one 64-position tile, blocks of at most 16 complex or
+// 32 real columns) whose rows arrive by tiled TMA copies (xmap) into two
+// chunk slots of shared memory, the next chunk's copy in flight while the
+// current one is turned into digits; otherwise the builders read G directly.
+template <bool CPLX, bool TMA>
 __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
+    const __grid_constant__ CUtensorMap xmap,
     const double *__restrict__ G, int64_t ld, int64_t m, const int32_t *__restrict__ pairs,
     const int32_t *__restrict__ cexp, unsigned long long *__restrict__ acc_out, int k2max,
     int rows_per_block, unsigned long long *__restrict__ counters, StepCtl ctl) {
     extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) unsigned long long bar_mma[2];
+    __shared__ __align__(8) unsigned long long bar_x[2];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int sexp[kOzMaxK2];
     __shared__ int s_abort;
@@ -206,6 +217,8 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
     if (tid == 0) {
         mbar_init(su32(&bar_mma[0]), 1);
         mbar_init(su32(&bar_mma[1]), 1);
+        mbar_init(su32(&bar_x[0]), 1);
+        mbar_init(su32(&bar_x[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     // operand rows beyond K2 of a partial last tile stay zero for every chunk
@@ -295,6 +308,71 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
         }
     };
 
+    // TMA: chunk j (rows row0 + 64 j ..) into slot j & 1, issued by thread 0
+    // once the slot's previous chunk has been turned into digits
+    uint8_t *sX = sm + 2 * GZ_BUF_BYTES;
+    constexpr int XBOXC = CPLX ? 16 : 32;  // columns per box
+    int x_last[2] = {-1, -1};              // last chunk issued into each slot (thread 0)
+    auto issue_x = [&](int j) {
+        if (!TMA || tid != 0 || j >= nsc) return;
+        const int slot = j & 1;
+        const uint32_t bar = su32(&bar_x[slot]);
+        const uint32_t dst = su32(sX) + (uint32_t)(slot * GZ_XSLOT);
+        const int y = (int)((CPLX ? 2 : 1) * (row0 + (int64_t)j * GZ_KC));
+        mbar_expect_tx(bar, (uint32_t)(((pd[1] > 0) + (pd[3] > 0)) * GZ_XBOX));
+        if (pd[1] > 0) tma_load_2d(dst, &xmap, y, pd[0], bar);
+        if (pd[3] > 0) tma_load_2d(dst + GZ_XBOX, &xmap, y, pd[2], bar);
+        x_last[slot] = j;
+    };
+    // digits of chunk i from its slot: an item is one pivot column and a row
+    // pair (complex: both of its positions, Re at c and Im at c + k)
+    auto build_x = [&](int i, int b) {
+        const int slot = i & 1;
+        if (!mbar_wait(su32(&bar_x[slot]), (uint32_t)((i >> 1) & 1), ctl.wait_ns)) {
+            s_abort = 1;
+            return;
+        }
+        const int64_t c0 = row0 + (int64_t)i * GZ_KC;
+        const int nrow = (int)min((int64_t)GZ_KC, row1 - c0);
+        uint8_t *buf = sm + (size_t)b * GZ_BUF_BYTES;
+        const uint8_t *xs = sX + (size_t)slot * GZ_XSLOT;
+        constexpr int NIT = (CPLX ? 32 : 64) * (GZ_KC / 2);
+        for (int idx = tid - 32; idx < NIT; idx += GZ_THREADS - 32) {
+            const int c = idx / (GZ_KC / 2);
+            const int lp = (idx % (GZ_KC / 2)) * 2;
+            if (c >= k) continue;
+            const int cs = c < pd[1] ? c : XBOXC + (c - pd[1]);
+            const bool in0 = lp < nrow, in1 = lp + 1 < nrow;
+            if (CPLX) {
+                const double2 *col = reinterpret_cast<const double2 *>(xs + (size_t)cs * (GZ_KC * 16));
+                const double2 z0 = in0 ? col[lp] : make_double2(0.0, 0.0);
+                const double2 z1 = in1 ? col[lp + 1] : make_double2(0.0, 0.0);
+                const int e = sexp[c];  // the same for Re and Im
+                const unsigned long long r0 = fixed63(z0.x, e), r1 = fixed63(z1.x, e);
+                const unsigned long long i0 = fixed63(z0.y, e), i1 = fixed63(z1.y, e);
+                const bool nr0 = neg_bits(z0.x), nr1 = neg_bits(z1.x), ni0 = neg_bits(z0.y), ni1 = neg_bits(z1.y);
+                const uint32_t offr = sw128_off(c, lp * 2), offi = sw128_off(c + k, lp * 2);
+#pragma unroll
+                for (int t = 1; t <= GZ_SLICES; ++t) {
+                    uint8_t *tile = buf + (t - 1) * GZ_SLICE_BYTES;
+                    *reinterpret_cast<uint32_t *>(tile + offr) = dg_digits2_bits(r0, nr0, r1, nr1, t);
+                    *reinterpret_cast<uint32_t *>(tile + offi) = dg_digits2_bits(i0, ni0, i1, ni1, t);
+                }
+            } else {
+                const double *col = reinterpret_cast<const double *>(xs + (size_t)cs * (GZ_KC * 8));
+                const double x0 = in0 ? col[lp] : 0.0, x1 = in1 ? col[lp + 1] : 0.0;
+                const int e = sexp[c];
+                const unsigned long long q0 = fixed63(x0, e), q1 = fixed63(x1, e);
+                const bool n0 = neg_bits(x0), n1 = neg_bits(x1);
+                const uint32_t off = sw128_off(c, lp * 2);
+#pragma unroll
+                for (int t = 1; t <= GZ_SLICES; ++t)
+                    *reinterpret_cast<uint32_t *>(buf + (t - 1) * GZ_SLICE_BYTES + off) =
+                        dg_digits2_bits(q0, n0, q1, n1, t);
+            }
+        }
+    };
+
     // For each A digit t, the B tiles of digits u, u + 1, ... are adjacent in
     // shared memory and their diagonals t + u, t + u + 1, ... are adjacent
     // 64-column groups in TMEM: one product with N = 64 * run covers a run of
@@ -355,11 +433,21 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
     if (!offd) {
         // diagonal tile: one operand tile serves as A and B; two buffers, the
         // digits of the next 64 rows built while the products read the current
-        if (nsc > 0 && warp != 0) build(0, 0, pa0);
+        if (TMA) {
+            issue_x(0);
+            issue_x(1);
+        }
+        if (nsc > 0 && warp != 0) {
+            if (TMA)
+                build_x(0, 0);
+            else
+                build(0, 0, pa0);
+        }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
+        issue_x(2);  // chunk 0's slot has been read
         for (int i = 0; i < nsc && !s_abort; ++i) {
             const int b = i & 1;
             const bool first = (i & 1) == 0;  // first 64 rows of a 128-row accumulation
@@ -371,7 +459,12 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
             pending[b] = true;
             if (i + 1 < nsc) {
                 wait_buf(b ^ 1, ctl.wait_ns);  // the products that read the other buffer are done
-                if (warp != 0) build(i + 1, b ^ 1, pa0);
+                if (warp != 0) {
+                    if (TMA)
+                        build_x(i + 1, b ^ 1);
+                    else
+                        build(i + 1, b ^ 1, pa0);
+                }
                 fence_async_smem();
             }
             if ((i & 1) == 1 || i == nsc - 1) {
@@ -383,6 +476,7 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
             }
             __syncthreads();
             tc_fence_after();
+            issue_x(i + 3);  // chunk i + 1's slot has been read
         }
     } else {
         // off-diagonal tile: A digits in buffer 0, B digits in buffer 1
@@ -438,6 +532,11 @@ __global__ void __launch_bounds__(GZ_THREADS, 1) gram_ozaki_kernel(
             }
         }
     }
+    // chunk copies still in flight (after a wait ran out) land before the
+    // shared memory is released
+    if (TMA && tid == 0)
+        for (int sl = 0; sl < 2; ++sl)
+            if (x_last[sl] >= 0) mbar_wait(su32(&bar_x[sl]), (uint32_t)((x_last[sl] >> 1) & 1), kWaitLimitNs);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -546,8 +645,8 @@ cudaError_t launch_colexp_pairs(bool cplx, const double *G, int64_t ld, int64_t 
 
 // Gram by digit products: cexp must hold the column exponents of G (launch_colexp);
 // acc (ozaki_gram_workspace_bytes) is zeroed here; A receives the FP64 blocks.
-cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
-                              const int32_t *pairs, int npairs, double *A, int kmax,
+cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m, int64_t ncols,
+                              const int32_t *pairs, int npairs, double *A, int kmax, int maxblk,
                               const int32_t *cexp, unsigned long long *acc, int slices,
                               unsigned long long *counters, cudaStream_t st, StepCtl ctl) {
     if (npairs <= 0) return cudaSuccess;
@@ -562,16 +661,25 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
     int rpb = 2 * GZ_KC * 8;
     while (rpb > 2 * GZ_KC && (int64_t)npairs * ntp * ((m + rpb - 1) / rpb) < 2 * 152) rpb /= 2;
     dim3 grid((unsigned)((m + rpb - 1) / rpb), npairs, ntp);
-    const size_t smem = (size_t)2 * GZ_BUF_BYTES + 1024;
-    if (cplx) {
-        if ((e = set_smem(gram_ozaki_kernel<true>, smem)) != cudaSuccess) return e;
-        gram_ozaki_kernel<true><<<grid, GZ_THREADS, smem, st>>>(G, ld, m, pairs, cexp, acc, k2max,
-                                                                 rpb, counters, ctl);
-    } else {
-        if ((e = set_smem(gram_ozaki_kernel<false>, smem)) != cudaSuccess) return e;
-        gram_ozaki_kernel<false><<<grid, GZ_THREADS, smem, st>>>(G, ld, m, pairs, cexp, acc, k2max,
-                                                                  rpb, counters, ctl);
-    }
+    // narrow pivots whose blocks fit a box, on 16-byte aligned rows: chunks by TMA
+    const int E = cplx ? 2 : 1;
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    const bool tma = T == 1 && maxblk > 0 && maxblk <= (cplx ? 16 : 32) && ((uintptr_t)G & 15) == 0 &&
+                     ((ld * E * 8) & 15) == 0 && ncols >= 1 && ld * E < (1ll << 31) &&
+                     encode_x_map(&map, cplx, G, ld, m, ncols, GZ_KC, cplx ? 16 : 32);
+    const size_t smem = (size_t)2 * GZ_BUF_BYTES + (tma ? 2 * (size_t)GZ_XSLOT : 0) + 1024;
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e2 = set_smem(kern, smem);
+        if (e2 != cudaSuccess) return e2;
+        kern<<<grid, GZ_THREADS, smem, st>>>(map, G, ld, m, pairs, cexp, acc, k2max, rpb, counters, ctl);
+        return cudaSuccess;
+    };
+    if (cplx)
+        e = tma ? run(gram_ozaki_kernel<true, true>) : run(gram_ozaki_kernel<true, false>);
+    else
+        e = tma ? run(gram_ozaki_kernel<false, true>) : run(gram_ozaki_kernel<false, false>);
+    if (e != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 g2((unsigned)((kmax * kmax + 255) / 256), npairs);
     if (cplx)

@@ -102,16 +102,6 @@ __device__ __forceinline__ int64_t un_gcol(const int32_t *pd, int c) {
     return c < pd[1] ? (int64_t)pd[0] + c : (int64_t)pd[2] + (c - pd[1]);
 }
 
-// Tiled 2-D TMA load of one box at (x, y) (x: innermost, in elements) into
-// shared memory, completing on the mbarrier's transaction count.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
 // 32 lanes x 16 consecutive 32-bit TMEM columns: store and load.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
     asm volatile(
@@ -751,22 +741,27 @@ bool un_supported(bool cplx, const double *Gs, int64_t ld, int64_t m, int64_t nc
     return encode_tiled() != nullptr;
 }
 
+bool encode_x_map(CUtensorMap *map, bool cplx, const double *G, int64_t ld, int64_t m, int64_t ncols,
+                  int box_rows, int box_cols) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const int E = cplx ? 2 : 1;
+    const cuuint64_t dims[2] = {(cuuint64_t)(m * E), (cuuint64_t)ncols};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * E * 8)};
+    const cuuint32_t box[2] = {(cuuint32_t)(E * box_rows), (cuuint32_t)box_cols};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(G), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_update_narrow(bool cplx, const double *Gs, double *Gd, int64_t ld, int64_t m, int64_t ncols,
                                  const int32_t *pairs, int npairs, const int32_t *cexp, const UpdDigits &ud,
                                  int nctas, unsigned long long *counters, cudaStream_t st, StepCtl ctl) {
-    const int E = cplx ? 2 : 1;
     const int s = ud.slices;
     if (s != kUdMaxSlices || !ud.img || !ud.wexp || nctas < 1) return cudaErrorInvalidValue;
-    EncodeTiledFn enc = encode_tiled();
-    if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)(m * E), (cuuint64_t)ncols};
-    const cuuint64_t strides[1] = {(cuuint64_t)(ld * E * 8)};
-    const cuuint32_t box[2] = {(cuuint32_t)(E * UN_CROWS), (cuuint32_t)(cplx ? un_boxc<true>() : un_boxc<false>())};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(Gs), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    if (!encode_x_map(&map, cplx, Gs, ld, m, ncols, UN_CROWS, cplx ? un_boxc<true>() : un_boxc<false>()))
         return cudaErrorInvalidValue;
     const size_t smem = (size_t)s * kUpdSliceBytes + (size_t)UN_ASLOTS * UN_ATILE + 2 * (size_t)UN_CHUNK_BYTES + 1024;
     auto run = [&](auto kern) -> cudaError_t {
