@@ -323,7 +323,9 @@ def kernel_roofline(jj, P, times, info, gemm_gram_digits, gemm_upd_digits, peaks
         if gemm_upd_digits:
             # the kernel contracts all 64 real-form positions of a pivot
             work = info["pairs_rotated"] * update_products(upd_digits) * 2.0 * m * 64 * 64
-            bound, peak, unit, name = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s", "update_digits_kernel"
+            # narrow pivots with the full digit count run the TMA-fed kernel
+            name = "update_narrow_kernel" if K2 <= 64 and upd_digits == 11 else "update_digits_kernel"
+            bound, peak, unit = "tensor", peaks.get("bf16_tflops", 1900.0), "TFLOP/s"
         else:
             work = info["pairs_rotated"] * m * k * k * mac
             bound, peak, unit, name = "alu", FP64_PEAK_TFLOPS, "TFLOP/s", "update_fp64_kernel"
@@ -642,6 +644,7 @@ def run_threelevel(args):
         G0 = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()
         Gw = torch.empty_like(G0)
     out = {}
+    lam = torch.empty(n, dtype=torch.float64, device="cuda")
     for name, kw in (("three_level", dict(block_width=128, inner_block_width=16, gemm=gemm)),
                      ("three_level_oriented", dict(block_width=128, inner_block_width=16, gemm=gemm,
                                                    block_strategy=jj.JJ_BLOCK_ORIENTED)),
@@ -661,6 +664,15 @@ def run_threelevel(args):
         s = e0.elapsed_time(e1) / 1e3
         out[name] = {"seconds": s, "sweeps": d["sweeps"], "s_per_sweep": s / max(d["sweeps"], 1),
                      "status": d["status"], "rotations": d["rotations"]}
+        if d["status"] == jj.JJ_OK and P.lam_exact is not None:
+            # eigenvalues against the construction J |Lambda| (sorted: lambda comes
+            # out in column order)
+            with torch.cuda.stream(stream):
+                h.jjacobi_extract(lam, None, 0, 1)
+            stream.synchronize()
+            got = np.sort(lam.cpu().numpy())
+            ref = np.sort(np.asarray(P.lam_exact, dtype=np.float64))
+            out[name]["max_rel_err_vs_construction"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
         h.close()
     print(json.dumps({"workload": "threelevel_f64_n16384_b128", "gemm": args.gemm,
                       "generation_s": gen_s, "max_sweeps": args.max_sweeps, "forms": out}),
