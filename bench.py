@@ -216,6 +216,7 @@ def bench_config(args, P, world: int = 1) -> dict:
     name = re.sub(r"_b\d+$", f"_b{args.block_width}", args.workload)
     return {"workload": name, "recipe": args.workload, "m": P.m, "n": P.n,
             "block_width": args.block_width, "gemm": args.gemm,
+            **({"inner_block_width": args.inner_block_width} if getattr(args, "inner_block_width", 0) else {}),
             "update_digits": (args.digits or 11) if args.gemm == "ozaki" and args.block_width else None,
             "strategy": args.strategy, "order": "round_robin",
             "pivot_factor": getattr(args, "pivot_factor", "cholesky"),
@@ -377,7 +378,7 @@ def run_ours(args):
     pf = jj.JJ_PIVOT_SPECIAL if args.pivot_factor == "special" else jj.JJ_PIVOT_CHOLESKY
     h = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
                   block_strategy=strat, max_sweeps=args.max_sweeps, ozaki_slices=args.digits,
-                  pivot_factor=pf)
+                  pivot_factor=pf, inner_block_width=args.inner_block_width)
     ok = (jj.JJ_OK, jj.JJ_NOT_CONVERGED) if args.max_sweeps else (jj.JJ_OK,)
 
     def step():
@@ -435,7 +436,7 @@ def run_ours(args):
     # dominant kernel's roofline
     hp_ = jj.Handle(m, n, dt_code, block_width=args.block_width, gemm=gemm, stream=stream,
                     profile=True, max_sweeps=args.profile_sweeps, block_strategy=strat,
-                    ozaki_slices=args.digits, pivot_factor=pf)
+                    ozaki_slices=args.digits, pivot_factor=pf, inner_block_width=args.inner_block_width)
     with torch.cuda.stream(stream):
         Gw.copy_(G0)
         pinfo_ = hp_.jjacobi_solve(Gw, Gw.stride(1), P.J, allow=(jj.JJ_OK, jj.JJ_NOT_CONVERGED))
@@ -730,6 +731,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block-width", type=int, default=16)
+    ap.add_argument("--inner-block-width", type=int, default=0,
+                    help="inner block width: the three-level form (e.g. --block-width 64 --inner-block-width 16)")
     ap.add_argument("--gemm", default="ozaki", choices=["hybrid", "ozaki", "fp64"])
     ap.add_argument("--pivot-factor", default="cholesky", choices=["cholesky", "special"],
                     help="full-block pivot factor: Cholesky of the pivot, or (3.9)-(3.11)")
