@@ -622,6 +622,44 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def make_threelevel_on_gpu(torch, synth):
+    """The 16384-column real recipe (synth's "threelevel_f64_n16384_b128": the
+    same seed, the same draws in the same order) with its two expensive steps
+    on the GPU: the QR of the Ginibre matrix (cuSOLVER through torch) and the
+    65536 column rotations. The exact eigenvalues are J |Lambda| as in the host
+    recipe; the bits of G differ from the host recipe's by rounding only."""
+    import math
+    import numpy as np
+    w = synth.WORKLOADS["threelevel_f64_n16384_b128"]
+    n, npos = w["n"], w["npos"]
+    rng = np.random.Generator(np.random.PCG64(w["seed"]))
+    Z = torch.from_numpy(rng.standard_normal((n, n))).cuda()
+    Q, R = torch.linalg.qr(Z)
+    del Z
+    Q = Q * torch.sign(torch.diagonal(R))[None, :]
+    del R
+    mag = np.exp(rng.uniform(math.log(w["lam"][0]), math.log(w["lam"][1]), n))
+    J = np.ones(n, dtype=np.int8)
+    J[npos:] = -1
+    draws = synth.random_rotation_draws(n, J, w["rots"], w["smax"], rng, False)
+    G = Q * torch.from_numpy(np.sqrt(mag)).cuda()[None, :]
+    del Q
+    for (r, s_, hyper, par, ph) in draws:
+        if hyper:
+            a, b = math.sqrt(1.0 + par * par), par
+            gr, gs = G[:, r].clone(), G[:, s_].clone()
+            G[:, r] = a * gr + b * gs
+            G[:, s_] = b * gr + a * gs
+        else:
+            a, b = math.cos(par), math.sin(par)
+            gr, gs = G[:, r].clone(), G[:, s_].clone()
+            G[:, r] = a * gr - b * gs
+            G[:, s_] = b * gr + a * gs
+    G = G.t().contiguous().t()  # column-major
+    torch.cuda.synchronize()
+    return G, J, J.astype(np.float64) * mag
+
+
 def run_threelevel(args):
     """The three-level workload (real, n = 16384, b = 128, inner blocks of 16):
     one solve (or --max-sweeps sweeps of it), against the plain form's sweeps."""
@@ -635,14 +673,23 @@ def run_threelevel(args):
     from paper_1008_4166_gb300 import jjacobi as jj
 
     t0 = time.time()
-    P = synth.make_workload("threelevel_f64_n16384_b128", precision="f64")
+    if args.gpu_input:
+        Gsrc, Jv, lam_exact = make_threelevel_on_gpu(torch, synth)
+        P = synth.Problem(G=None, J=Jv, lam_exact=lam_exact, name="threelevel_gpu_input", seed=1004,
+                          graded=False)
+    else:
+        P = synth.make_workload("threelevel_f64_n16384_b128", precision="f64")
+        Gsrc = None
     gen_s = time.time() - t0
-    n, m = P.n, P.m
+    # progress on stderr: generation and every form as it finishes (a long run
+    # that is stopped still leaves its finished forms)
+    print(json.dumps({"generation_s": gen_s}), file=sys.stderr, flush=True)
+    n, m = (Gsrc.shape[1], Gsrc.shape[0]) if Gsrc is not None else (P.n, P.m)
     gemm = {"ozaki": jj.JJ_GEMM_OZAKI_FP16, "hybrid": jj.JJ_GEMM_OZAKI_GRAM,
             "fp64": jj.JJ_GEMM_FP64}[args.gemm]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        G0 = torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()
+        G0 = Gsrc if Gsrc is not None else torch.from_numpy(np.ascontiguousarray(P.G.T)).to("cuda").t()
         Gw = torch.empty_like(G0)
     out = {}
     lam = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -674,6 +721,7 @@ def run_threelevel(args):
             got = np.sort(lam.cpu().numpy())
             ref = np.sort(np.asarray(P.lam_exact, dtype=np.float64))
             out[name]["max_rel_err_vs_construction"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
+        print(json.dumps({name: out[name]}), file=sys.stderr, flush=True)
         h.close()
     print(json.dumps({"workload": "threelevel_f64_n16384_b128", "gemm": args.gemm,
                       "generation_s": gen_s, "max_sweeps": args.max_sweeps, "forms": out}),
@@ -749,6 +797,8 @@ def main():
     ap.add_argument("--max-sweeps", type=int, default=0,
                     help="cap the sweeps of each solve (0: to convergence; for short profiling runs)")
     ap.add_argument("--forms", default="three_level,three_level_oriented,two_level,plain")
+    ap.add_argument("--gpu-input", action="store_true",
+                    help="three-level workload: build the input's QR and rotations on the GPU")
     ap.add_argument("--study", default="", help="orders,crossover: ordering and crossover studies")
     args = ap.parse_args()
     args.block_width_set = any(a.startswith("--block-width") for a in sys.argv[1:])

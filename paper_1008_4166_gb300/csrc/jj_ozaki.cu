@@ -657,8 +657,10 @@ cudaError_t launch_gram_ozaki(bool cplx, const double *G, int64_t ld, int64_t m,
     // tile pairs of the widest pivot (upper triangle of T x T tiles of 64)
     const int T = (k2max + 63) / 64;
     const int ntp = T * (T + 1) / 2;
-    // rows per block: enough blocks to fill the GPU, a multiple of 128 rows
-    int rpb = 2 * GZ_KC * 8;
+    // rows per block: 512 (measured: 512 and 640 rows balance the waves of
+    // 1-per-SM blocks best at m = 4096), fewer when that leaves the GPU idle;
+    // a multiple of 128 rows
+    int rpb = 2 * GZ_KC * 4;
     while (rpb > 2 * GZ_KC && (int64_t)npairs * ntp * ((m + rpb - 1) / rpb) < 2 * 152) rpb /= 2;
     dim3 grid((unsigned)((m + rpb - 1) / rpb), npairs, ntp);
     // narrow pivots whose blocks fit a box, on 16-byte aligned rows: chunks by TMA

@@ -115,14 +115,18 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 
 // Out of the normal range (never for the method's inputs): ldexp, kept out of
 // line so that the common path carries none of its instructions.
-__device__ __noinline__ double un_scaled_slow(unsigned long long mant, int e, bool neg) {
-    const double v = ldexp((double)mant, e);
+__device__ __noinline__ double un_scaled_slow(double d, int sc, bool neg) {
+    const double v = ldexp(d, sc);
     return neg ? -v : v;
 }
 
 // (hi:lo), a two's-complement 128-bit integer, times 2^e rounded to the
-// nearest double (ties to even). Integer operations and selects only: every
-// lane of a warp takes the same instructions whatever its value.
+// nearest double (ties to even). The magnitude is normalised so that its
+// leading one is bit 63 of a 64-bit word t64 whose bit 0 also carries the OR
+// of every bit below it (a sticky bit far under the rounding position); one
+// correctly rounded conversion of t64 then rounds the whole value, and the
+// power of two enters through the exponent field. Selects instead of
+// branches: every lane of a warp takes the same instructions.
 __device__ __forceinline__ double un_i128_to_double(long long hi, unsigned long long lo, int e) {
     const unsigned long long sg = (unsigned long long)(hi >> 63);  // all ones when negative
     unsigned long long l = lo ^ sg, h = (unsigned long long)hi ^ sg;
@@ -135,22 +139,15 @@ __device__ __forceinline__ double un_i128_to_double(long long hi, unsigned long 
     const int z = __clzll((long long)hs);      // 64 when the value is zero
     const int zs = z & 63;
     const unsigned long long top = (hs << zs) | ((ls >> 1) >> (63 - zs));
-    const unsigned long long rest = ls << zs;
-    const int lz = (hz ? 64 : 0) + z;          // leading zeros of the 128-bit magnitude
-    unsigned long long mant = top >> 11;       // 53 bits, leading one at bit 52
-    const unsigned long long rem = top & 0x7FFull;
-    const bool up = rem > 0x400ull || (rem == 0x400ull && (rest != 0ull || (mant & 1ull)));
-    mant += up ? 1ull : 0ull;
-    const int carry = (int)(mant >> 53);
-    mant >>= carry;
-    const int ex = 127 - lz + e + carry;       // exponent of the leading bit
-    const int biased = ex + 1023;
-    if (__builtin_expect(biased < 1 || biased > 2046, 0)) {
-        if (hs == 0ull) return 0.0;
-        return un_scaled_slow(mant, ex - 52, sg != 0ull);
-    }
-    return __longlong_as_double((long long)((sg << 63) | ((unsigned long long)biased << 52) |
-                                            (mant & 0xFFFFFFFFFFFFFull)));
+    const unsigned long long t64 = top | ((ls << zs) != 0ull ? 1ull : 0ull);
+    const int sc = e + 64 - ((hz ? 64 : 0) + z);  // |value| = t64 2^sc
+    const double d = __ull2double_rn(t64);
+    const long long bits = __double_as_longlong(d);
+    const int ex = (int)((bits >> 52) & 0x7FF) + sc;
+    if (hs == 0ull) return 0.0;
+    if (__builtin_expect(ex < 1 || ex > 2046, 0)) return un_scaled_slow(d, sc, sg != 0ull);
+    return __longlong_as_double(
+        (long long)(((unsigned long long)bits + ((unsigned long long)(long long)sc << 52)) | (sg << 63)));
 }
 
 // Digits T0 .. T0 + NT - 1 (those up to t_hi) of two values at positions
