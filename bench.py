@@ -698,7 +698,7 @@ def run_threelevel(args):
                                                    block_strategy=jj.JJ_BLOCK_ORIENTED)),
                      ("two_level", dict(block_width=128, gemm=jj.JJ_GEMM_FP64)),
                      ("plain", dict(block_width=0))):
-        if name not in args.forms:
+        if name not in args.forms.split(","):
             continue
         h = jj.Handle(m, n, jj.JJ_F64, stream=stream, max_sweeps=args.max_sweeps, **kw)
         with torch.cuda.stream(stream):
