@@ -1,7 +1,7 @@
 """The three-level forms at the published full size, in the launch
-configuration bench.py timed for the real workload of order 16384 (outer
-pivots of 256 columns with FP64 contractions, inner blocks of 16 with digit
-products: --gemm ozaki, one capped sweep).
+configuration bench.py times for the real workload of order 16384 (outer
+pivots of 256 columns and inner blocks of 16, digit products at both levels:
+--gemm ozaki, one capped sweep).
 
 The workload's own recipe takes minutes to generate on the host (a Haar QR of
 a 16384 x 16384 matrix), so this test takes a Gaussian G of the same shape and
