@@ -138,3 +138,48 @@ def test_eleven_digits_meet_fp64_accuracy_on_graded_iterates(graded_pivot):
     entry is within FP64's bound with a wide margin."""
     ratio = _ratio(graded_pivot, 11)
     assert np.max(ratio) <= 0.05
+
+
+def _kernel_fold(S, s=11, pa=6):
+    """The update kernels' combination of the diagonal sums S[d] (d = 2..s+1):
+    phase A folds the groups 2..pa+1, phase B the groups pa+2..s+1, each as
+    Horner sums in base 256 with a pair of groups (d, d + 1) first combined in
+    int32 when d <= 8, and the total is T = accA 256^(s - pa) + accB. Returns T,
+    checking every int32 and int64 intermediate against its range."""
+    def fold(lo, hi):
+        acc, d = 0, lo
+        while d + 1 <= hi and d <= 8:
+            pr = S[d] * 256 + S[d + 1]
+            assert -2 ** 31 <= pr < 2 ** 31
+            acc = acc * 65536 + pr
+            assert -2 ** 63 <= acc < 2 ** 63
+            d += 2
+        while d <= hi:
+            acc = acc * 256 + S[d]
+            assert -2 ** 63 <= acc < 2 ** 63
+            d += 1
+        return acc
+    acc_a = fold(2, pa + 1)
+    acc_b = fold(pa + 2, s + 1)
+    return (acc_a << (8 * (s - pa))) + acc_b
+
+
+def test_kernel_fold_order_gives_the_exact_digit_sum():
+    """The kernels' fold of the group sums (int32 pairs, int64 Horner, the
+    phase-A sum shifted by 8 (s - 6) bits) equals the plain sum
+    sum_d S_d 256^(s + 1 - d), on random group sums and on the extreme ones
+    (every digit -128, the largest magnitude a group can reach: d - 1
+    products of 64 terms of 2^14)."""
+    rng = np.random.default_rng(9)
+    s = 11
+    for trial in range(200):
+        if trial == 0:
+            S = {d: (d - 1) * 64 * 128 * 128 for d in range(2, s + 2)}
+        elif trial == 1:
+            S = {d: -(d - 1) * 64 * 128 * 128 for d in range(2, s + 2)}
+        else:
+            S = {d: int(rng.integers(-(d - 1) * 64 * 2 ** 14, (d - 1) * 64 * 2 ** 14 + 1))
+                 for d in range(2, s + 2)}
+        assert all(abs(v) < 2 ** 24 for v in S.values())  # exact in the fp32 accumulators
+        ref = sum(S[d] * 256 ** (s + 1 - d) for d in range(2, s + 2))
+        assert _kernel_fold(S, s) == ref
